@@ -1,0 +1,152 @@
+/*
+ * ks.h -- C-ABI of the GB300 (sm_103a) CKKS hybrid KeySwitch library (libks.so).
+ *
+ * The operation is the KeySwitch of the paper's Sec. II-A / Fig. 1: the input
+ * polynomial d at level L (L+1 RNS limbs, NTT form) is split into dnum digits of
+ * alpha = ceil((L+1)/dnum) limbs (Table I); each digit is raised to the basis
+ * Q u P by iNTT -> fast basis conversion (BConv) -> NTT ("ModUp"), multiplied by
+ * its evaluation-key pair and accumulated over the digits; the two accumulated
+ * polynomials are then brought back to Q by iNTT -> BConv -> NTT and scaled by
+ * P^{-1} ("ModDown"). The four dataflows of Sec. III-A (DigitSerial/DigitParallel
+ * x OutputBulk/OutputChunked, Table III) are selectable and compute identical bits.
+ *
+ * Conventions, all calls:
+ *  - Ring Z_q[x]/(x^N + 1), N = 2^log2n. NTT form: slot k holds a(psi^(2 brv(k)+1))
+ *    where psi = g^((q-1)/2N) and g is the smallest quadratic non-residue >= 2.
+ *  - Polynomials are uint64 limb-major arrays [limb][N]; the Q-limbs come first
+ *    (q_0..q_L), then the P-limbs (p_0..p_{alpha-1}); QP = L+1+alpha limbs.
+ *  - Digit j covers Q-limbs [j*alpha, min((j+1)*alpha, L+1)); beta =
+ *    ceil((L+1)/alpha) digits (beta <= dnum).
+ *  - Every residue is canonical ([0, m)) on input and is written canonical.
+ *  - "_dev" pointers are device memory (16-byte aligned) owned by the caller;
+ *    "_host" pointers are host memory owned by the caller. The library never
+ *    frees caller memory.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) unless stated otherwise. Errors found on the host are returned at
+ *    once and nothing is launched; CUDA launch errors return KS_ECUDA.
+ *  - Return 0 on success or a negative KS_E* code; ks_strerror() names it.
+ */
+#ifndef KS_H_
+#define KS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KS_OK 0
+#define KS_EINVAL (-1)    /* bad shape, level, variant, chunks or null pointer */
+#define KS_EPRIME (-2)    /* a modulus is not prime, not 1 mod 2N, >= 2^62, or repeated */
+#define KS_ENOMEM (-3)    /* device allocation failed */
+#define KS_ECUDA (-4)     /* a CUDA call or launch failed */
+#define KS_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define KS_EALIGN (-6)    /* a pointer is not 16-byte aligned */
+
+/* Dataflows (Sec. III-A, Table III). DS = DigitSerial (digits one after another,
+ * one launch sequence per digit), DP = DigitParallel (all digits in one launch),
+ * OB = OutputBulk (all output limbs per launch), OC = OutputChunked (the output
+ * limbs of each phase split into `chunks` groups processed in turn). */
+#define KS_AUTO 0
+#define KS_DSOB 1
+#define KS_DPOB 2
+#define KS_DSOC 3
+#define KS_DPOC 4
+/* OR-ed into the variant: run BConv, NTT and the key multiply / P^{-1} scaling as
+ * separate kernels instead of fusing BConv into the first NTT pass and the
+ * element-wise step into the last one (the fusion of Sec. III-B). */
+#define KS_UNFUSED 0x100
+
+typedef struct {
+  uint32_t dnum;     /* decomposition number (>= 1) */
+  uint32_t log2n;    /* N = 2^log2n, 4 <= log2n <= 17 */
+  uint32_t L;        /* level: the input has L+1 limbs (1 <= L+1 <= 128) */
+  const uint64_t *q; /* host array of the L+1 ciphertext primes */
+  uint32_t nq;       /* must equal L+1 */
+  const uint64_t *p; /* host array of the alpha special primes */
+  uint32_t np;       /* must equal alpha = ceil((L+1)/dnum) */
+} ks_params;
+
+typedef struct {
+  uint32_t N, alpha, beta, QP, nq, np;
+  size_t evk_words; /* beta*2*QP*N */
+  size_t in_words;  /* (L+1)*N */
+  size_t out_words; /* 2*(L+1)*N */
+  size_t table_bytes; /* device bytes held by the context's constant tables */
+} ks_info;
+
+typedef struct ks_context ks_context;
+
+/* Validates the parameters (primality by deterministic Miller-Rabin, q = 1 mod 2N,
+ * q < 2^62, all distinct) and builds the twiddle and basis-conversion tables on
+ * the current device (synchronous). On success *out owns them until
+ * ks_context_destroy. Returns KS_EINVAL / KS_EPRIME / KS_ENOMEM / KS_ECUDA. */
+int ks_context_create(const ks_params *prm, ks_context **out);
+
+/* Frees the context's tables and internal workspace. NULL is ignored. */
+void ks_context_destroy(ks_context *ctx);
+
+int ks_context_info(const ks_context *ctx, ks_info *info);
+
+/* Evaluation keys from given randomness (the random draws are inputs):
+ *   evk_j = (b_j, a_j), b_j = -a_j*s_to + e_j + [P*g_j]*s_from over Q u P,
+ * with g_j = 1 mod the primes of digit j, 0 mod every other prime.
+ *   s_from_dev [N] int8 ternary: the key switched FROM (s'); s_to_dev [N] int8: TO (s)
+ *   a_dev      [beta][QP][N] uint64, uniform, NTT form
+ *   e_dev      [beta][N] int32, small error (coefficient form)
+ *   evk_dev    [beta][2][QP][N] uint64 output, NTT form (pair index 0 = b, 1 = a)
+ * Not on the timed path; allocates and frees its own scratch. */
+int ks_keygen(ks_context *ctx, const int8_t *s_from_dev, const int8_t *s_to_dev,
+              const uint64_t *a_dev, const int32_t *e_dev, uint64_t *evk_dev,
+              void *stream);
+
+/* Device bytes of scratch that ks_switch needs for (variant, chunks). */
+int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *bytes);
+
+/* One KeySwitch (Sec. II-A, Fig. 1) at level L.
+ *   d_dev   [L+1][N]            input, NTT form
+ *   evk_dev [beta][2][QP][N]    keys from ks_keygen (or any canonical keys)
+ *   out_dev [2][L+1][N]         output pair, NTT form; must not alias the inputs
+ *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED), or KS_AUTO (DPOB, fused)
+ *   chunks  2..10 for the OC variants (0 = 2); ignored for OB
+ *   workspace_dev / workspace_bytes: caller scratch of at least
+ *           ks_workspace_size() bytes, or NULL/0 to use the context's internal
+ *           workspace (allocated on first use and grown as needed; calls that use it
+ *           must then be ordered, e.g. issued on one stream).
+ * Asynchronous on `stream`. */
+int ks_switch(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev,
+              uint64_t *out_dev, int variant, int chunks, void *workspace_dev,
+              size_t workspace_bytes, void *stream);
+
+/* ks_switch with host buffers: copies d_host to the device, switches, copies the
+ * result to out_host, and synchronizes `stream` before returning. Pinned host
+ * memory gives the full copy bandwidth. evk stays device-resident. */
+int ks_switch_host(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
+                   uint64_t *out_host, int variant, int chunks, void *stream);
+
+/* A batch of independent KeySwitches of uneven (dnum, N, L). */
+typedef struct {
+  ks_context *ctx;
+  const uint64_t *d_dev;   /* [L+1][N] */
+  const uint64_t *evk_dev; /* [beta][2][QP][N] */
+  uint64_t *out_dev;       /* [2][L+1][N] */
+} ks_job;
+
+#define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph and replay it */
+#define KS_BATCH_AUTOTUNE 0x2 /* pick per-job variants by timing (cached per shape) */
+
+/* Runs njobs KeySwitches on `stream`. */
+int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream);
+
+/* Reads and clears the context's sticky device error word (bounded waits that
+ * gave up). Synchronizes `stream`. Returns KS_OK or KS_ETIMEOUT. */
+int ks_sync_status(ks_context *ctx, void *stream);
+
+const char *ks_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KS_H_ */

@@ -1,0 +1,45 @@
+// 64-bit modular arithmetic for the KeySwitch kernels (device side).
+//
+// Moduli are < 2^62. Three reductions are used:
+//  * Shoup multiplication by a constant w with w' = floor(w 2^64 / m):
+//      y*w - umulhi(y, w')*m  lies in [0, 2m) for any y < 2^64.
+//  * Montgomery reduction (REDC) of a 128-bit sum T < m 2^64:
+//      (T + u m) / 2^64 with u = T_lo * (-m^-1) mod 2^64, result in [0, 2m).
+//    Basis-conversion and key-multiply sums are accumulated exactly in 128 bits
+//    and reduced once; constants carry the 2^64 factors that REDC removes.
+//  * Lazy ranges: forward butterflies keep values in [0, 4m), inverse ones in
+//    [0, 2m) (Harvey's butterflies); outputs are made canonical at the end.
+#pragma once
+#include <cstdint>
+
+typedef unsigned long long u64;
+
+struct U128 {
+  u64 lo, hi;
+};
+
+__device__ __forceinline__ void mac128(U128 &acc, u64 a, u64 b) {
+  asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+      "madc.hi.u64 %1, %2, %3, %1;"
+      : "+l"(acc.lo), "+l"(acc.hi)
+      : "l"(a), "l"(b));
+}
+
+// T * 2^-64 mod m in [0, 2m) for T < m * 2^64; minv = -m^-1 mod 2^64.
+__device__ __forceinline__ u64 redc(const U128 &t, u64 m, u64 minv) {
+  const u64 u = t.lo * minv;
+  return t.hi + __umul64hi(u, m) + (t.lo != 0ull ? 1ull : 0ull);
+}
+
+// y * w mod m in [0, 2m).
+__device__ __forceinline__ u64 shoup(u64 y, u64 w, u64 wp, u64 m) {
+  const u64 q = __umul64hi(y, wp);
+  return y * w - q * m;
+}
+
+__device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }
+
+// [0, 4m) -> [0, m)
+__device__ __forceinline__ u64 canon4(u64 x, u64 m) { return csub(csub(x, 2 * m), m); }
+
+__device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 m) { return csub(a + b, m); }

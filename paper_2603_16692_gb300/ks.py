@@ -1,0 +1,204 @@
+"""Thin ctypes binding of libks.so (include/ks.h), same names as the C-ABI.
+
+Only argument marshalling happens here: every step of the KeySwitch runs in the
+library's CUDA kernels. PyTorch supplies device memory (uint64 / int8 / int32
+tensors) and streams. There is no CPU fallback: if libks.so cannot be built or
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+KS_OK, KS_EINVAL, KS_EPRIME, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_EALIGN = 0, -1, -2, -3, -4, -5, -6
+KS_AUTO, KS_DSOB, KS_DPOB, KS_DSOC, KS_DPOC = 0, 1, 2, 3, 4
+KS_UNFUSED = 0x100
+KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE = 0x1, 0x2
+VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
+
+
+class KSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class ks_params(ctypes.Structure):
+    _fields_ = [("dnum", ctypes.c_uint32), ("log2n", ctypes.c_uint32), ("L", ctypes.c_uint32),
+                ("q", ctypes.POINTER(ctypes.c_uint64)), ("nq", ctypes.c_uint32),
+                ("p", ctypes.POINTER(ctypes.c_uint64)), ("np", ctypes.c_uint32)]
+
+
+class ks_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
+                ("QP", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("np", ctypes.c_uint32),
+                ("evk_words", ctypes.c_size_t), ("in_words", ctypes.c_size_t),
+                ("out_words", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t)]
+
+
+class ks_job(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("d_dev", ctypes.c_void_p),
+                ("evk_dev", ctypes.c_void_p), ("out_dev", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# exported symbols declared in include/ks.h
+SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_keygen",
+           "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
+           "ks_sync_status", "ks_strerror")
+
+
+def lib_path() -> str:
+    return _build.SO
+
+
+def load(build: bool = True):
+    """Load libks.so (building it first if needed). Raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.SO
+        if not os.path.exists(path):
+            raise RuntimeError(f"libks.so missing at {path}: the CUDA extension is required")
+        l = ctypes.CDLL(path)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        l.ks_context_create.argtypes = [ctypes.POINTER(ks_params), ctypes.POINTER(vp)]
+        l.ks_context_destroy.argtypes = [vp]
+        l.ks_context_destroy.restype = None
+        l.ks_context_info.argtypes = [vp, ctypes.POINTER(ks_info)]
+        l.ks_keygen.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        l.ks_workspace_size.argtypes = [vp, i, i, ctypes.POINTER(sz)]
+        l.ks_switch.argtypes = [vp, vp, vp, vp, i, i, vp, sz, vp]
+        l.ks_switch_host.argtypes = [vp, vp, vp, vp, i, i, vp]
+        l.ks_switch_batch.argtypes = [ctypes.POINTER(ks_job), i, i, vp]
+        l.ks_sync_status.argtypes = [vp, vp]
+        l.ks_strerror.argtypes = [i]
+        l.ks_strerror.restype = ctypes.c_char_p
+        for name in SYMBOLS:
+            if name not in ("ks_context_destroy", "ks_strerror"):
+                getattr(l, name).restype = i
+        _lib = l
+        return l
+
+
+def strerror(code: int) -> str:
+    return load().ks_strerror(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != KS_OK:
+        raise KSError(rc, where)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def ks_context_create(dnum: int, log2n: int, L: int, q, p) -> int:
+    """Returns an opaque context handle (int)."""
+    qa = (ctypes.c_uint64 * len(q))(*[int(x) for x in q])
+    pa = (ctypes.c_uint64 * len(p))(*[int(x) for x in p])
+    prm = ks_params(dnum, log2n, L, qa, len(q), pa, len(p))
+    h = ctypes.c_void_p()
+    _check(load().ks_context_create(ctypes.byref(prm), ctypes.byref(h)), "ks_context_create")
+    return h.value
+
+
+def ks_context_destroy(ctx: int):
+    load().ks_context_destroy(ctx)
+
+
+def ks_context_info(ctx: int) -> dict:
+    inf = ks_info()
+    _check(load().ks_context_info(ctx, ctypes.byref(inf)), "ks_context_info")
+    return {k: getattr(inf, k) for k, _ in ks_info._fields_}
+
+
+def ks_keygen(ctx: int, s_from, s_to, a, e, evk, stream=None):
+    _check(load().ks_keygen(ctx, _ptr(s_from), _ptr(s_to), _ptr(a), _ptr(e), _ptr(evk),
+                            _stream(stream)), "ks_keygen")
+
+
+def ks_workspace_size(ctx: int, variant: int, chunks: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(load().ks_workspace_size(ctx, variant, chunks, ctypes.byref(n)), "ks_workspace_size")
+    return n.value
+
+
+def ks_switch(ctx: int, d, evk, out, variant: int = KS_AUTO, chunks: int = 0, workspace=None,
+              stream=None):
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(load().ks_switch(ctx, _ptr(d), _ptr(evk), _ptr(out), variant, chunks,
+                            _ptr(workspace), ws_bytes, _stream(stream)), "ks_switch")
+
+
+def ks_switch_host(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO, chunks: int = 0,
+                   stream=None):
+    """d_host / out_host: CPU tensors (pinned for full bandwidth) or numpy arrays."""
+    def hp(x):
+        return x.ctypes.data if hasattr(x, "ctypes") else x.data_ptr()
+    _check(load().ks_switch_host(ctx, hp(d_host), _ptr(evk), hp(out_host), variant, chunks,
+                                 _stream(stream)), "ks_switch_host")
+
+
+def ks_switch_batch(jobs, flags: int = 0, stream=None):
+    """jobs: sequence of (ctx, d, evk, out) with device tensors."""
+    arr = (ks_job * len(jobs))()
+    for k, (ctx, d, evk, out) in enumerate(jobs):
+        arr[k] = ks_job(ctx, _ptr(d), _ptr(evk), _ptr(out))
+    _check(load().ks_switch_batch(arr, len(jobs), flags, _stream(stream)), "ks_switch_batch")
+
+
+def ks_sync_status(ctx: int, stream=None) -> int:
+    return load().ks_sync_status(ctx, _stream(stream))
+
+
+class Context:
+    """Owns a ks_context for one parameter set (workload.Params)."""
+
+    def __init__(self, prm):
+        self.prm = prm
+        self.h = ks_context_create(prm.dnum, prm.logn, prm.L, prm.q, prm.p)
+        self.info = ks_context_info(self.h)
+
+    def close(self):
+        if self.h:
+            ks_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def keygen(self, s_from, s_to, a, e, stream=None):
+        import torch
+        prm = self.prm
+        evk = torch.empty((prm.beta, 2, prm.QP, prm.N), dtype=torch.uint64, device=a.device)
+        ks_keygen(self.h, s_from, s_to, a, e, evk, stream)
+        return evk
+
+    def switch(self, d, evk, out=None, variant=KS_AUTO, chunks=0, workspace=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((2, self.prm.L + 1, self.prm.N), dtype=torch.uint64, device=d.device)
+        ks_switch(self.h, d, evk, out, variant, chunks, workspace, stream)
+        return out

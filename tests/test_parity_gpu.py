@@ -1,0 +1,129 @@
+"""GPU KeySwitch == oracle, bit for bit (integer work: the bar is exact equality).
+
+Covers the single-pass NTT sizes (N <= 4096) and the two-pass ones (N >= 8192),
+every dataflow (DSOB, DPOB, DSOC, DPOC) fused and unfused, chunks 1..10 and more
+chunks than limbs, ragged last digits and chunks, dnum = 1 and dnum = L+1, the
+three plain workloads (2,2^13,7), (2,2^15,10), (4,2^16,35) at full size with
+seeds 0-2, key generation, the host-buffer entry point and caller workspaces.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_16692_gb300 import ks
+from paper_2603_16692_gb300 import workload as W
+from tests.gpu_util import dev, first_mismatch, host, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+ALL = [(name, v) for name, v in ks.VARIANTS.items()]
+
+
+def run_gpu(prm, s_from, s_to, a, e, d, variants, chunk_list=(0,)):
+    import torch
+    ctx = ks.Context(prm)
+    try:
+        evk = ctx.keygen(dev(s_from), dev(s_to), dev(a), dev(e))
+        torch.cuda.synchronize()
+        dd = dev(d)
+        outs = {}
+        for v in variants:
+            chunks = chunk_list if v & 0xff in (ks.KS_DSOC, ks.KS_DPOC) else (0,)
+            for c in chunks:
+                out = ctx.switch(dd, evk, variant=v, chunks=c)
+                torch.cuda.synchronize()
+                outs[(v, c)] = host(out)
+        return host(evk), outs
+    finally:
+        ctx.close()
+
+
+def check(cfg, seed, variants, chunk_list=(0,)):
+    prm, s_from, s_to, a, e, d, evk_o, out_o = oracle_case(cfg, seed)
+    evk_g, outs = run_gpu(prm, s_from, s_to, a, e, d, variants, chunk_list)
+    assert np.array_equal(evk_g, evk_o), "keygen: " + first_mismatch(evk_g, evk_o)
+    for (v, c), out in outs.items():
+        assert np.array_equal(out, out_o), f"variant {v:#x} chunks {c}: " + first_mismatch(
+            out, out_o)
+        for i, q in enumerate(prm.q):
+            assert int(out[:, i].max()) < q
+
+
+SMALL = [(2, 1, 1), (1, 2, 0), (2, 3, 2), (3, 4, 5), (2, 5, 7), (4, 6, 9), (10, 7, 12),
+         (3, 8, 6), (2, 9, 3), (5, 10, 11), (2, 11, 4), (3, 12, 8)]
+
+
+@pytest.mark.parametrize("cfg", SMALL)
+def test_single_pass_sizes_all_variants(cfg):
+    vs = [v for _, v in ALL] + [v | ks.KS_UNFUSED for _, v in ALL]
+    check(cfg, 1, vs, chunk_list=(1, 2, 3, 7))
+
+
+TWO_PASS = [(2, 13, 3), (3, 14, 6), (4, 15, 9), (2, 16, 2), (6, 17, 5), (1, 13, 2), (13, 13, 12)]
+
+
+@pytest.mark.parametrize("cfg", TWO_PASS)
+def test_two_pass_sizes_all_variants(cfg):
+    vs = [v for _, v in ALL] + [v | ks.KS_UNFUSED for _, v in ALL]
+    check(cfg, 2, vs, chunk_list=(2, 5, 64))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("cfg", [W.C1, W.C2])
+def test_plain_workloads_every_variant_and_chunks(cfg, seed):
+    vs = [v for _, v in ALL] + [v | ks.KS_UNFUSED for _, v in ALL]
+    check(cfg, seed, vs, chunk_list=tuple(range(2, 11)))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_c3_every_variant(seed):
+    vs = [v for _, v in ALL] + [v | ks.KS_UNFUSED for _, v in ALL]
+    chunks = tuple(range(2, 11)) if seed == 0 else (2, 4, 6)
+    check(W.C3, seed, vs, chunk_list=chunks)
+
+
+def test_host_entry_point_and_workspace():
+    import torch
+    prm, s_from, s_to, a, e, d, evk_o, out_o = oracle_case(W.C2, 0)
+    ctx = ks.Context(prm)
+    try:
+        evk = dev(evk_o)
+        d_h = torch.from_numpy(d.copy()).pin_memory()
+        out_h = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64).pin_memory()
+        ks.ks_switch_host(ctx.h, d_h, evk, out_h, ks.KS_DPOC, 3)
+        assert np.array_equal(out_h.numpy(), out_o)
+        for v in (ks.KS_DSOB, ks.KS_DPOC | ks.KS_UNFUSED):
+            nbytes = ks.ks_workspace_size(ctx.h, v, 4)
+            ws = torch.empty(nbytes // 8, dtype=torch.uint64, device="cuda")
+            out = ctx.switch(dev(d), evk, variant=v, chunks=4, workspace=ws)
+            assert np.array_equal(host(out), out_o)
+            small = torch.empty(nbytes // 8 - 64, dtype=torch.uint64, device="cuda")
+            with pytest.raises(ks.KSError) as ei:
+                ctx.switch(dev(d), evk, variant=v, chunks=4, workspace=small)
+            assert ei.value.code == ks.KS_EINVAL
+    finally:
+        ctx.close()
+
+
+def test_bad_calls_return_errors():
+    import torch
+    prm, s_from, s_to, a, e, d, evk_o, out_o = oracle_case(W.C1, 0)
+    ctx = ks.Context(prm)
+    try:
+        evk = dev(evk_o)
+        dd = dev(d)
+        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
+        lib = ks.load()
+        s = torch.cuda.current_stream().cuda_stream
+        assert lib.ks_switch(ctx.h, dd.data_ptr() + 8, evk.data_ptr(), out.data_ptr(), 0, 0,
+                             None, 0, s) == ks.KS_EALIGN
+        assert lib.ks_switch(ctx.h, dd.data_ptr(), evk.data_ptr(), out.data_ptr(), 9, 0, None, 0,
+                             s) == ks.KS_EINVAL
+        assert lib.ks_switch(ctx.h, dd.data_ptr(), evk.data_ptr(), out.data_ptr(), ks.KS_DSOC,
+                             65, None, 0, s) == ks.KS_EINVAL
+        # nothing was launched by the failed calls; a good call still works
+        ctx.switch(dd, evk, out=out)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(out), out_o)
+        assert ks.ks_sync_status(ctx.h) == ks.KS_OK
+    finally:
+        ctx.close()
