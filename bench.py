@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""KeySwitch throughput benchmark: one JSON line on rank 0.
+
+A step is one hybrid KeySwitch (iNTT, ModUp BConv + NTT, key multiply, iNTT,
+ModDown BConv + NTT, P^-1 scaling) of the workload's input polynomial, launched
+through the C-ABI (ks_switch) on device-resident buffers. Each step uses the
+next (d, evk, out) set from a ring of distinct buffers larger than twice the L2
+cache, so every step reads its inputs from HBM.
+
+Default workload: plain KeySwitch (dnum, N, L) = (2, 2^15, 10). With --gpus N > 1
+(torchrun, one process per GPU) every rank runs an independent replica: the
+KeySwitches of different ranks share nothing ("replicas only", weak scaling).
+
+--impl reference times the plain CPU oracle instead (the baseline the CUDA path
+is checked against), on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2603_16692_gb300 import workload as W  # noqa: E402
+
+METRIC = "KeySwitch/s per (dnum,N,L) on 1 GB300, % HBM roofline, selector regret"
+UNIT = "KeySwitch/s"
+WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
+
+# Integer-pipe peak used for the ALU roofline: 152 SMs x 64 32-bit IMAD lanes per SM
+# per clock x the maximum SM clock, divided by 10 IMADs per 64-bit Shoup modular
+# multiplication (one 64x64 high product ~4 IMAD + two 64-bit low products ~3 each).
+SMS, IMAD_PER_SM_CLK, IMAD_PER_MODOP = 152, 64, 10
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
+# of this bench's command (profiles/); keyed by workload and kernel. None = not
+# captured for the current kernel code.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=30)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--variant", default="DPOB")
+    ap.add_argument("--chunks", type=int, default=0)
+    ap.add_argument("--unfused", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="bound on the oracle sample (CPU baseline)")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def workload_config(prm, variant_name, chunks, unfused, ring, ring_mb, l2_mb):
+    return {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
+            "N": prm.N, "L": prm.L, "alpha": prm.alpha, "beta": prm.beta, "QP": prm.QP,
+            "qbits": 50, "pbits": 60, "variant": variant_name + ("-unfused" if unfused else ""),
+            "chunks": chunks, "l2": f"ring of {ring} distinct (d, evk, out) sets, {ring_mb:.0f} MB"
+            f" > 2 x L2 ({l2_mb:.0f} MB): every step reads HBM"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reported baseline and the reference arm)
+
+def oracle_sample(prm, seconds: float, max_reps: int):
+    """Time oracle KeySwitches on all host cores for about `seconds` (at least one)."""
+    from oracle import oracle as O
+    s_from, s_to, a, e = W.gen_keys(prm, 0)
+    d = W.gen_input(prm, 0)
+    evk = O.keygen(prm, s_from, s_to, a, e)
+    O.keyswitch(prm, d, evk)  # warm (tables, threads)
+    reps, t0 = 0, time.perf_counter()
+    while reps < max_reps:
+        O.keyswitch(prm, d, evk)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return reps, el, O.default_threads()
+
+
+def run_reference(args, prm, rank: int, world: int):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    one = oracle_sample(prm, 0.0, 1)
+    t_one = one[1]
+    budget = 90.0
+    steps = max(1, min(args.steps, int(budget / max(t_one, 1e-6))))
+    warm = min(args.warmup, 2)
+    for _ in range(warm):
+        oracle_sample(prm, 0.0, 1)
+    reps, el, cores = oracle_sample(prm, 1e9, steps)
+    value = reps / el
+    sample = f"{reps} of {args.steps} requested steps timed (each one full KeySwitch of the" \
+             f" workload, all host threads); capped at ~{budget:.0f} s of CPU work"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": reps, "warmup": warm, "ms_per_step": el / reps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
+                       "N": prm.N, "L": prm.L},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100", "-i",
+                                       gpu_id], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.windows = []
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        keep, allrows = [], []
+        for r in rows:
+            if len(r) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(r[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                sm, smax = float(r[2]), float(r[3])
+            except ValueError:
+                continue
+            allrows.append((ts, sm, smax, r))
+            if any(t0 - 1.0 <= ts <= t1 + 1.0 for t0, t1 in self.windows):
+                keep.append((ts, sm, smax, r))
+        use = keep or allrows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for _, _, _, r in use for n, v in zip(names, r[6:10])
+                          if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(s for _, s, _, _ in use),
+                "sm_max_mhz": max(m for _, _, m, _ in use), "reasons": reasons,
+                "samples": len(use), "power_w_max": max(float(r[4]) for *_, r in use
+                                                        if r[4].replace(".", "").isdigit())
+                if any(r[4].replace(".", "").isdigit() for *_, r in use) else None}
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    prm = W.make_params(*WORKLOADS[args.workload])
+
+    if args.impl == "reference":
+        run_reference(args, prm, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2603_16692_gb300 import ks
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    variant = ks.VARIANTS[args.variant.upper()] | (ks.KS_UNFUSED if args.unfused else 0)
+    ctx = ks.Context(prm)
+    dev = torch.device("cuda", local)
+    s_from, s_to, a, e = W.gen_keys(prm, 0)
+
+    def to_dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+    evk0 = ctx.keygen(to_dev(s_from), to_dev(s_to), to_dev(a), to_dev(e))
+    d0 = to_dev(W.gen_input(prm, 0))
+    set_bytes = (evk0.numel() + d0.numel() + 2 * d0.numel()) * 8
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    ring = max(2, -(-2 * l2 // set_bytes) + 1)
+    sets = [(d0.clone(), evk0.clone(), torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64,
+                                                   device=dev)) for _ in range(ring)]
+    del evk0
+    stream = torch.cuda.current_stream(dev)
+    ws = torch.empty(ks.ks_workspace_size(ctx.h, variant, args.chunks) // 8 + 1,
+                     dtype=torch.uint64, device=dev)
+
+    def step(k):
+        d, evk, out = sets[k % ring]
+        ks.ks_switch(ctx.h, d, evk, out, variant, args.chunks, ws, stream)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 30:
+        gpu_id = "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id)
+
+    # warm-up, then the timed region: K steps between two synchronized barriers
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    ev1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    sampler.mark(t_wall0, t_wall1)
+    el_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([el_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * args.steps / (el_ms / 1e3)
+
+    # per-kernel event timing over a second pass of the same steps (kept out of `value`)
+    kprof = min(args.steps, 500)
+    ks.ks_profile_begin()
+    for k in range(kprof):
+        step(k)
+    stats = ks.ks_profile_end()
+    launches_per_step = sum(s["launches"] for s in stats) / kprof
+
+    # end to end through the host-buffer entry point (pinned memory, copies in the region)
+    d_h = torch.from_numpy(W.gen_input(prm, 0)).pin_memory()
+    out_h = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64).pin_memory()
+    ke = max(10, min(args.steps, 1000))
+    for k in range(5):
+        ks.ks_switch_host(ctx.h, d_h, sets[k % ring][1], out_h, variant, args.chunks, stream)
+    barrier()
+    t_wall2 = time.time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(ke):
+        ks.ks_switch_host(ctx.h, d_h, sets[k % ring][1], out_h, variant, args.chunks, stream)
+    e1.record(stream)
+    barrier()
+    sampler.mark(t_wall2, time.time())
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * ke / (e2e_ms / 1e3)
+    clocks = sampler.stop()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * IMAD_PER_SM_CLK * sm_mhz * 1e6 / IMAD_PER_MODOP / 1e9  # Gmodop/s
+    dom = max(stats, key=lambda s: s["ms"])
+    per_launch_ms = dom["ms"] / dom["launches"]
+    ops_l, bytes_l = dom["ops"] / dom["launches"], dom["bytes"] / dom["launches"]
+    alu_ach = ops_l / (per_launch_ms / 1e3) / 1e9
+    hbm_ach = bytes_l / (per_launch_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get(args.workload, {}).get(dom["name"])
+    roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu_ach, "peak": alu_peak,
+                "unit": "Gmodop/s", "frac": alu_ach / alu_peak, "traffic": traffic,
+                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_mhz:.0f}"
+                               f" MHz / {IMAD_PER_MODOP} IMAD per modop",
+                "algo_bytes_per_launch": bytes_l, "hbm_achieved_gbs": hbm_ach,
+                "hbm_frac": hbm_ach / hbm,
+                "share": dom["ms"] / sum(s["ms"] for s in stats)}
+    algo = prm.algo_bytes()
+    ks_gbs = algo * value / world / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded uniform d, ternary keys, rounded-Gaussian errors)",
+        "config": workload_config(prm, args.variant.upper(), args.chunks, args.unfused, ring,
+                                  ring * set_bytes / 1e6, l2 / 1e6),
+        "roofline": roofline,
+        "ks_hbm_roofline": {"bound": "hbm", "achieved": ks_gbs, "peak": hbm, "unit": "GB/s",
+                            "frac": ks_gbs / hbm, "algo_bytes_per_ks": algo,
+                            "peak_source": peaks["source"]},
+        "kernels": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in s.items()}
+                    for s in sorted(stats, key=lambda s: -s["ms"])],
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": (prm.L + 1) * prm.N * 8,
+                "d2h_bytes_per_step": 2 * (prm.L + 1) * prm.N * 8},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu:
+        reps, el, cores = oracle_sample(prm, args.cpu_seconds, 10000)
+        line["cpu_baseline"] = {"value": reps / el, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{reps} full KeySwitches of the same workload in"
+                                          f" {el:.1f} s (bounded at ~{args.cpu_seconds:.0f} s)"}
+    else:
+        line["cpu_baseline"] = None
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

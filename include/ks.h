@@ -143,7 +143,28 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream);
  * gave up). Synchronizes `stream`. Returns KS_OK or KS_ETIMEOUT. */
 int ks_sync_status(ks_context *ctx, void *stream);
 
+/* Per-kernel timing with CUDA events, for measurement. Between ks_profile_begin and
+ * ks_profile_end every kernel launch made by ks_switch on this thread is bracketed
+ * by an event pair on its stream and tagged with its algorithmic traffic (the
+ * bytes it must read and write at least: each input and output once) and its
+ * modular operation count (butterflies, multiply-accumulates, scalings).
+ * ks_profile_end synchronizes those events and aggregates them by kernel name. */
+typedef struct {
+  char name[40];
+  int launches;
+  double ms;     /* summed event time */
+  double bytes;  /* summed algorithmic bytes */
+  double ops;    /* summed modular operations */
+} ks_kernel_stat;
+
+int ks_profile_begin(void);
+int ks_profile_end(ks_kernel_stat *stats, int max_stats, int *count);
+
 const char *ks_strerror(int code);
+
+/* The CUDA runtime's message for the last CUDA error that made a call of this
+ * thread return KS_ECUDA or KS_ENOMEM ("no error" if none). */
+const char *ks_cuda_error_string(void);
 
 #ifdef __cplusplus
 }

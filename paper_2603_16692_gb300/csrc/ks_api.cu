@@ -18,10 +18,7 @@
 #include <new>
 
 #include "ks_internal.h"
-
-namespace ks {
-bool is_prime_u64(u64 n);
-}
+#include "ks_ntt.cuh"
 
 using namespace ks;
 
@@ -82,8 +79,11 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   return KS_OK;
 }
 
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return KS_OK;
+  g_last_cuda = e;
   if (e == cudaErrorMemoryAllocation) return KS_ENOMEM;
   return KS_ECUDA;
 }
@@ -94,25 +94,79 @@ int cuda_rc(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_rc(e_); \
   } while (0)
 
+// ---------------------------------------------------------------------------
+// Optional per-launch event timing (ks_profile_begin / ks_profile_end).
+
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+  double bytes, ops;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+thread_local Profiler g_prof;
+
+// Run one launcher; when profiling, bracket it with events on its stream.
+template <class F>
+cudaError_t timed(const char *name, double bytes, double ops, cudaStream_t s, F f) {
+  if (!g_prof.on) return f();
+  cudaEvent_t a = g_prof.get(), b = g_prof.get();
+  cudaEventRecord(a, s);
+  cudaError_t e = f();
+  cudaEventRecord(b, s);
+  g_prof.recs.push_back({name, a, b, bytes, ops});
+  return e;
+}
+
 int run_plan(ks_context *c, const Plan &pl, const u64 *d, const u64 *evk, u64 *out, u64 *ws,
              cudaStream_t s) {
   const size_t N = c->N;
+  const double W = (double)N * 8;                       // bytes per limb
+  const double BF_A = (double)N / 2 * c->loga;          // butterflies, column pass
+  const double BF_B = (double)N / 2 * c->logb;          // butterflies, row pass
+  const bool single = c->loga == 0;
+  const LaunchTable &L = *c->lt;
   u64 *v = ws + pl.off_v, *tmp = ws + pl.off_tmp, *acc = ws + pl.off_acc, *vp = ws + pl.off_vp,
       *tmp2 = ws + pl.off_tmp2;
   const bool dp = pl.base == KS_DPOB || pl.base == KS_DPOC;
   const bool oc = pl.base == KS_DSOC || pl.base == KS_DPOC;
+  static thread_local TaskList tl, tg;
+  static thread_local std::vector<uint32_t> big;
+  auto dsize = [&](int j) { return std::min(c->nq, (j + 1) * c->alpha) - j * c->alpha; };
 
   // Input iNTT, fused with the per-limb factor N^-1 * Qhat_{j,i}^-1 of the ModUp BConv.
-  KS_TRY(launch_intt(c, d, 0, v, 0, 1, c->nq, 0, c->tab.iscale_q, nullptr, s));
+  {
+    const double nl = c->nq;
+    KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? N : 0)), s, [&] {
+      return L.intt_row(c, d, 0, v, 0, 1, c->nq, 0, c->tab.iscale_q, s);
+    }));
+    if (!single)
+      KS_TRY(timed("intt_col(d)", 2 * nl * W, nl * (BF_A + N), s, [&] {
+        return L.intt_col(c, v, 0, 1, c->nq, 0, c->tab.iscale_q, s);
+      }));
+  }
 
   // Phase 1: ModUp (BConv + NTT) and key multiply, per output group.
-  static thread_local TaskList tl;
-  int targets[kMaxLimbs];
   for (int ch = 0; ch < pl.chunks; ++ch) {
     const int t0 = ch * pl.clen, t1 = std::min(c->qp, t0 + pl.clen);
     if (t0 >= t1) continue;
-    int nt = 0;
-    for (int t = t0; t < t1; ++t) targets[nt++] = t;
+    tg.n = 0;
+    for (int t = t0; t < t1; ++t) tg.t[tg.n++] = pack_task(t, 0, 0);
     SlotMap sm;
     sm.st = 1;
     sm.base = oc ? -t0 : 0;
@@ -120,45 +174,101 @@ int run_plan(ks_context *c, const Plan &pl, const u64 *d, const u64 *evk, u64 *o
     const int jstep = dp ? c->beta : 1;
     for (int j0 = 0; j0 < c->beta; j0 += jstep) {
       const int j1 = j0 + jstep;
-      tl.n = 0;
+      big.clear();
+      double src_b = 0, conv_ops = 0, own = 0;
       for (int j = j0; j < j1; ++j) {
-        const int lo = j * c->alpha, hi = std::min(c->nq, lo + c->alpha);
+        const int lo = j * c->alpha, hi = lo + dsize(j);
+        src_b += dsize(j) * W;
         for (int t = t0; t < t1; ++t) {
-          if (t >= lo && t < hi) continue;
-          tl.t[tl.n++] = pack_task(t, j, j * sm.sj + t * sm.st + sm.base);
+          if (t >= lo && t < hi) {
+            own += 1;
+            continue;
+          }
+          big.push_back(pack_task(t, j, j * sm.sj + t * sm.st + sm.base));
+          conv_ops += (double)N * (dsize(j) + 1);
         }
       }
+      const double nconv = (double)big.size(), nt = tg.n, nd = j1 - j0;
       const bool first = j0 == 0;
+      for (size_t p0 = 0; p0 < big.size(); p0 += kMaxTasks) {
+        tl.n = (int)std::min<size_t>(kMaxTasks, big.size() - p0);
+        std::memcpy(tl.t, big.data() + p0, tl.n * sizeof(uint32_t));
+        const double f = (double)tl.n / std::max(1.0, nconv);
+        if (!pl.unfused) {
+          if (!single)
+            KS_TRY(timed("modup_col", tl.n * W + f * src_b, f * conv_ops + tl.n * BF_A, s,
+                         [&] { return L.modup_col(c, tl, v, tmp, s); }));
+        } else {
+          KS_TRY(timed("bconv_up", tl.n * W + f * src_b, f * conv_ops, s,
+                       [&] { return launch_bconv_up(c, tl, v, tmp, s); }));
+          if (!single)
+            KS_TRY(timed("ntt_col", 2 * tl.n * W, tl.n * BF_A, s,
+                         [&] { return L.ntt_col(c, tl, tmp, s); }));
+          KS_TRY(timed("ntt_row", 2 * tl.n * W, tl.n * BF_B, s,
+                       [&] { return L.ntt_row(c, tl, tmp, s); }));
+        }
+      }
+      // key multiply: evk 2 words per (digit, target); ext from tmp (or d on own limbs);
+      // acc written (and read when accumulating over digit launches)
+      const double km_bytes = (2 * nd * nt + nconv + own + (first ? 2 : 4) * nt) * W;
+      const double km_ops = 2 * nd * nt * N + own * N;
       if (!pl.unfused) {
-        KS_TRY(launch_modup_col(c, tl, v, tmp, s));
-        KS_TRY(launch_modup_row(c, targets, nt, j0, j1, sm, first, d, v, tmp, evk, acc, s));
+        const double b = km_bytes + (single ? src_b - nconv * W : 0);
+        const double o = km_ops + nconv * BF_B + (single ? conv_ops : 0);
+        KS_TRY(timed("modup_row_keymult", b, o, s, [&] {
+          return L.modup_row(c, tg, j0, j1, sm, first, d, v, tmp, evk, acc, s);
+        }));
       } else {
-        KS_TRY(launch_bconv_up(c, tl, v, tmp, s));
-        KS_TRY(launch_ntt_plain(c, tl, tmp, nullptr, s));
-        KS_TRY(launch_keymult(c, targets, nt, j0, j1, sm, first, d, tmp, evk, acc, s));
+        KS_TRY(timed("keymult", km_bytes, km_ops, s, [&] {
+          return launch_keymult(c, tg, j0, j1, sm, first, d, tmp, evk, acc, s);
+        }));
       }
     }
   }
 
   // iNTT of the P-limbs of both accumulators, fused with N^-1 * Phat_k^-1.
-  KS_TRY(launch_intt(c, acc + (size_t)c->nq * N, c->qp, vp, c->np, 2, c->np, c->nq,
-                     c->tab.iscale_p, nullptr, s));
+  {
+    const double nl = 2.0 * c->np;
+    KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? N : 0)), s, [&] {
+      return L.intt_row(c, acc + (size_t)c->nq * N, c->qp, vp, c->np, 2, c->np, c->nq,
+                        c->tab.iscale_p, s);
+    }));
+    if (!single)
+      KS_TRY(timed("intt_col(accP)", 2 * nl * W, nl * (BF_A + N), s, [&] {
+        return L.intt_col(c, vp, c->np, 2, c->np, c->nq, c->tab.iscale_p, s);
+      }));
+  }
 
   // Phase 2: ModDown (BConv P->Q + NTT) and (acc - .) * P^-1, per output group.
   for (int ch = 0; ch < pl.chunks; ++ch) {
     const int i0 = ch * pl.clq, i1 = std::min(c->nq, i0 + pl.clq);
     if (i0 >= i1) continue;
     const int span = oc ? pl.clq : c->nq;
+    const int ibase = oc ? i0 : 0;
     tl.n = 0;
     for (int cc = 0; cc < 2; ++cc)
-      for (int i = i0; i < i1; ++i) tl.t[tl.n++] = pack_task(i, cc, cc * span + (i - (oc ? i0 : 0)));
+      for (int i = i0; i < i1; ++i) tl.t[tl.n++] = pack_task(i, cc, cc * span + (i - ibase));
+    tg.n = 0;
+    for (int i = i0; i < i1; ++i) tg.t[tg.n++] = pack_task(i, 0, i - ibase);
+    const double n = tl.n, vp_b = 2.0 * c->np * W, conv = n * N * (c->np + 1.0);
     if (!pl.unfused) {
-      KS_TRY(launch_moddown_col(c, tl, vp, tmp2, s));
-      KS_TRY(launch_moddown_row(c, tl, vp, tmp2, acc, out, s));
+      if (!single)
+        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, s,
+                     [&] { return L.moddown_col(c, tl, vp, tmp2, s); }));
+      const double b = 3 * n * W + (single ? vp_b - n * W : 0);
+      const double o = n * (BF_B + N) + (single ? conv : 0);
+      KS_TRY(timed("moddown_row", b, o, s, [&] {
+        return L.moddown_row(c, tg, span, vp, tmp2, acc, out, s);
+      }));
     } else {
-      KS_TRY(launch_bconv_down(c, tl, vp, tmp2, s));
-      KS_TRY(launch_ntt_plain(c, tl, tmp2, nullptr, s));
-      KS_TRY(launch_moddown_scale(c, tl, tmp2, acc, out, s));
+      KS_TRY(timed("bconv_down", n * W + vp_b, conv, s,
+                   [&] { return launch_bconv_down(c, tl, vp, tmp2, s); }));
+      if (!single)
+        KS_TRY(timed("ntt_col", 2 * n * W, n * BF_A, s,
+                     [&] { return L.ntt_col(c, tl, tmp2, s); }));
+      KS_TRY(timed("ntt_row", 2 * n * W, n * BF_B, s, [&] { return L.ntt_row(c, tl, tmp2, s); }));
+      KS_TRY(timed("moddown_scale", 3 * n * W, n * N, s,
+                   [&] { return launch_moddown_scale(c, tl, tmp2, acc, out, s); }));
     }
   }
   return KS_OK;
@@ -180,6 +290,8 @@ const char *ks_strerror(int code) {
     default: return "unknown error";
   }
 }
+
+const char *ks_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }
 
 int ks_context_create(const ks_params *prm, ks_context **out) {
   if (!prm || !out || !prm->q || !prm->p) return KS_EINVAL;
@@ -218,7 +330,14 @@ int ks_context_create(const ks_params *prm, ks_context **out) {
   c->np = alpha;
   c->qp = qp;
   c->N = 1 << logn;
-  c->geo = ks::make_geo(logn);
+  c->loga = ks::geo_loga(logn);
+  c->logb = logn - c->loga;
+  c->loggr = ks::geo_loggr(logn);
+  c->lt = ks::launch_table(logn);
+  if (!c->lt) {
+    delete c;
+    return KS_EINVAL;
+  }
   c->mods = mods;
   // basis-conversion sums: run * max_source * m < m 2^64
   c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
@@ -349,7 +468,8 @@ int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uin
       TaskList part;
       part.n = std::min(kMaxTasks, npoly * c->qp - k0);
       for (int k = 0; k < part.n; ++k) part.t[k] = pack_task((k0 + k) % c->qp, 0, k0 + k);
-      err = launch_ntt_plain(c, part, polys, nullptr, s);
+      err = c->lt->ntt_col(c, part, polys, s);
+      if (!err) err = c->lt->ntt_row(c, part, polys, s);
       if (err) break;
     }
     if (err) { rc = cuda_rc(err); break; }
@@ -371,6 +491,42 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
     if (rc) return rc;
   }
   return KS_OK;
+}
+
+int ks_profile_begin(void) {
+  g_prof.on = true;
+  return KS_OK;
+}
+
+int ks_profile_end(ks_kernel_stat *stats, int max_stats, int *count) {
+  g_prof.on = false;
+  std::vector<ks_kernel_stat> agg;
+  int rc = KS_OK;
+  for (auto &r : g_prof.recs) {
+    float ms = 0;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) rc = cuda_rc(e);
+    ks_kernel_stat *hit = nullptr;
+    for (auto &x : agg)
+      if (std::strncmp(x.name, r.name, sizeof(x.name)) == 0) hit = &x;
+    if (!hit) {
+      agg.push_back(ks_kernel_stat{});
+      hit = &agg.back();
+      std::strncpy(hit->name, r.name, sizeof(hit->name) - 1);
+    }
+    hit->launches += 1;
+    hit->ms += ms;
+    hit->bytes += r.bytes;
+    hit->ops += r.ops;
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+  if (count) *count = (int)agg.size();
+  if (stats)
+    for (int k = 0; k < (int)agg.size() && k < max_stats; ++k) stats[k] = agg[k];
+  return rc;
 }
 
 int ks_sync_status(ks_context *c, void *stream) {

@@ -1,0 +1,237 @@
+// Element-wise KeySwitch kernels (sm_103a): the unfused building blocks
+// (BConv, key multiply, ModDown scaling as separate passes) and the key-generation
+// helpers. Coalesced one-word-per-thread loops; grid (blocks over N, tasks).
+#include <cuda_runtime.h>
+
+#include "ks_arith.cuh"
+#include "ks_internal.h"
+
+namespace ks {
+namespace {
+
+struct EArgs {
+  Tables tab;
+  int N, nq, np, qp, alpha, beta, run_up, run_down;
+};
+
+EArgs eargs(const ks_context *c) {
+  EArgs a;
+  a.tab = c->tab;
+  a.N = c->N;
+  a.nq = c->nq;
+  a.np = c->np;
+  a.qp = c->qp;
+  a.alpha = c->alpha;
+  a.beta = c->beta;
+  a.run_up = c->run_up;
+  a.run_down = c->run_down;
+  return a;
+}
+
+// y = sum_k src_k[n] * cst[k] reduced by REDC in runs of `run` terms, canonical.
+__device__ __forceinline__ u64 bconv_point(const u64 *__restrict__ src, size_t N, size_t n,
+                                           int ns, const u64 *cst, int run, const ModInfo &mi) {
+  u64 z = 0;
+  int k = 0;
+  while (k < ns) {
+    const int kend = min(ns, k + run);
+    U128 acc = {0, 0};
+    for (; k < kend; ++k) mac128(acc, __ldg(src + (size_t)k * N + n), cst[k]);
+    z = csub(z + csub(redc(acc, mi.m, mi.minv), mi.m), mi.m);
+  }
+  return z;
+}
+
+// ModUp BConv of digit j onto limb t (Montgomery-scaled), task (t, j, slot).
+__global__ void k_bconv_up(EArgs a, TaskList tl, const u64 *__restrict__ v, u64 *tmp) {
+  __shared__ u64 cst[kMaxLimbs];
+  const uint32_t w = tl.t[blockIdx.y];
+  const int t = task_limb(w), j = task_dig(w);
+  const int i0 = j * a.alpha, ns = min(a.nq, i0 + a.alpha) - i0;
+  for (int k = threadIdx.x; k < ns; k += blockDim.x)
+    cst[k] = a.tab.cup[((size_t)j * a.qp + t) * a.alpha + k];
+  __syncthreads();
+  const ModInfo mi = a.tab.mod[t];
+  const size_t N = a.N;
+  u64 *o = tmp + (size_t)task_slot(w) * N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x)
+    o[n] = bconv_point(v + (size_t)i0 * N, N, n, ns, cst, a.run_up, mi);
+}
+
+// ModDown BConv of the P-limbs of polynomial c onto q_i, task (i, c, slot).
+__global__ void k_bconv_down(EArgs a, TaskList tl, const u64 *__restrict__ vp, u64 *tmp2) {
+  __shared__ u64 cst[kMaxLimbs];
+  const uint32_t w = tl.t[blockIdx.y];
+  const int i = task_limb(w), c = task_dig(w);
+  for (int k = threadIdx.x; k < a.np; k += blockDim.x)
+    cst[k] = a.tab.cdown[(size_t)i * a.alpha + k];
+  __syncthreads();
+  const ModInfo mi = a.tab.mod[i];
+  const size_t N = a.N;
+  u64 *o = tmp2 + (size_t)task_slot(w) * N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x)
+    o[n] = bconv_point(vp + (size_t)c * a.np * N, N, n, a.np, cst, a.run_down, mi);
+}
+
+// acc_c[t] (+)= sum_{j0 <= j < j1} ext_j[t] * evk[j][c][t], task (t).
+__global__ void k_keymult(EArgs a, TaskList tl, int j0, int j1, SlotMap smap, int first,
+                          const u64 *__restrict__ d, const u64 *__restrict__ tmp,
+                          const u64 *__restrict__ evk, u64 *acc) {
+  const int t = task_limb(tl.t[blockIdx.y]);
+  const ModInfo mi = a.tab.mod[t];
+  const size_t N = a.N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x) {
+    U128 s0 = {0, 0}, s1 = {0, 0};
+    for (int j = j0; j < j1; ++j) {
+      const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
+      u64 y;
+      if (t >= lo && t < hi)
+        y = csub(shoup(__ldg(d + (size_t)t * N + n), mi.r1, mi.r1s, mi.m), mi.m);
+      else
+        y = __ldg(tmp + (size_t)(j * smap.sj + t * smap.st + smap.base) * N + n);
+      mac128(s0, y, __ldg(evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + n));
+      mac128(s1, y, __ldg(evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + n));
+    }
+    u64 r0v = csub(redc(s0, mi.m, mi.minv), mi.m);
+    u64 r1v = csub(redc(s1, mi.m, mi.minv), mi.m);
+    u64 *a0 = acc + (size_t)t * N + n;
+    u64 *a1 = acc + ((size_t)a.qp + t) * N + n;
+    if (!first) {
+      r0v = addmod(r0v, *a0, mi.m);
+      r1v = addmod(r1v, *a1, mi.m);
+    }
+    *a0 = r0v;
+    *a1 = r1v;
+  }
+}
+
+// out_c[i] = (acc_c[i] - zhat) * P^-1, task (i, c, slot of zhat).
+__global__ void k_moddown_scale(EArgs a, TaskList tl, const u64 *__restrict__ tmp2,
+                                const u64 *__restrict__ acc, u64 *out) {
+  const uint32_t w = tl.t[blockIdx.y];
+  const int i = task_limb(w), c = task_dig(w);
+  const u64 m = a.tab.mod[i].m;
+  const ulonglong2 pv = a.tab.pinv[i];
+  const size_t N = a.N;
+  const u64 *z = tmp2 + (size_t)task_slot(w) * N;
+  const u64 *ac = acc + ((size_t)c * a.qp + i) * N;
+  u64 *o = out + ((size_t)c * a.nq + i) * N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x)
+    o[n] = csub(shoup(__ldg(ac + n) + m - __ldg(z + n), pv.x, pv.y, m), m);
+}
+
+// polys [2 + beta][QP][N]: 0 = s_from, 1 = s_to, 2 + j = e_j, as residues mod each prime.
+__global__ void k_keygen_lift(EArgs a, const int8_t *__restrict__ sf,
+                              const int8_t *__restrict__ st, const int32_t *__restrict__ e,
+                              u64 *polys) {
+  const int poly = blockIdx.z, t = blockIdx.y;
+  const u64 m = a.tab.mod[t].m;
+  const size_t N = a.N;
+  u64 *o = polys + ((size_t)poly * a.qp + t) * N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x) {
+    long long x;
+    if (poly == 0)
+      x = sf[n];
+    else if (poly == 1)
+      x = st[n];
+    else
+      x = e[(size_t)(poly - 2) * N + n];
+    const u64 r = (u64)(x < 0 ? -x : x) % m;
+    o[n] = (x < 0 && r) ? m - r : r;
+  }
+}
+
+// x*y mod m for arbitrary canonical x, y: two Montgomery reductions (x y 2^-64, then * 2^128).
+__device__ __forceinline__ u64 mulmod_full(u64 x, u64 y, const ModInfo &mi) {
+  U128 p = {0, 0};
+  mac128(p, x, y);
+  const u64 t = csub(redc(p, mi.m, mi.minv), mi.m);
+  U128 p2 = {0, 0};
+  mac128(p2, t, mi.r2);
+  return csub(redc(p2, mi.m, mi.minv), mi.m);
+}
+
+// evk[j][0][t] = -a_j s_to + e_j + [P g_j]_t s_from; evk[j][1][t] = a_j.
+__global__ void k_keygen_combine(EArgs a, const u64 *__restrict__ polys,
+                                 const u64 *__restrict__ arand, u64 *evk) {
+  const int j = blockIdx.z, t = blockIdx.y;
+  const ModInfo mi = a.tab.mod[t];
+  const u64 m = mi.m;
+  const size_t N = a.N;
+  const bool in_digit = t < a.nq && t >= j * a.alpha && t < min((j + 1) * a.alpha, a.nq);
+  const u64 pg = in_digit ? a.tab.pmod[t].x : 0;
+  const u64 *sf = polys + ((size_t)0 * a.qp + t) * N;
+  const u64 *st = polys + ((size_t)1 * a.qp + t) * N;
+  const u64 *ej = polys + ((size_t)(2 + j) * a.qp + t) * N;
+  const u64 *aj = arand + ((size_t)j * a.qp + t) * N;
+  u64 *b = evk + ((size_t)(j * 2 + 0) * a.qp + t) * N;
+  u64 *ao = evk + ((size_t)(j * 2 + 1) * a.qp + t) * N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const u64 av = aj[n];
+    u64 v = ej[n];
+    const u64 as = mulmod_full(av, st[n], mi);
+    v = v >= as ? v - as : v + m - as;
+    v = addmod(v, mulmod_full(pg, sf[n], mi), m);
+    b[n] = v;
+    ao[n] = av;
+  }
+}
+
+int ew_blocks(size_t N) {
+  const size_t b = (N + 1023) / 1024;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_bconv_up(const ks_context *c, const TaskList &tl, const u64 *v, u64 *tmp,
+                            cudaStream_t s) {
+  if (tl.n == 0) return cudaSuccess;
+  k_bconv_up<<<dim3(ew_blocks(c->N), tl.n), 256, 0, s>>>(eargs(c), tl, v, tmp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bconv_down(const ks_context *c, const TaskList &tl, const u64 *vp,
+                              u64 *tmp2, cudaStream_t s) {
+  if (tl.n == 0) return cudaSuccess;
+  k_bconv_down<<<dim3(ew_blocks(c->N), tl.n), 256, 0, s>>>(eargs(c), tl, vp, tmp2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keymult(const ks_context *c, const TaskList &targets, int j0, int j1,
+                           SlotMap sm, bool first, const u64 *d, const u64 *tmp,
+                           const u64 *evk, u64 *acc, cudaStream_t s) {
+  if (targets.n == 0) return cudaSuccess;
+  k_keymult<<<dim3(ew_blocks(c->N), targets.n), 256, 0, s>>>(eargs(c), targets, j0, j1, sm,
+                                                             first ? 1 : 0, d, tmp, evk, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moddown_scale(const ks_context *c, const TaskList &tl, const u64 *tmp2,
+                                 const u64 *acc, u64 *out, cudaStream_t s) {
+  if (tl.n == 0) return cudaSuccess;
+  k_moddown_scale<<<dim3(ew_blocks(c->N), tl.n), 256, 0, s>>>(eargs(c), tl, tmp2, acc, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
+                               const int32_t *e, u64 *polys, cudaStream_t s) {
+  k_keygen_lift<<<dim3(ew_blocks(c->N), c->qp, 2 + c->beta), 256, 0, s>>>(eargs(c), sf, st, e,
+                                                                          polys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keygen_combine(const ks_context *c, const u64 *polys, const u64 *arand,
+                                  u64 *evk, cudaStream_t s) {
+  k_keygen_combine<<<dim3(ew_blocks(c->N), c->qp, c->beta), 256, 0, s>>>(eargs(c), polys, arand,
+                                                                        evk);
+  return cudaGetLastError();
+}
+
+}  // namespace ks

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ks_internal.h"
+#include "ks_ntt.cuh"
 
 namespace ks {
 
@@ -121,33 +122,13 @@ void par_for(int n, F f) {
 
 bool is_prime_u64(u64 n) { return miller_rabin(n); }
 
-Geo make_geo(int logn) {
-  Geo g;
-  g.logn = logn;
-  if (logn <= 12) {
-    g.loga = 0;
-    g.logb = logn;
-    g.Gc = 1;
-    g.Gr = 1;
-    g.ntc = 32;
-    int nt = (1 << logn) / 8;
-    g.ntr = std::max(32, std::min(512, nt));
-  } else {
-    g.loga = logn / 2;
-    g.logb = logn - g.loga;
-    g.Gc = 16;
-    g.Gr = 2048 >> g.logb;
-    g.ntc = 256;
-    g.ntr = 256;
-  }
-  return g;
-}
-
 int build_tables(ks_context *c) {
   const int QP = c->qp, nq = c->nq, np = c->np, alpha = c->alpha, beta = c->beta;
-  const int logn = c->logn, loga = c->geo.loga, logb = c->geo.logb;
+  const int logn = c->logn, loga = c->loga, logb = c->logb, loggr = c->loggr;
   const size_t N = (size_t)1 << logn, N1 = (size_t)1 << loga, N2 = (size_t)1 << logb;
+  const size_t GR = (size_t)1 << loggr;
   const size_t rowlen = (N2 - 1) * N1;
+  const size_t twr_tile = (N2 - 1) * GR;  // entries per row tile
 
   std::vector<ModInfo> mod(QP);
   std::vector<ulonglong2> twc_f(QP * N1), twc_i(QP * N1), twr_f(QP * rowlen),
@@ -178,16 +159,20 @@ int build_tables(ks_context *c) {
       twc_f[t * N1 + k] = shoup_pair(k ? pw[e] : 1, m);
       twc_i[t * N1 + k] = shoup_pair(k ? pwi[e] : 1, m);
     }
-    // Row table: entry ((2^ls - 1 + c) * N1 + r) = psi^brv_logn((N1 + r) 2^ls + c).
-    for (int ls = 0; ls < logb; ++ls)
-      for (size_t cc = 0; cc < ((size_t)1 << ls); ++cc)
-        for (size_t r = 0; r < N1; ++r) {
-          const size_t k = ((N1 + r) << ls) + cc;
-          const unsigned e = brv((unsigned)k, logn);
-          const size_t idx = t * rowlen + ((((size_t)1 << ls) - 1 + cc) << loga) + r;
-          twr_f[idx] = shoup_pair(pw[e], m);
-          twr_i[idx] = shoup_pair(pwi[e], m);
-        }
+    // Row table, by row tile b of GR rows (r = b*GR + g), stage-major inside a tile:
+    // entry (b*(N2-1) + 2^ls - 1 + c)*GR + g = psi^brv_logn((N1 + r) 2^ls + c).
+    for (size_t b = 0; b < N1 / GR; ++b)
+      for (int ls = 0; ls < logb; ++ls)
+        for (size_t cc = 0; cc < ((size_t)1 << ls); ++cc)
+          for (size_t g = 0; g < GR; ++g) {
+            const size_t r = b * GR + g;
+            const size_t k = ((N1 + r) << ls) + cc;
+            const unsigned e = brv((unsigned)k, logn);
+            const size_t idx =
+                t * rowlen + b * twr_tile + ((((size_t)1 << ls) - 1 + cc) << loggr) + g;
+            twr_f[idx] = shoup_pair(pw[e], m);
+            twr_i[idx] = shoup_pair(pwi[e], m);
+          }
   });
 
   // iNTT scales: N^-1 * Qhat_{j,i}^-1 mod q_i for the digit j holding i.

@@ -38,25 +38,14 @@ __host__ __device__ inline int task_limb(uint32_t w) { return (int)(w & 0xff); }
 __host__ __device__ inline int task_dig(uint32_t w) { return (int)((w >> 8) & 0xff); }
 __host__ __device__ inline int task_slot(uint32_t w) { return (int)(w >> 16); }
 
-// Geometry of the two-pass NTT: N = N1 * N2. The column pass runs the first
-// log N1 stages on N2 independent N1-point columns (stride N2); the row pass
-// runs the remaining log N2 stages on N1 contiguous rows of N2 elements. For
-// N <= 4096 there is a single pass (N1 = 1) done by the row kernels.
-struct Geo {
-  int logn, loga, logb;  // N = 2^logn, N1 = 2^loga, N2 = 2^logb
-  int Gc;                // columns per column-pass tile
-  int Gr;                // rows per row-pass tile
-  int ntc, ntr;          // threads per CTA for the column / row kernels
-};
-
 // Device-resident constant tables of one context (all pointers into one
 // allocation).
 struct Tables {
   ModInfo *mod;          // [QP]
   ulonglong2 *twc_f;     // [QP][N1]  column-pass forward twiddles (w, w')
   ulonglong2 *twc_i;     // [QP][N1]  column-pass inverse twiddles
-  ulonglong2 *twr_f;     // [QP][(N2-1)*N1] row-pass forward twiddles
-  ulonglong2 *twr_i;     // [QP][(N2-1)*N1]
+  ulonglong2 *twr_f;     // [QP][N1/GR][N2-1][GR] row-pass forward twiddles by row tile
+  ulonglong2 *twr_i;     // [QP][N1/GR][N2-1][GR]
   ulonglong2 *iscale_q;  // [nq]  N^-1 * Qhat_{j,i}^-1 mod q_i   (Shoup pair)
   ulonglong2 *iscale_p;  // [np]  N^-1 * Phat_k^-1 mod p_k
   u64 *cup;              // [beta][QP][alpha] (Qhat_{j,i} mod m_t) 2^128 mod m_t
@@ -66,12 +55,15 @@ struct Tables {
   int *err;              // sticky device error word
 };
 
+struct LaunchTable;
+
 }  // namespace ks
 
 struct ks_context {
   int dnum, logn, L, alpha, beta, nq, np, qp;
   int N;
-  ks::Geo geo;
+  int loga, logb, loggr;  // two-pass split N = 2^loga * 2^logb; rows per row tile 2^loggr
+  const ks::LaunchTable *lt = nullptr;
   int run_up = 1, run_down = 1;  // max terms per exact 128-bit BConv sum
   std::vector<u64> mods;  // host copy, Q then P
   void *table_mem = nullptr;
@@ -91,38 +83,52 @@ namespace ks {
 
 // Host-side helpers (ks_host.cu)
 int build_tables(ks_context *ctx);
-Geo make_geo(int logn);
+bool is_prime_u64(u64 n);
 
-// Launchers (ks_kernels.cu). All return cudaError_t of the launch.
 struct SlotMap {
   int sj, st, base;  // slot = j*sj + t*st + base
 };
 
-cudaError_t launch_intt(const ks_context *c, const u64 *src, int src_outer, u64 *dst,
-                        int dst_outer, int outer, int inner, int prime_base,
-                        const ulonglong2 *scale, u64 *mid, cudaStream_t s);
-cudaError_t launch_modup_col(const ks_context *c, const TaskList &tl, const u64 *v,
-                             u64 *tmp, cudaStream_t s);
-cudaError_t launch_modup_row(const ks_context *c, const int *targets, int ntargets, int j0,
-                             int j1, SlotMap sm, bool first, const u64 *d, const u64 *v,
-                             const u64 *tmp, const u64 *evk, u64 *acc, cudaStream_t s);
-cudaError_t launch_moddown_col(const ks_context *c, const TaskList &tl, const u64 *vp,
-                               u64 *tmp2, cudaStream_t s);
-cudaError_t launch_moddown_row(const ks_context *c, const TaskList &tl, const u64 *vp,
-                               const u64 *tmp2, const u64 *acc, u64 *out, cudaStream_t s);
-// unfused building blocks
+// Per-N launchers of the templated NTT kernels (ks_kern.cuh, ks_inst_*.cu).
+struct LaunchTable {
+  // iNTT of `outer` x `inner` limbs: src + (o*src_outer + i)*N -> dst + (o*dst_outer + i)*N,
+  // limb i modulo prime prime_base + i, scaled by scale[i] (Shoup pair). Row pass
+  // first (src -> dst), then the column pass in place on dst (none when N <= 4096).
+  cudaError_t (*intt_row)(const ks_context *, const u64 *src, int src_outer, u64 *dst,
+                          int dst_outer, int outer, int inner, int prime_base,
+                          const ulonglong2 *scale, cudaStream_t);
+  cudaError_t (*intt_col)(const ks_context *, u64 *dst, int dst_outer, int outer, int inner,
+                          int prime_base, const ulonglong2 *scale, cudaStream_t);
+  // ModUp column pass: tasks (t, j, slot): BConv of digit j onto limb t + first NTT pass.
+  cudaError_t (*modup_col)(const ks_context *, const TaskList &, const u64 *v, u64 *tmp,
+                           cudaStream_t);
+  // ModUp row pass + key multiply: tasks (t): digits j0..j1-1 into acc.
+  cudaError_t (*modup_row)(const ks_context *, const TaskList &, int j0, int j1, SlotMap,
+                           bool first, const u64 *d, const u64 *v, const u64 *tmp,
+                           const u64 *evk, u64 *acc, cudaStream_t);
+  // ModDown column pass: tasks (i, c, slot): BConv of the P-limbs of c onto q_i + NTT pass.
+  cudaError_t (*moddown_col)(const ks_context *, const TaskList &, const u64 *vp, u64 *tmp2,
+                             cudaStream_t);
+  // ModDown row pass + scaling: tasks (i, -, slot of c=0); c = 1 uses slot + span.
+  cudaError_t (*moddown_row)(const ks_context *, const TaskList &, int span, const u64 *vp,
+                             const u64 *tmp2, const u64 *acc, u64 *out, cudaStream_t);
+  // Plain forward NTT in place of buf[slot] for tasks (t, -, slot): column pass (none
+  // when N <= 4096), then row pass with canonical output.
+  cudaError_t (*ntt_col)(const ks_context *, const TaskList &, u64 *buf, cudaStream_t);
+  cudaError_t (*ntt_row)(const ks_context *, const TaskList &, u64 *buf, cudaStream_t);
+};
+const LaunchTable *launch_table(int logn);
+
+// Element-wise kernels (ks_elem.cu): the unfused building blocks and keygen.
 cudaError_t launch_bconv_up(const ks_context *c, const TaskList &tl, const u64 *v, u64 *tmp,
                             cudaStream_t s);
 cudaError_t launch_bconv_down(const ks_context *c, const TaskList &tl, const u64 *vp,
                               u64 *tmp2, cudaStream_t s);
-cudaError_t launch_ntt_plain(const ks_context *c, const TaskList &tl, u64 *buf, u64 *mid,
-                             cudaStream_t s);
-cudaError_t launch_keymult(const ks_context *c, const int *targets, int ntargets, int j0,
-                           int j1, SlotMap sm, bool first, const u64 *d, const u64 *tmp,
+cudaError_t launch_keymult(const ks_context *c, const TaskList &targets, int j0, int j1,
+                           SlotMap sm, bool first, const u64 *d, const u64 *tmp,
                            const u64 *evk, u64 *acc, cudaStream_t s);
 cudaError_t launch_moddown_scale(const ks_context *c, const TaskList &tl, const u64 *tmp2,
                                  const u64 *acc, u64 *out, cudaStream_t s);
-// keygen helpers
 cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
                                const int32_t *e, u64 *polys, cudaStream_t s);
 cudaError_t launch_keygen_combine(const ks_context *c, const u64 *polys, const u64 *a,

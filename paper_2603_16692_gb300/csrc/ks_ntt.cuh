@@ -1,138 +1,147 @@
-// Negacyclic NTT stages on a shared-memory tile (device side).
+// Negacyclic NTT stages on a shared-memory tile (device side), with the tile
+// geometry fixed at compile time.
 //
 // Transform (ring x^N + 1): forward Cooley-Tukey stages s = 0..logN-1 with
 // m = 2^s, t = N/2^(s+1) and twiddle psi^brv(m+i) for block i; this gives slot
 // k = a(psi^(2 brv(k)+1)) (bit-reversed evaluation order). The inverse runs the
 // Gentleman-Sande stages in reverse with psi^-brv(m+i), then scales by N^-1.
 //
-// A tile holds G independent sub-transforms of M = 2^logM points; point x of
+// N = N1 * N2. The column pass runs stages 0..log N1-1 on the N2 columns (each an
+// N1-point transform with twiddle index 2^ls + c for local stage ls, block c);
+// the row pass runs the remaining stages on the N1 rows of N2 contiguous points
+// (twiddle index (N1 + row) 2^ls + c). For N <= 4096 one row pass does all.
+//
+// A tile holds G = 2^LOGG sub-transforms of M = 2^LOGM points; point x of
 // sub-transform g lives at s[x*P + g] (P = G+1 for G > 1: an odd pitch keeps
-// 64-bit accesses free of bank conflicts when consecutive threads walk x).
-// Both passes of the two-pass NTT (columns of N1 points, rows of N2 points) are
-// such sub-transforms: local stage ls, local block c use the global twiddle
-// index (B << ls) + c, with B = 1 for the column pass and B = N1 + row for the
-// row pass. TwAcc turns (ls, c, g) into an index of the pass's twiddle table.
+// 64-bit accesses free of bank conflicts). Twiddles sit in shared memory:
+// column pass: tw[k], k = 2^ls + c (the first N1 entries of the table);
+// row pass: tw[(2^ls - 1 + c) * G + g] (the tile's rows, stage-major).
 //
 // Each round moves 2^R points of one butterfly group into registers, runs R
-// stages there (radix-2^R), and writes them back.
+// stages there (radix-2^R), and writes them back; every offset is a constant.
 #pragma once
 #include "ks_arith.cuh"
 
 namespace ks {
 
-struct TwAcc {
-  const ulonglong2 *tw;
-  int off;        // 0: column table indexed by (1<<ls)+c;  1: row table
-  int logstride;  // 0 for the column table, log N1 for the row table
-  int rowbase;    // row of sub-transform g = 0 (row pass)
-  int rowstep;    // 1 for the row pass, 0 for the column pass
-  __device__ __forceinline__ ulonglong2 get(int ls, int c, int g) const {
-    const int idx = ((((1 << ls) + c - off)) << logstride) + rowbase + g * rowstep;
-    return __ldg(tw + idx);
-  }
+// Compile-time geometry of the two passes for N = 2^LOGN (also used on the host
+// to lay out the row-pass twiddle table by row tile).
+__host__ __device__ constexpr int geo_loga(int logn) { return logn <= 12 ? 0 : logn / 2; }
+__host__ __device__ constexpr int geo_tile_log(int logn) {
+  return logn <= 12 ? logn : (logn >= 15 ? 11 : 10);
+}
+__host__ __device__ constexpr int geo_loggr(int logn) {
+  return geo_tile_log(logn) - (logn - geo_loga(logn));
+}
+
+template <int LOGN>
+struct GeoT {
+  static constexpr int LOGA = geo_loga(LOGN);  // log N1
+  static constexpr int LOGB = LOGN - LOGA;     // log N2
+  static constexpr int TILE_LOG = geo_tile_log(LOGN);
+  static constexpr int LOGGC = LOGA == 0 ? 0 : TILE_LOG - LOGA;  // columns per column tile
+  static constexpr int LOGGR = TILE_LOG - LOGB;                  // rows per row tile
+  static constexpr int TILE = 1 << TILE_LOG;
+  static constexpr int NT = TILE / 8 < 32 ? 32 : TILE / 8;  // threads: one radix-8 group each
+  static constexpr int EPT = (TILE + NT - 1) / NT;           // tile elements per thread
+  static constexpr int GC = 1 << LOGGC, GR = 1 << LOGGR;
+  static constexpr int PC = GC == 1 ? 1 : GC + 1;
+  static constexpr int PR = GR == 1 ? 1 : GR + 1;
+  static constexpr int N1 = 1 << LOGA, N2 = 1 << LOGB;
+  static constexpr int TWC = N1;                  // column-pass twiddles per tile
+  static constexpr int TWR = (N2 - 1) * GR;       // row-pass twiddles per tile
+  static constexpr int SMEM_COL = (N1 * PC) * 8 + TWC * 16;
+  static constexpr int SMEM_ROW = (N2 * PR) * 8 + TWR * 16;
 };
 
-template <int R>
-__device__ __forceinline__ void fwd_round(u64 *s, int logM, int logG, int P, int ls0,
-                                          const TwAcc &tw, u64 m) {
+__device__ __forceinline__ void bfly_fwd(u64 &a, u64 &b, const ulonglong2 w, u64 m, u64 m2) {
+  u64 X = a;
+  X = X >= m2 ? X - m2 : X;
+  const u64 T = shoup(b, w.x, w.y, m);
+  a = X + T;
+  b = X - T + m2;
+}
+
+__device__ __forceinline__ void bfly_inv(u64 &a, u64 &b, const ulonglong2 w, u64 m, u64 m2) {
+  const u64 X = a, Y = b;
+  u64 S = X + Y;
+  a = S >= m2 ? S - m2 : S;
+  b = shoup(X - Y + m2, w.x, w.y, m);
+}
+
+template <int LOGM, int LOGG, int P, int NT, bool ROW, bool INV, int LS0, int R>
+__device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
+  constexpr int SUB = LOGM - LS0 - R;
+  constexpr int NG = 1 << (LOGM - R + LOGG);
   const u64 m2 = 2 * m;
-  const int sub_log = logM - ls0 - R;
-  const int ngroups = 1 << (logM - R + logG);
-  const int gmask = (1 << logG) - 1;
-  for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
-    const int g = grp & gmask;
-    const int rest = grp >> logG;
-    const int lo = rest & ((1 << sub_log) - 1);
-    const int hi = rest >> sub_log;
-    const int x0 = (hi << (logM - ls0)) + lo;
+#pragma unroll
+  for (int it = 0; it < (NG + NT - 1) / NT; ++it) {
+    const int grp = threadIdx.x + it * NT;
+    if (NG % NT != 0 && grp >= NG) break;
+    const int g = grp & ((1 << LOGG) - 1);
+    const int rest = grp >> LOGG;
+    const int lo = rest & ((1 << SUB) - 1);
+    const int hi = rest >> SUB;
+    u64 *base = s + ((hi << (LOGM - LS0)) + lo) * P + g;
     u64 v[1 << R];
 #pragma unroll
-    for (int u = 0; u < (1 << R); ++u) v[u] = s[(x0 + (u << sub_log)) * P + g];
+    for (int u = 0; u < (1 << R); ++u) v[u] = base[(u << SUB) * P];
+    if (!INV) {
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int half = 1 << (R - 1 - q);
+      for (int q = 0; q < R; ++q) {
+        const int half = 1 << (R - 1 - q);
+        // twiddle index of local stage LS0+q, block (hi << q) + (u >> (R-q))
+        const ulonglong2 *twq =
+            ROW ? tw + ((((1 << (LS0 + q)) - 1 + (hi << q)) << LOGG) + g)
+                : tw + (1 << (LS0 + q)) + (hi << q);
 #pragma unroll
-      for (int u = 0; u < (1 << R); ++u) {
-        if (u & half) continue;
-        const ulonglong2 w = tw.get(ls0 + q, (hi << q) + (u >> (R - q)), g);
-        u64 X = v[u];
-        X = X >= m2 ? X - m2 : X;
-        const u64 T = shoup(v[u + half], w.x, w.y, m);
-        v[u] = X + T;
-        v[u + half] = X - T + m2;
+        for (int u = 0; u < (1 << R); ++u) {
+          if (u & half) continue;
+          const ulonglong2 w = twq[ROW ? ((u >> (R - q)) << LOGG) : (u >> (R - q))];
+          bfly_fwd(v[u], v[u + half], w, m, m2);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = R - 1; q >= 0; --q) {
+        const int half = 1 << (R - 1 - q);
+        const ulonglong2 *twq =
+            ROW ? tw + ((((1 << (LS0 + q)) - 1 + (hi << q)) << LOGG) + g)
+                : tw + (1 << (LS0 + q)) + (hi << q);
+#pragma unroll
+        for (int u = 0; u < (1 << R); ++u) {
+          if (u & half) continue;
+          const ulonglong2 w = twq[ROW ? ((u >> (R - q)) << LOGG) : (u >> (R - q))];
+          bfly_inv(v[u], v[u + half], w, m, m2);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < (1 << R); ++u) s[(x0 + (u << sub_log)) * P + g] = v[u];
+    for (int u = 0; u < (1 << R); ++u) base[(u << SUB) * P] = v[u];
   }
 }
 
-template <int R>
-__device__ __forceinline__ void inv_round(u64 *s, int logM, int logG, int P, int ls0,
-                                          const TwAcc &tw, u64 m) {
-  const u64 m2 = 2 * m;
-  const int sub_log = logM - ls0 - R;
-  const int ngroups = 1 << (logM - R + logG);
-  const int gmask = (1 << logG) - 1;
-  for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
-    const int g = grp & gmask;
-    const int rest = grp >> logG;
-    const int lo = rest & ((1 << sub_log) - 1);
-    const int hi = rest >> sub_log;
-    const int x0 = (hi << (logM - ls0)) + lo;
-    u64 v[1 << R];
-#pragma unroll
-    for (int u = 0; u < (1 << R); ++u) v[u] = s[(x0 + (u << sub_log)) * P + g];
-#pragma unroll
-    for (int q = R - 1; q >= 0; --q) {
-      const int half = 1 << (R - 1 - q);
-#pragma unroll
-      for (int u = 0; u < (1 << R); ++u) {
-        if (u & half) continue;
-        const ulonglong2 w = tw.get(ls0 + q, (hi << q) + (u >> (R - q)), g);
-        const u64 X = v[u], Y = v[u + half];
-        u64 S = X + Y;
-        S = S >= m2 ? S - m2 : S;
-        v[u] = S;
-        v[u + half] = shoup(X - Y + m2, w.x, w.y, m);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < (1 << R); ++u) s[(x0 + (u << sub_log)) * P + g] = v[u];
-  }
-}
-
-// Forward stages 0..logM-1 of every sub-transform in the tile. Inputs in
-// [0, 4m), outputs in [0, 4m). Caller syncs before; this syncs after each round.
-__device__ __forceinline__ void tile_ntt_fwd(u64 *s, int logM, int logG, int P,
-                                             const TwAcc &tw, u64 m) {
-  for (int ls0 = 0; ls0 < logM;) {
-    const int r = min(3, logM - ls0);
-    if (r == 3)
-      fwd_round<3>(s, logM, logG, P, ls0, tw, m);
-    else if (r == 2)
-      fwd_round<2>(s, logM, logG, P, ls0, tw, m);
-    else
-      fwd_round<1>(s, logM, logG, P, ls0, tw, m);
+// Forward stages 0..LOGM-1 of every sub-transform in the tile. Inputs in
+// [0, 4m), outputs in [0, 4m). Caller syncs before; each round syncs after.
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int LS0 = 0>
+__device__ __forceinline__ void tile_fwd(u64 *s, const ulonglong2 *tw, u64 m) {
+  if constexpr (LS0 < LOGM) {
+    constexpr int R = (LOGM - LS0) >= 3 ? 3 : (LOGM - LS0);
+    ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R>(s, tw, m);
     __syncthreads();
-    ls0 += r;
+    tile_fwd<LOGM, LOGG, P, NT, ROW, LS0 + R>(s, tw, m);
   }
 }
 
-// Inverse stages logM-1..0. Inputs in [0, 2m), outputs in [0, 2m).
-__device__ __forceinline__ void tile_ntt_inv(u64 *s, int logM, int logG, int P,
-                                             const TwAcc &tw, u64 m) {
-  const int nr = (logM + 2) / 3;
-  for (int k = nr - 1; k >= 0; --k) {
-    const int ls0 = 3 * k;
-    const int r = min(3, logM - ls0);
-    if (r == 3)
-      inv_round<3>(s, logM, logG, P, ls0, tw, m);
-    else if (r == 2)
-      inv_round<2>(s, logM, logG, P, ls0, tw, m);
-    else
-      inv_round<1>(s, logM, logG, P, ls0, tw, m);
+// Inverse stages LOGM-1..0. Inputs in [0, 2m), outputs in [0, 2m).
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int K = (LOGM + 2) / 3 - 1>
+__device__ __forceinline__ void tile_inv(u64 *s, const ulonglong2 *tw, u64 m) {
+  if constexpr (K >= 0 && LOGM > 0) {
+    constexpr int LS0 = 3 * K;
+    constexpr int R = (LOGM - LS0) >= 3 ? 3 : (LOGM - LS0);
+    ntt_round<LOGM, LOGG, P, NT, ROW, true, LS0, R>(s, tw, m);
     __syncthreads();
+    tile_inv<LOGM, LOGG, P, NT, ROW, K - 1>(s, tw, m);
   }
 }
 

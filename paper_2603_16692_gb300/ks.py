@@ -23,7 +23,10 @@ VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
 class KSError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} ({code})")
+        msg = f"{where}: {strerror(code)} ({code})"
+        if code in (KS_ECUDA, KS_ENOMEM):
+            msg += ": " + load().ks_cuda_error_string().decode()
+        super().__init__(msg)
 
 
 class ks_params(ctypes.Structure):
@@ -39,6 +42,11 @@ class ks_info(ctypes.Structure):
                 ("out_words", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t)]
 
 
+class ks_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("ops", ctypes.c_double)]
+
+
 class ks_job(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("d_dev", ctypes.c_void_p),
                 ("evk_dev", ctypes.c_void_p), ("out_dev", ctypes.c_void_p)]
@@ -50,7 +58,8 @@ _lock = threading.Lock()
 # exported symbols declared in include/ks.h
 SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_keygen",
            "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
-           "ks_sync_status", "ks_strerror")
+           "ks_sync_status", "ks_strerror", "ks_cuda_error_string", "ks_profile_begin",
+           "ks_profile_end")
 
 
 def lib_path() -> str:
@@ -80,8 +89,12 @@ def load(build: bool = True):
         l.ks_sync_status.argtypes = [vp, vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
+        l.ks_profile_begin.argtypes = []
+        l.ks_profile_end.argtypes = [ctypes.POINTER(ks_kernel_stat), i, ctypes.POINTER(i)]
+        l.ks_cuda_error_string.argtypes = []
+        l.ks_cuda_error_string.restype = ctypes.c_char_p
         for name in SYMBOLS:
-            if name not in ("ks_context_destroy", "ks_strerror"):
+            if name not in ("ks_context_destroy", "ks_strerror", "ks_cuda_error_string"):
                 getattr(l, name).restype = i
         _lib = l
         return l
@@ -164,6 +177,19 @@ def ks_switch_batch(jobs, flags: int = 0, stream=None):
     for k, (ctx, d, evk, out) in enumerate(jobs):
         arr[k] = ks_job(ctx, _ptr(d), _ptr(evk), _ptr(out))
     _check(load().ks_switch_batch(arr, len(jobs), flags, _stream(stream)), "ks_switch_batch")
+
+
+def ks_profile_begin():
+    _check(load().ks_profile_begin(), "ks_profile_begin")
+
+
+def ks_profile_end() -> list:
+    """[{name, launches, ms, bytes, ops}] aggregated over the profiled launches."""
+    arr = (ks_kernel_stat * 64)()
+    n = ctypes.c_int()
+    _check(load().ks_profile_end(arr, 64, ctypes.byref(n)), "ks_profile_end")
+    return [{"name": arr[k].name.decode(), "launches": arr[k].launches, "ms": arr[k].ms,
+             "bytes": arr[k].bytes, "ops": arr[k].ops} for k in range(min(n.value, 64))]
 
 
 def ks_sync_status(ctx: int, stream=None) -> int:
