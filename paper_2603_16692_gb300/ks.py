@@ -59,7 +59,7 @@ _lock = threading.Lock()
 SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_keygen",
            "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
            "ks_sync_status", "ks_strerror", "ks_cuda_error_string", "ks_profile_begin",
-           "ks_profile_end")
+           "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc")
 
 
 def lib_path() -> str:
@@ -89,12 +89,16 @@ def load(build: bool = True):
         l.ks_sync_status.argtypes = [vp, vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
+        l.ks_noalloc_scratch_bytes.argtypes = []
+        l.ks_noalloc_scratch_bytes.restype = sz
+        l.ks_switch_noalloc.argtypes = [vp, vp, vp, vp, i, i, vp]
         l.ks_profile_begin.argtypes = []
         l.ks_profile_end.argtypes = [ctypes.POINTER(ks_kernel_stat), i, ctypes.POINTER(i)]
         l.ks_cuda_error_string.argtypes = []
         l.ks_cuda_error_string.restype = ctypes.c_char_p
         for name in SYMBOLS:
-            if name not in ("ks_context_destroy", "ks_strerror", "ks_cuda_error_string"):
+            if name not in ("ks_context_destroy", "ks_strerror", "ks_cuda_error_string",
+                            "ks_noalloc_scratch_bytes"):
                 getattr(l, name).restype = i
         _lib = l
         return l
@@ -160,6 +164,26 @@ def ks_switch(ctx: int, d, evk, out, variant: int = KS_AUTO, chunks: int = 0, wo
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(load().ks_switch(ctx, _ptr(d), _ptr(evk), _ptr(out), variant, chunks,
                             _ptr(workspace), ws_bytes, _stream(stream)), "ks_switch")
+
+
+def ks_noalloc_scratch_bytes() -> int:
+    return load().ks_noalloc_scratch_bytes()
+
+
+def ks_switch_noalloc(ctx: int, d, evk, out, variant: int = KS_AUTO, chunks: int = 0,
+                      stream=None):
+    """ks_switch on the library's static scratch (no device allocation).
+
+    For callers that cannot allocate device memory while switching keys (inside
+    CUDA-graph capture, under a fixed memory budget). Raises ValueError when the
+    workload's scratch exceeds ks_noalloc_scratch_bytes()."""
+    need = ks_workspace_size(ctx, variant, chunks)
+    if need > ks_noalloc_scratch_bytes():
+        raise ValueError(f"ks_switch_noalloc: needs {need} bytes of scratch, the static scratch "
+                         f"holds {ks_noalloc_scratch_bytes()}; use an OutputChunked variant or "
+                         f"ks_switch with a workspace")
+    _check(load().ks_switch_noalloc(ctx, _ptr(d), _ptr(evk), _ptr(out), variant, chunks,
+                                    _stream(stream)), "ks_switch_noalloc")
 
 
 def ks_switch_host(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO, chunks: int = 0,
