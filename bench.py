@@ -52,12 +52,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
-    ap.add_argument("--variant", default="DPOB")
+    ap.add_argument("--variant", default="tuned",
+                    help="tuned (ks_tune picks), or DSOB/DPOB/DSOC/DPOC")
     ap.add_argument("--chunks", type=int, default=0)
     ap.add_argument("--unfused", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="bound on the oracle sample (CPU baseline)")
+    ap.add_argument("--radix4", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-job uneven batch measurement")
+    ap.add_argument("--batch-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -184,6 +189,77 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# The uneven batch: 64 KeySwitches, (dnum, N, L) drawn per job from N in 2^13..2^17,
+# L in [4, 60], dnum in [2, 10] (seed 0), run as one ks_switch_batch (CUDA graph,
+# tuned plans) against the plain form (one ks_switch per job, one fixed dataflow,
+# sequential on one stream).
+
+def batch_measure(args, ks, torch, dev, stream, hbm):
+    jobs = W.batch_jobs(0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+
+    def rand_limbs(mods, lead, n):
+        t = torch.empty((*lead, len(mods), n), dtype=torch.int64, device=dev)
+        for i, m in enumerate(mods):
+            t[..., i, :] = torch.randint(0, m, (*lead, n), generator=gen, device=dev,
+                                         dtype=torch.int64)
+        return t.view(torch.uint64)
+
+    ctxs, arg, algo = {}, [], 0
+    for cfg in jobs:
+        prm = W.make_params(*cfg)
+        if cfg not in ctxs:
+            ctxs[cfg] = ks.Context(prm)
+        d = rand_limbs(prm.q, (), prm.N)
+        evk = rand_limbs(prm.mods, (prm.beta, 2), prm.N)
+        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device=dev)
+        arg.append((ctxs[cfg].h, d, evk, out))
+        algo += prm.algo_bytes()
+    torch.cuda.synchronize(dev)
+
+    def timed(fn, reps):
+        fn()
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps  # ms per batch
+
+    plain = {}
+    for name, v, c in (("DSOB", ks.KS_DSOB, 0), ("DPOB", ks.KS_DPOB, 0),
+                       ("DPOC-c4", ks.KS_DPOC, 4), ("DSOC-c2", ks.KS_DSOC, 2)):
+        def run_plain(v=v, c=c):
+            for h, d, evk, out in arg:
+                ks.ks_switch(h, d, evk, out, v, c, None, stream)
+        plain[name] = len(jobs) / (timed(run_plain, max(2, args.batch_steps // 4)) / 1e3)
+    flags = ks.KS_BATCH_GRAPH | ks.KS_BATCH_AUTOTUNE
+    ms = timed(lambda: ks.ks_switch_batch(arg, flags, stream), args.batch_steps)
+    value = len(jobs) / (ms / 1e3)
+    best_name = max(plain, key=plain.get)
+    tuned = {}
+    for c in ctxs.values():
+        inf = ks.ks_context_info(c.h)
+        name = ks.variant_name(inf["tuned_variant"], inf["tuned_chunks"])
+        tuned[name] = tuned.get(name, 0) + 1
+    out = {"workload": "64 KeySwitches, (dnum,N,L) per job from N 2^13..2^17, L 4..60, "
+                       "dnum 2..10 (seed 0)",
+           "value": value, "unit": "KeySwitch/s", "ms_per_batch": ms,
+           "form": "one ks_switch_batch call (CUDA graph replay, per-context tuned plans, "
+                   "same-shape jobs share launches, contexts on concurrent streams)",
+           "plain_ks_per_s": plain, "plain_best_fixed": best_name,
+           "speedup_vs_best_fixed": value / plain[best_name],
+           "speedup_vs_dsob": value / plain["DSOB"],
+           "algo_bytes_per_batch": algo, "hbm_frac": algo / (ms / 1e3) / 1e9 / hbm,
+           "tuned_plans": tuned}
+    for c in ctxs.values():
+        c.close()
+    return out
+
 
 def main():
     args = parse()
@@ -211,7 +287,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    variant = ks.VARIANTS[args.variant.upper()] | (ks.KS_UNFUSED if args.unfused else 0)
     ctx = ks.Context(prm)
     dev = torch.device("cuda", local)
     s_from, s_to, a, e = W.gen_keys(prm, 0)
@@ -228,6 +303,13 @@ def main():
                                                    device=dev)) for _ in range(ring)]
     del evk0
     stream = torch.cuda.current_stream(dev)
+    if args.variant.lower() == "tuned":
+        variant, chunks = ks.ks_tune(ctx.h, sets[0][0], sets[0][1], sets[0][2], 1, stream)
+    else:
+        variant = ks.VARIANTS[args.variant.upper()] | (ks.KS_UNFUSED if args.unfused else 0) | \
+            (ks.KS_RADIX4 if args.radix4 else 0)
+        chunks = args.chunks
+    args.chunks = chunks
     ws = torch.empty(ks.ks_workspace_size(ctx.h, variant, args.chunks) // 8 + 1,
                      dtype=torch.uint64, device=dev)
 
@@ -321,8 +403,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded uniform d, ternary keys, rounded-Gaussian errors)",
-        "config": workload_config(prm, args.variant.upper(), args.chunks, args.unfused, ring,
-                                  ring * set_bytes / 1e6, l2 / 1e6),
+        "config": workload_config(prm, ks.variant_name(variant, args.chunks), args.chunks,
+                                  False, ring, ring * set_bytes / 1e6, l2 / 1e6),
         "roofline": roofline,
         "ks_hbm_roofline": {"bound": "hbm", "achieved": ks_gbs, "peak": hbm, "unit": "GB/s",
                             "frac": ks_gbs / hbm, "algo_bytes_per_ks": algo,
@@ -335,6 +417,8 @@ def main():
                 "d2h_bytes_per_step": 2 * (prm.L + 1) * prm.N * 8},
         "clocks": clocks,
     }
+    if not args.no_batch:
+        line["batch64"] = batch_measure(args, ks, torch, dev, stream, hbm)
     if world == 1 and not args.no_cpu:
         reps, el, cores = oracle_sample(prm, args.cpu_seconds, 10000)
         line["cpu_baseline"] = {"value": reps / el, "unit": UNIT, "cores": cores,

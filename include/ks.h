@@ -57,6 +57,9 @@ extern "C" {
  * separate kernels instead of fusing BConv into the first NTT pass and the
  * element-wise step into the last one (the fusion of Sec. III-B). */
 #define KS_UNFUSED 0x100
+/* OR-ed into the variant: register rounds of radix 4 (4 points per thread, twice the
+ * threads per tile) instead of radix 8; more parallelism for small workloads. */
+#define KS_RADIX4 0x200
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -74,6 +77,10 @@ typedef struct {
   size_t in_words;  /* (L+1)*N */
   size_t out_words; /* 2*(L+1)*N */
   size_t table_bytes; /* device bytes held by the context's constant tables */
+  int tuned_variant;  /* plan picked by ks_tune (0 = not tuned) */
+  int tuned_chunks;
+  int tuned_batch;    /* batch size it was tuned for */
+  float tuned_ms;     /* its time per KeySwitch in the tuning run */
 } ks_info;
 
 typedef struct ks_context ks_context;
@@ -155,11 +162,26 @@ typedef struct {
   uint64_t *out_dev;       /* [2][L+1][N] */
 } ks_job;
 
-#define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph and replay it */
-#define KS_BATCH_AUTOTUNE 0x2 /* pick per-job variants by timing (cached per shape) */
+#define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph, replay it on later
+                                 calls with the same jobs (same pointers) */
+#define KS_BATCH_AUTOTUNE 0x2 /* ks_tune each context first (once per group size) */
 
-/* Runs njobs KeySwitches on `stream`. */
+/* Runs njobs independent KeySwitches on `stream` (asynchronous). Jobs sharing a
+ * context form a group: its jobs share every kernel launch (up to 16 jobs per
+ * launch, grid z) with the context's tuned plan (KS_AUTO). Groups run concurrently on
+ * internal streams forked from and joined back to `stream`. The scratch is a
+ * library-owned arena (grown on demand, outside any capture). Calls are serialized
+ * internally; the arena is shared, so batches must not overlap on the GPU with other
+ * batches (issue them on one stream). With KS_BATCH_GRAPH the whole batch is one
+ * CUDA graph launch after the first call. */
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream);
+
+/* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
+ * {radix 8, radix 4} on this job (replicated `batch` times, 1..16, in one launch set)
+ * and stores the fastest as the context's KS_AUTO plan. Writes the switched result to
+ * out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
+int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,
+            int batch, int *variant, int *chunks, void *stream);
 
 /* Reads and clears the context's sticky device error word (bounded waits that
  * gave up). Synchronizes `stream`. Returns KS_OK or KS_ETIMEOUT. */

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "ks_internal.h"
@@ -27,6 +28,7 @@ namespace {
 struct Plan {
   int base;      // KS_DSOB..KS_DPOC
   bool unfused;
+  int rl;        // register-round radix: 3 (8 points per thread) or 2 (4 points)
   int chunks;    // phase-1 and phase-2 group counts (1 for OB)
   int clen;      // max QP-limbs per phase-1 group
   int clq;       // max Q-limbs per phase-2 group
@@ -37,9 +39,18 @@ struct Plan {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
-  int base = variant & 0xff;
-  if (variant & ~(0xff | KS_UNFUSED)) return KS_EINVAL;
-  if (base == KS_AUTO) base = KS_DPOB;
+  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4)) return KS_EINVAL;
+  if ((variant & 0xff) == KS_AUTO) {
+    // the tuned choice for single KeySwitches, else DPOB fused radix 8
+    const int tv = c->tuned_variant;
+    if (tv > 0) {
+      variant = tv | (variant & ~0xff);
+      if (chunks == 0) chunks = c->tuned_chunks;
+    } else {
+      variant = KS_DPOB | (variant & ~0xff);
+    }
+  }
+  const int base = variant & 0xff;
   if (base < KS_DSOB || base > KS_DPOC) return KS_EINVAL;
   const bool oc = base == KS_DSOC || base == KS_DPOC;
   if (oc) {
@@ -50,6 +61,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   }
   pl->base = base;
   pl->unfused = (variant & KS_UNFUSED) != 0;
+  pl->rl = (variant & KS_RADIX4) ? 2 : 3;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
   pl->clq = (c->nq + chunks - 1) / chunks;
@@ -133,95 +145,91 @@ cudaError_t timed(const char *name, double bytes, double ops, cudaStream_t s, F 
   return e;
 }
 
-int run_plan(ks_context *c, const Plan &pl, const u64 *d, const u64 *evk, u64 *out, u64 *ws,
-             cudaStream_t s) {
+int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
+  if (js.n == 0) return KS_OK;
   const size_t N = c->N;
-  const double W = (double)N * 8;                       // bytes per limb
-  const double BF_A = (double)N / 2 * c->loga;          // butterflies, column pass
-  const double BF_B = (double)N / 2 * c->logb;          // butterflies, row pass
+  const double J = js.n;                                 // jobs per launch
+  const double W = (double)N * 8 * J;                    // bytes per limb, all jobs
+  const double BF_A = (double)N / 2 * c->loga * J;       // butterflies, column pass
+  const double BF_B = (double)N / 2 * c->logb * J;       // butterflies, row pass
+  const double NJ = (double)N * J;
   const bool single = c->loga == 0;
-  const LaunchTable &L = *c->lt;
-  u64 *v = ws + pl.off_v, *tmp = ws + pl.off_tmp, *acc = ws + pl.off_acc, *vp = ws + pl.off_vp,
-      *tmp2 = ws + pl.off_tmp2;
+  const LaunchTable &L = pl.rl == 2 ? *c->lt4 : *c->lt;
+  WsOff wo;
+  wo.v = (long long)pl.off_v;
+  wo.tmp = (long long)pl.off_tmp;
+  wo.acc = (long long)pl.off_acc;
+  wo.vp = (long long)pl.off_vp;
+  wo.tmp2 = (long long)pl.off_tmp2;
   const bool dp = pl.base == KS_DPOB || pl.base == KS_DPOC;
   const bool oc = pl.base == KS_DSOC || pl.base == KS_DPOC;
-  static thread_local TaskList tl, tg;
-  static thread_local std::vector<uint32_t> big;
   auto dsize = [&](int j) { return std::min(c->nq, (j + 1) * c->alpha) - j * c->alpha; };
 
   // Input iNTT, fused with the per-limb factor N^-1 * Qhat_{j,i}^-1 of the ModUp BConv.
   {
     const double nl = c->nq;
-    KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? N : 0)), s, [&] {
-      return L.intt_row(c, d, 0, v, 0, 1, c->nq, 0, c->tab.iscale_q, s);
-    }));
+    KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), s,
+                 [&] { return L.intt_row(c, js, wo, 0, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(d)", 2 * nl * W, nl * (BF_A + N), s, [&] {
-        return L.intt_col(c, v, 0, 1, c->nq, 0, c->tab.iscale_q, s);
-      }));
+      KS_TRY(timed("intt_col(d)", 2 * nl * W, nl * (BF_A + NJ), s,
+                   [&] { return L.intt_col(c, js, wo, 0, s); }));
   }
 
   // Phase 1: ModUp (BConv + NTT) and key multiply, per output group.
   for (int ch = 0; ch < pl.chunks; ++ch) {
     const int t0 = ch * pl.clen, t1 = std::min(c->qp, t0 + pl.clen);
     if (t0 >= t1) continue;
-    tg.n = 0;
-    for (int t = t0; t < t1; ++t) tg.t[tg.n++] = pack_task(t, 0, 0);
-    SlotMap sm;
-    sm.st = 1;
-    sm.base = oc ? -t0 : 0;
-    sm.sj = dp ? (oc ? pl.clen : c->qp) : 0;
+    Tasks up = {};
+    up.mode = TASK_UP;
+    up.t0 = t0;
+    up.t1 = t1;
+    up.sm.st = 1;
+    up.sm.base = oc ? -t0 : 0;
+    up.sm.sj = dp ? (oc ? pl.clen : c->qp) : 0;
     const int jstep = dp ? c->beta : 1;
     for (int j0 = 0; j0 < c->beta; j0 += jstep) {
-      const int j1 = j0 + jstep;
-      big.clear();
-      double src_b = 0, conv_ops = 0, own = 0;
-      for (int j = j0; j < j1; ++j) {
-        const int lo = j * c->alpha, hi = lo + dsize(j);
-        src_b += dsize(j) * W;
-        for (int t = t0; t < t1; ++t) {
-          if (t >= lo && t < hi) {
-            own += 1;
-            continue;
-          }
-          big.push_back(pack_task(t, j, j * sm.sj + t * sm.st + sm.base));
-          conv_ops += (double)N * (dsize(j) + 1);
+      up.j0 = j0;
+      up.j1 = j0 + jstep;
+      up.first = j0 == 0 ? 1 : 0;
+      Tasks tg = up;
+      tg.mode = TASK_TARGET;
+      const int nconv = L.count(c, up);
+      double src_b = 0, conv_ops = 0;
+      for (int j = up.j0; j < up.j1; ++j) src_b += dsize(j) * W;
+      {
+        for (int j = up.j0; j < up.j1; ++j) {
+          Tasks one = up;
+          one.j0 = j;
+          one.j1 = j + 1;
+          conv_ops += (double)L.count(c, one) * NJ * (dsize(j) + 1);
         }
       }
-      const double nconv = (double)big.size(), nt = tg.n, nd = j1 - j0;
-      const bool first = j0 == 0;
-      for (size_t p0 = 0; p0 < big.size(); p0 += kMaxTasks) {
-        tl.n = (int)std::min<size_t>(kMaxTasks, big.size() - p0);
-        std::memcpy(tl.t, big.data() + p0, tl.n * sizeof(uint32_t));
-        const double f = (double)tl.n / std::max(1.0, nconv);
-        if (!pl.unfused) {
-          if (!single)
-            KS_TRY(timed("modup_col", tl.n * W + f * src_b, f * conv_ops + tl.n * BF_A, s,
-                         [&] { return L.modup_col(c, tl, v, tmp, s); }));
-        } else {
-          KS_TRY(timed("bconv_up", tl.n * W + f * src_b, f * conv_ops, s,
-                       [&] { return launch_bconv_up(c, tl, v, tmp, s); }));
-          if (!single)
-            KS_TRY(timed("ntt_col", 2 * tl.n * W, tl.n * BF_A, s,
-                         [&] { return L.ntt_col(c, tl, tmp, s); }));
-          KS_TRY(timed("ntt_row", 2 * tl.n * W, tl.n * BF_B, s,
-                       [&] { return L.ntt_row(c, tl, tmp, s); }));
-        }
+      const double nt = t1 - t0, nd = up.j1 - up.j0;
+      const double own = nd * nt - nconv;
+      if (!pl.unfused) {
+        if (!single)
+          KS_TRY(timed("modup_col", nconv * W + src_b, conv_ops + nconv * BF_A, s,
+                       [&] { return L.modup_col(c, js, wo, up, s); }));
+      } else {
+        KS_TRY(timed("bconv_up", nconv * W + src_b, conv_ops, s,
+                     [&] { return launch_bconv_up(c, js, wo, up, nconv, s); }));
+        if (!single)
+          KS_TRY(timed("ntt_col", 2 * nconv * W, nconv * BF_A, s,
+                       [&] { return L.ntt_col(c, js, wo, up, BUF_TMP, s); }));
+        KS_TRY(timed("ntt_row", 2 * nconv * W, nconv * BF_B, s,
+                     [&] { return L.ntt_row(c, js, wo, up, BUF_TMP, s); }));
       }
       // key multiply: evk 2 words per (digit, target); ext from tmp (or d on own limbs);
       // acc written (and read when accumulating over digit launches)
-      const double km_bytes = (2 * nd * nt + nconv + own + (first ? 2 : 4) * nt) * W;
-      const double km_ops = 2 * nd * nt * N + own * N;
+      const double km_bytes = (2 * nd * nt + nconv + own + (up.first ? 2 : 4) * nt) * W;
+      const double km_ops = 2 * nd * nt * NJ + own * NJ;
       if (!pl.unfused) {
         const double b = km_bytes + (single ? src_b - nconv * W : 0);
         const double o = km_ops + nconv * BF_B + (single ? conv_ops : 0);
-        KS_TRY(timed("modup_row_keymult", b, o, s, [&] {
-          return L.modup_row(c, tg, j0, j1, sm, first, d, v, tmp, evk, acc, s);
-        }));
+        KS_TRY(timed("modup_row_keymult", b, o, s, [&] { return L.modup_row(c, js, wo, tg, s); }));
       } else {
-        KS_TRY(timed("keymult", km_bytes, km_ops, s, [&] {
-          return launch_keymult(c, tg, j0, j1, sm, first, d, tmp, evk, acc, s);
-        }));
+        KS_TRY(timed("keymult", km_bytes, km_ops, s,
+                     [&] { return launch_keymult(c, js, wo, tg, s); }));
       }
     }
   }
@@ -229,49 +237,115 @@ int run_plan(ks_context *c, const Plan &pl, const u64 *d, const u64 *evk, u64 *o
   // iNTT of the P-limbs of both accumulators, fused with N^-1 * Phat_k^-1.
   {
     const double nl = 2.0 * c->np;
-    KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? N : 0)), s, [&] {
-      return L.intt_row(c, acc + (size_t)c->nq * N, c->qp, vp, c->np, 2, c->np, c->nq,
-                        c->tab.iscale_p, s);
-    }));
+    KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), s,
+                 [&] { return L.intt_row(c, js, wo, 1, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(accP)", 2 * nl * W, nl * (BF_A + N), s, [&] {
-        return L.intt_col(c, vp, c->np, 2, c->np, c->nq, c->tab.iscale_p, s);
-      }));
+      KS_TRY(timed("intt_col(accP)", 2 * nl * W, nl * (BF_A + NJ), s,
+                   [&] { return L.intt_col(c, js, wo, 1, s); }));
   }
 
   // Phase 2: ModDown (BConv P->Q + NTT) and (acc - .) * P^-1, per output group.
   for (int ch = 0; ch < pl.chunks; ++ch) {
     const int i0 = ch * pl.clq, i1 = std::min(c->nq, i0 + pl.clq);
     if (i0 >= i1) continue;
-    const int span = oc ? pl.clq : c->nq;
-    const int ibase = oc ? i0 : 0;
-    tl.n = 0;
-    for (int cc = 0; cc < 2; ++cc)
-      for (int i = i0; i < i1; ++i) tl.t[tl.n++] = pack_task(i, cc, cc * span + (i - ibase));
-    tg.n = 0;
-    for (int i = i0; i < i1; ++i) tg.t[tg.n++] = pack_task(i, 0, i - ibase);
-    const double n = tl.n, vp_b = 2.0 * c->np * W, conv = n * N * (c->np + 1.0);
+    Tasks dn = {};
+    dn.mode = TASK_DOWN;
+    dn.i0 = i0;
+    dn.i1 = i1;
+    dn.span = oc ? pl.clq : c->nq;
+    dn.ibase = oc ? i0 : 0;
+    Tasks d1 = dn;
+    d1.mode = TASK_DOWN1;
+    const double n = 2.0 * (i1 - i0), vp_b = 2.0 * c->np * W, conv = n * NJ * (c->np + 1.0);
     if (!pl.unfused) {
       if (!single)
         KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, s,
-                     [&] { return L.moddown_col(c, tl, vp, tmp2, s); }));
+                     [&] { return L.moddown_col(c, js, wo, dn, s); }));
       const double b = 3 * n * W + (single ? vp_b - n * W : 0);
-      const double o = n * (BF_B + N) + (single ? conv : 0);
-      KS_TRY(timed("moddown_row", b, o, s, [&] {
-        return L.moddown_row(c, tg, span, vp, tmp2, acc, out, s);
-      }));
+      const double o = n * (BF_B + NJ) + (single ? conv : 0);
+      KS_TRY(timed("moddown_row", b, o, s, [&] { return L.moddown_row(c, js, wo, d1, s); }));
     } else {
       KS_TRY(timed("bconv_down", n * W + vp_b, conv, s,
-                   [&] { return launch_bconv_down(c, tl, vp, tmp2, s); }));
+                   [&] { return launch_bconv_down(c, js, wo, dn, (int)n, s); }));
       if (!single)
         KS_TRY(timed("ntt_col", 2 * n * W, n * BF_A, s,
-                     [&] { return L.ntt_col(c, tl, tmp2, s); }));
-      KS_TRY(timed("ntt_row", 2 * n * W, n * BF_B, s, [&] { return L.ntt_row(c, tl, tmp2, s); }));
-      KS_TRY(timed("moddown_scale", 3 * n * W, n * N, s,
-                   [&] { return launch_moddown_scale(c, tl, tmp2, acc, out, s); }));
+                     [&] { return L.ntt_col(c, js, wo, dn, BUF_TMP2, s); }));
+      KS_TRY(timed("ntt_row", 2 * n * W, n * BF_B, s,
+                   [&] { return L.ntt_row(c, js, wo, dn, BUF_TMP2, s); }));
+      KS_TRY(timed("moddown_scale", 3 * n * W, n * NJ, s,
+                   [&] { return launch_moddown_scale(c, js, wo, dn, (int)n, s); }));
     }
   }
   return KS_OK;
+}
+
+// Shared state of ks_switch_batch: the batch workspace arena, fork streams,
+// dependency events and the captured graphs (keyed by the jobs' pointers).
+struct BatchState {
+  std::mutex mu;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  size_t next_event = 0;
+  std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
+  cudaStream_t stream(int g) {
+    const size_t k = (size_t)g % 16;
+    while (streams.size() <= k) {
+      cudaStream_t st = nullptr;
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      streams.push_back(st);
+    }
+    return streams[k];
+  }
+  cudaStream_t cap = nullptr;
+  cudaStream_t capture_stream() {
+    if (!cap) cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    return cap;
+  }
+  // Launch a graph after the work queued on s, and make s wait for it.
+  int launch_ordered(cudaGraphExec_t exec, cudaStream_t s) {
+    cudaStream_t c = capture_stream();
+    cudaEvent_t before = event(), after = event();
+    cudaError_t e = cudaEventRecord(before, s);
+    if (!e) e = cudaStreamWaitEvent(c, before, 0);
+    if (!e) e = cudaGraphLaunch(exec, c);
+    if (!e) e = cudaEventRecord(after, c);
+    if (!e) e = cudaStreamWaitEvent(s, after, 0);
+    return cuda_rc(e);
+  }
+  cudaEvent_t event() {
+    if (events.size() < 256) {
+      cudaEvent_t e = nullptr;
+      cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      events.push_back(e);
+      return e;
+    }
+    return events[next_event++ % events.size()];
+  }
+};
+
+BatchState g_batch;
+
+void clear_graphs_locked() {
+  for (auto &kv : g_batch.graphs) cudaGraphExecDestroy(kv.second);
+  g_batch.graphs.clear();
+}
+
+// Drop the captured graphs that use context c (before c is freed).
+void forget_graphs(ks_context *c) {
+  std::lock_guard<std::mutex> lk(g_batch.mu);
+  for (auto it = g_batch.graphs.begin(); it != g_batch.graphs.end();) {
+    bool uses = false;
+    for (size_t k = 2; k + 3 < it->first.size(); k += 4)
+      if (it->first[k] == (uintptr_t)c) uses = true;
+    if (uses) {
+      cudaGraphExecDestroy(it->second);
+      it = g_batch.graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
 }
 
 }  // namespace
@@ -333,10 +407,12 @@ int ks_context_create(const ks_params *prm, ks_context **out) {
   c->loga = ks::geo_loga(logn);
   c->logb = logn - c->loga;
   c->loggr = ks::geo_loggr(logn);
-  c->lt = ks::launch_table(logn);
-  if (!c->lt) {
+  c->lt = ks::launch_table(logn, 3);
+  c->lt4 = ks::launch_table(logn, 2);
+  if (!c->lt || !c->lt4 || c->lt->prepare() != cudaSuccess || c->lt4->prepare() != cudaSuccess) {
+    cudaGetLastError();
     delete c;
-    return KS_EINVAL;
+    return KS_ECUDA;
   }
   c->mods = mods;
   // basis-conversion sums: run * max_source * m < m 2^64
@@ -354,6 +430,7 @@ int ks_context_create(const ks_params *prm, ks_context **out) {
 
 void ks_context_destroy(ks_context *c) {
   if (!c) return;
+  forget_graphs(c);
   if (c->table_mem) cudaFree(c->table_mem);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
@@ -372,6 +449,10 @@ int ks_context_info(const ks_context *c, ks_info *info) {
   info->in_words = (size_t)c->nq * c->N;
   info->out_words = (size_t)2 * c->nq * c->N;
   info->table_bytes = c->table_bytes;
+  info->tuned_variant = c->tuned_variant;
+  info->tuned_chunks = c->tuned_chunks;
+  info->tuned_batch = c->tuned_batch;
+  info->tuned_ms = c->tuned_ms;
   return KS_OK;
 }
 
@@ -394,9 +475,15 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
   if (rc) return rc;
   const size_t need = pl.total * 8;
   cudaStream_t s = (cudaStream_t)stream;
+  JobSet js;
+  js.n = 1;
+  js.j[0].d = (const u64 *)d;
+  js.j[0].evk = (const u64 *)evk;
+  js.j[0].out = (u64 *)out;
   if (ws) {
     if (ws_bytes < need) return KS_EINVAL;
-    return run_plan(c, pl, (const u64 *)d, (const u64 *)evk, (u64 *)out, (u64 *)ws, s);
+    js.j[0].ws = (u64 *)ws;
+    return run_plan(c, pl, js, s);
   }
   std::lock_guard<std::mutex> lk(c->ws_mu);
   if (c->ws_bytes < need) {
@@ -413,7 +500,8 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
     }
     c->ws_bytes = need;
   }
-  return run_plan(c, pl, (const u64 *)d, (const u64 *)evk, (u64 *)out, (u64 *)c->ws, s);
+  js.j[0].ws = (u64 *)c->ws;
+  return run_plan(c, pl, js, s);
 }
 
 int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
@@ -463,15 +551,16 @@ int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uin
   do {
     cudaError_t err = launch_keygen_lift(c, s_from, s_to, e, polys, s);
     if (err) { rc = cuda_rc(err); break; }
-    // transform every lifted limb in place (task lists of at most kMaxTasks)
-    for (int k0 = 0; k0 < npoly * c->qp; k0 += kMaxTasks) {
-      TaskList part;
-      part.n = std::min(kMaxTasks, npoly * c->qp - k0);
-      for (int k = 0; k < part.n; ++k) part.t[k] = pack_task((k0 + k) % c->qp, 0, k0 + k);
-      err = c->lt->ntt_col(c, part, polys, s);
-      if (!err) err = c->lt->ntt_row(c, part, polys, s);
-      if (err) break;
-    }
+    // transform every lifted limb in place
+    JobSet js = {};
+    js.n = 1;
+    js.j[0].ws = polys;
+    WsOff wo = {};
+    Tasks lin = {};
+    lin.mode = TASK_LINEAR;
+    lin.n = npoly * c->qp;
+    err = c->lt->ntt_col(c, js, wo, lin, BUF_TMP, s);
+    if (!err) err = c->lt->ntt_row(c, js, wo, lin, BUF_TMP, s);
     if (err) { rc = cuda_rc(err); break; }
     err = launch_keygen_combine(c, polys, (const u64 *)a, (u64 *)evk, s);
     if (err) { rc = cuda_rc(err); break; }
@@ -484,12 +573,230 @@ int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uin
 
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
   if (njobs < 0 || (njobs > 0 && !jobs)) return KS_EINVAL;
-  (void)flags;
+  if (flags & ~(KS_BATCH_GRAPH | KS_BATCH_AUTOTUNE)) return KS_EINVAL;
+  if (njobs == 0) return KS_OK;
   for (int k = 0; k < njobs; ++k) {
-    int rc = ks_switch(jobs[k].ctx, jobs[k].d_dev, jobs[k].evk_dev, jobs[k].out_dev, KS_AUTO, 0,
-                       nullptr, 0, stream);
-    if (rc) return rc;
+    const ks_job &jb = jobs[k];
+    if (!jb.ctx || !jb.d_dev || !jb.evk_dev || !jb.out_dev) return KS_EINVAL;
+    if (!aligned16(jb.d_dev) || !aligned16(jb.evk_dev) || !aligned16(jb.out_dev))
+      return KS_EALIGN;
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  // Groups of jobs sharing a context, in order of first appearance.
+  std::vector<ks_context *> ctxs;
+  std::vector<std::vector<int>> members;
+  for (int k = 0; k < njobs; ++k) {
+    size_t g = 0;
+    while (g < ctxs.size() && ctxs[g] != jobs[k].ctx) ++g;
+    if (g == ctxs.size()) {
+      ctxs.push_back(jobs[k].ctx);
+      members.emplace_back();
+    }
+    members[g].push_back(k);
+  }
+  if (flags & KS_BATCH_AUTOTUNE) {
+    for (size_t g = 0; g < ctxs.size(); ++g) {
+      ks_context *c = ctxs[g];
+      if (c->tuned_batch == std::min<int>(kMaxBatch, (int)members[g].size()) &&
+          c->tuned_variant > 0)
+        continue;
+      const ks_job &jb = jobs[members[g][0]];
+      int v = 0, ch = 0;
+      int rc = ks_tune(c, jb.d_dev, jb.evk_dev, jb.out_dev,
+                       std::min<int>(kMaxBatch, (int)members[g].size()), &v, &ch,
+                       stream);
+      if (rc) return rc;
+    }
+  }
+  std::vector<Plan> plans(ctxs.size());
+  size_t total = 0;
+  for (size_t g = 0; g < ctxs.size(); ++g) {
+    int rc = make_plan(ctxs[g], KS_AUTO, 0, &plans[g]);
+    if (rc) return rc;
+    total += plans[g].total * 8 * members[g].size();
+  }
+  std::lock_guard<std::mutex> lk(g_batch.mu);
+  if (g_batch.arena_bytes < total) {
+    if (g_batch.arena) {
+      cudaDeviceSynchronize();
+      cudaFree(g_batch.arena);
+    }
+    clear_graphs_locked();
+    g_batch.arena = nullptr;
+    g_batch.arena_bytes = 0;
+    if (cudaMalloc(&g_batch.arena, total) != cudaSuccess) {
+      cudaGetLastError();
+      return KS_ENOMEM;
+    }
+    g_batch.arena_bytes = total;
+  }
+  std::vector<uintptr_t> key;
+  const bool graph = (flags & KS_BATCH_GRAPH) != 0;
+  if (graph) {
+    key.push_back((uintptr_t)njobs);
+    key.push_back((uintptr_t)s);
+    for (int k = 0; k < njobs; ++k) {
+      key.push_back((uintptr_t)jobs[k].ctx);
+      key.push_back((uintptr_t)jobs[k].d_dev);
+      key.push_back((uintptr_t)jobs[k].evk_dev);
+      key.push_back((uintptr_t)jobs[k].out_dev);
+    }
+    for (size_t g = 0; g < ctxs.size(); ++g) {
+      key.push_back((uintptr_t)ctxs[g]->tuned_variant);
+      key.push_back((uintptr_t)ctxs[g]->tuned_chunks);
+    }
+    auto it = g_batch.graphs.find(key);
+    if (it != g_batch.graphs.end()) return g_batch.launch_ordered(it->second, s);
+  }
+  // A graph is captured on an internal stream (the caller's may be the legacy default
+  // stream, which cannot be captured) and launched ordered after `s`.
+  const cudaStream_t caller = s;
+  if (graph) {
+    s = g_batch.capture_stream();
+    KS_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  }
+  const bool prof = g_prof.on;
+  if (graph) g_prof.on = false;
+  // Enqueue: each context group on its own stream (fork from s, join back to s);
+  // inside a group, up to kMaxBatch jobs share each launch (grid z).
+  int rc = KS_OK;
+  {
+    const int G = (int)ctxs.size();
+    cudaEvent_t fork = nullptr;
+    if (G > 1) {
+      fork = g_batch.event();
+      cudaEventRecord(fork, s);
+    }
+    char *base = (char *)g_batch.arena;
+    for (int g = 0; g < G && rc == KS_OK; ++g) {
+      cudaStream_t sg = s;
+      if (G > 1) {
+        sg = g_batch.stream(g);
+        cudaStreamWaitEvent(sg, fork, 0);
+      }
+      const Plan &pl = plans[g];
+      const std::vector<int> &mem = members[g];
+      for (size_t k0 = 0; k0 < mem.size() && rc == KS_OK; k0 += kMaxBatch) {
+        JobSet js;
+        js.n = (int)std::min<size_t>(kMaxBatch, mem.size() - k0);
+        for (int q = 0; q < js.n; ++q) {
+          const ks_job &jb = jobs[mem[k0 + q]];
+          js.j[q].d = (const u64 *)jb.d_dev;
+          js.j[q].evk = (const u64 *)jb.evk_dev;
+          js.j[q].out = (u64 *)jb.out_dev;
+          js.j[q].ws = (u64 *)base;
+          base += pl.total * 8;
+        }
+        rc = run_plan(ctxs[g], pl, js, sg);
+      }
+      if (G > 1) {
+        cudaEvent_t done = g_batch.event();
+        cudaEventRecord(done, sg);
+        cudaStreamWaitEvent(s, done, 0);
+      }
+    }
+  }
+  g_prof.on = prof;
+  if (graph) {
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &gr);
+    if (rc == KS_OK && e != cudaSuccess) rc = cuda_rc(e);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == KS_OK) {
+      e = cudaGraphInstantiate(&exec, gr, 0);
+      if (e != cudaSuccess) rc = cuda_rc(e);
+    }
+    if (gr) cudaGraphDestroy(gr);
+    if (rc != KS_OK) {
+      cudaGetLastError();
+      return rc;
+    }
+    g_batch.graphs[key] = exec;
+    return g_batch.launch_ordered(exec, caller);
+  }
+  return rc;
+}
+
+int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out, int batch,
+            int *variant, int *chunks, void *stream) {
+  if (!c || !d || !evk || !out || batch < 1 || batch > kMaxBatch) return KS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int bases[][2] = {{KS_DPOB, 0}, {KS_DSOB, 0}, {KS_DPOC, 2}, {KS_DPOC, 4}, {KS_DSOC, 2}};
+  size_t ws_max = 0;
+  for (auto &b : bases)
+    for (int r4 = 0; r4 < 2; ++r4) {
+      Plan pl;
+      if (make_plan(c, b[0] | (r4 ? KS_RADIX4 : 0), b[1], &pl) == KS_OK)
+        ws_max = std::max(ws_max, pl.total * 8);
+    }
+  const size_t out_b = (size_t)2 * c->nq * c->N * 8;
+  void *mem = nullptr;
+  if (cudaMalloc(&mem, batch * (ws_max + out_b)) != cudaSuccess) {
+    cudaGetLastError();
+    return KS_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool prof = g_prof.on;
+  g_prof.on = false;
+  float best = 1e30f;
+  int best_v = KS_DPOB, best_c = 0, rc = KS_OK;
+  for (auto &b : bases) {
+    for (int r4 = 0; r4 < 2 && rc == KS_OK; ++r4) {
+      const int v = b[0] | (r4 ? KS_RADIX4 : 0);
+      Plan pl;
+      if (make_plan(c, v, b[1], &pl) != KS_OK) continue;
+      JobSet js;
+      js.n = batch;
+      for (int q = 0; q < batch; ++q) {
+        char *base = (char *)mem + q * (ws_max + out_b);
+        js.j[q].d = (const u64 *)d;
+        js.j[q].evk = (const u64 *)evk;
+        js.j[q].out = (u64 *)(base + ws_max);
+        js.j[q].ws = (u64 *)base;
+      }
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 4 && rc == KS_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = run_plan(c, pl, js, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = KS_ECUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_min = std::min(ms_min, ms);
+      }
+      if (ms_min < best) {
+        best = ms_min;
+        best_v = v;
+        best_c = b[1];
+      }
+    }
+  }
+  g_prof.on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == KS_OK) {
+    // leave the caller's out with the switched result (every candidate computes it)
+    Plan pl;
+    make_plan(c, best_v, best_c, &pl);
+    JobSet js;
+    js.n = 1;
+    js.j[0].d = (const u64 *)d;
+    js.j[0].evk = (const u64 *)evk;
+    js.j[0].out = (u64 *)out;
+    js.j[0].ws = (u64 *)mem;
+    rc = run_plan(c, pl, js, s);
+    if (rc == KS_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = KS_ECUDA;
+  }
+  cudaFree(mem);
+  if (rc) return rc;
+  c->tuned_variant = best_v;
+  c->tuned_chunks = best_c;
+  c->tuned_batch = batch;
+  c->tuned_ms = best / batch;
+  if (variant) *variant = best_v;
+  if (chunks) *chunks = best_c;
   return KS_OK;
 }
 

@@ -5,46 +5,81 @@
 #include "ks_internal.h"
 
 namespace ks {
-const LaunchTable &launch_table_1();
-const LaunchTable &launch_table_2();
-const LaunchTable &launch_table_3();
-const LaunchTable &launch_table_4();
-const LaunchTable &launch_table_5();
-const LaunchTable &launch_table_6();
-const LaunchTable &launch_table_7();
-const LaunchTable &launch_table_8();
-const LaunchTable &launch_table_9();
-const LaunchTable &launch_table_10();
-const LaunchTable &launch_table_11();
-const LaunchTable &launch_table_12();
-const LaunchTable &launch_table_13();
-const LaunchTable &launch_table_14();
-const LaunchTable &launch_table_15();
-const LaunchTable &launch_table_16();
-const LaunchTable &launch_table_17();
+const LaunchTable &launch_table_1_3();
+const LaunchTable &launch_table_1_2();
+const LaunchTable &launch_table_2_3();
+const LaunchTable &launch_table_2_2();
+const LaunchTable &launch_table_3_3();
+const LaunchTable &launch_table_3_2();
+const LaunchTable &launch_table_4_3();
+const LaunchTable &launch_table_4_2();
+const LaunchTable &launch_table_5_3();
+const LaunchTable &launch_table_5_2();
+const LaunchTable &launch_table_6_3();
+const LaunchTable &launch_table_6_2();
+const LaunchTable &launch_table_7_3();
+const LaunchTable &launch_table_7_2();
+const LaunchTable &launch_table_8_3();
+const LaunchTable &launch_table_8_2();
+const LaunchTable &launch_table_9_3();
+const LaunchTable &launch_table_9_2();
+const LaunchTable &launch_table_10_3();
+const LaunchTable &launch_table_10_2();
+const LaunchTable &launch_table_11_3();
+const LaunchTable &launch_table_11_2();
+const LaunchTable &launch_table_12_3();
+const LaunchTable &launch_table_12_2();
+const LaunchTable &launch_table_13_3();
+const LaunchTable &launch_table_13_2();
+const LaunchTable &launch_table_14_3();
+const LaunchTable &launch_table_14_2();
+const LaunchTable &launch_table_15_3();
+const LaunchTable &launch_table_15_2();
+const LaunchTable &launch_table_16_3();
+const LaunchTable &launch_table_16_2();
+const LaunchTable &launch_table_17_3();
+const LaunchTable &launch_table_17_2();
 
-const LaunchTable *launch_table(int logn) {
-  switch (logn) {
-    case 1: return &launch_table_1();
-    case 2: return &launch_table_2();
-    case 3: return &launch_table_3();
-    case 4: return &launch_table_4();
-    case 5: return &launch_table_5();
-    case 6: return &launch_table_6();
-    case 7: return &launch_table_7();
-    case 8: return &launch_table_8();
-    case 9: return &launch_table_9();
-    case 10: return &launch_table_10();
-    case 11: return &launch_table_11();
-    case 12: return &launch_table_12();
-    case 13: return &launch_table_13();
-    case 14: return &launch_table_14();
-    case 15: return &launch_table_15();
-    case 16: return &launch_table_16();
-    case 17: return &launch_table_17();
+const LaunchTable *launch_table(int logn, int rl) {
+  switch (logn * 4 + rl) {
+    case 7: return &launch_table_1_3();
+    case 6: return &launch_table_1_2();
+    case 11: return &launch_table_2_3();
+    case 10: return &launch_table_2_2();
+    case 15: return &launch_table_3_3();
+    case 14: return &launch_table_3_2();
+    case 19: return &launch_table_4_3();
+    case 18: return &launch_table_4_2();
+    case 23: return &launch_table_5_3();
+    case 22: return &launch_table_5_2();
+    case 27: return &launch_table_6_3();
+    case 26: return &launch_table_6_2();
+    case 31: return &launch_table_7_3();
+    case 30: return &launch_table_7_2();
+    case 35: return &launch_table_8_3();
+    case 34: return &launch_table_8_2();
+    case 39: return &launch_table_9_3();
+    case 38: return &launch_table_9_2();
+    case 43: return &launch_table_10_3();
+    case 42: return &launch_table_10_2();
+    case 47: return &launch_table_11_3();
+    case 46: return &launch_table_11_2();
+    case 51: return &launch_table_12_3();
+    case 50: return &launch_table_12_2();
+    case 55: return &launch_table_13_3();
+    case 54: return &launch_table_13_2();
+    case 59: return &launch_table_14_3();
+    case 58: return &launch_table_14_2();
+    case 63: return &launch_table_15_3();
+    case 62: return &launch_table_15_2();
+    case 67: return &launch_table_16_3();
+    case 66: return &launch_table_16_2();
+    case 71: return &launch_table_17_3();
+    case 70: return &launch_table_17_2();
     default: return nullptr;
   }
 }
+
 namespace kern {
 cudaError_t smem_opt_in(const void *kernel, int bytes) {
   static std::mutex mu;

@@ -5,28 +5,14 @@
 
 #include "ks_arith.cuh"
 #include "ks_internal.h"
+#include "ks_kern.cuh"
 
 namespace ks {
 namespace {
 
-struct EArgs {
-  Tables tab;
-  int N, nq, np, qp, alpha, beta, run_up, run_down;
-};
-
-EArgs eargs(const ks_context *c) {
-  EArgs a;
-  a.tab = c->tab;
-  a.N = c->N;
-  a.nq = c->nq;
-  a.np = c->np;
-  a.qp = c->qp;
-  a.alpha = c->alpha;
-  a.beta = c->beta;
-  a.run_up = c->run_up;
-  a.run_down = c->run_down;
-  return a;
-}
+using EArgs = kern::KArgs;
+inline EArgs eargs(const ks_context *c) { return kern::make_args(c); }
+using kern::decode;
 
 // y = sum_k src_k[n] * cst[k] reduced by REDC in runs of `run` terms, canonical.
 __device__ __forceinline__ u64 bconv_point(const u64 *__restrict__ src, size_t N, size_t n,
@@ -42,10 +28,13 @@ __device__ __forceinline__ u64 bconv_point(const u64 *__restrict__ src, size_t N
   return z;
 }
 
-// ModUp BConv of digit j onto limb t (Montgomery-scaled), task (t, j, slot).
-__global__ void k_bconv_up(EArgs a, TaskList tl, const u64 *__restrict__ v, u64 *tmp) {
+// ModUp BConv of digit j onto limb t (Montgomery-scaled), TASK_UP item (t, j, slot).
+__global__ void k_bconv_up(EArgs a, JobSet js, WsOff wo, Tasks tk) {
   __shared__ u64 cst[kMaxLimbs];
-  const uint32_t w = tl.t[blockIdx.y];
+  const JobPtr jp = js.j[blockIdx.z];
+  const u64 *v = jp.ws + wo.v;
+  u64 *tmp = jp.ws + wo.tmp;
+  const uint32_t w = decode(a, tk, blockIdx.y);
   const int t = task_limb(w), j = task_dig(w);
   const int i0 = j * a.alpha, ns = min(a.nq, i0 + a.alpha) - i0;
   for (int k = threadIdx.x; k < ns; k += blockDim.x)
@@ -59,10 +48,13 @@ __global__ void k_bconv_up(EArgs a, TaskList tl, const u64 *__restrict__ v, u64 
     o[n] = bconv_point(v + (size_t)i0 * N, N, n, ns, cst, a.run_up, mi);
 }
 
-// ModDown BConv of the P-limbs of polynomial c onto q_i, task (i, c, slot).
-__global__ void k_bconv_down(EArgs a, TaskList tl, const u64 *__restrict__ vp, u64 *tmp2) {
+// ModDown BConv of the P-limbs of polynomial c onto q_i, TASK_DOWN item (i, c, slot).
+__global__ void k_bconv_down(EArgs a, JobSet js, WsOff wo, Tasks tk) {
   __shared__ u64 cst[kMaxLimbs];
-  const uint32_t w = tl.t[blockIdx.y];
+  const JobPtr jp = js.j[blockIdx.z];
+  const u64 *vp = jp.ws + wo.vp;
+  u64 *tmp2 = jp.ws + wo.tmp2;
+  const uint32_t w = decode(a, tk, blockIdx.y);
   const int i = task_limb(w), c = task_dig(w);
   for (int k = threadIdx.x; k < a.np; k += blockDim.x)
     cst[k] = a.tab.cdown[(size_t)i * a.alpha + k];
@@ -75,31 +67,32 @@ __global__ void k_bconv_down(EArgs a, TaskList tl, const u64 *__restrict__ vp, u
     o[n] = bconv_point(vp + (size_t)c * a.np * N, N, n, a.np, cst, a.run_down, mi);
 }
 
-// acc_c[t] (+)= sum_{j0 <= j < j1} ext_j[t] * evk[j][c][t], task (t).
-__global__ void k_keymult(EArgs a, TaskList tl, int j0, int j1, SlotMap smap, int first,
-                          const u64 *__restrict__ d, const u64 *__restrict__ tmp,
-                          const u64 *__restrict__ evk, u64 *acc) {
-  const int t = task_limb(tl.t[blockIdx.y]);
+// acc_c[t] (+)= sum_{j0 <= j < j1} ext_j[t] * evk[j][c][t], TASK_TARGET item t.
+__global__ void k_keymult(EArgs a, JobSet js, WsOff wo, Tasks tk) {
+  const JobPtr jp = js.j[blockIdx.z];
+  const u64 *tmp = jp.ws + wo.tmp;
+  u64 *acc = jp.ws + wo.acc;
+  const int t = task_limb(decode(a, tk, blockIdx.y));
   const ModInfo mi = a.tab.mod[t];
   const size_t N = a.N;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
        n += (size_t)gridDim.x * blockDim.x) {
     U128 s0 = {0, 0}, s1 = {0, 0};
-    for (int j = j0; j < j1; ++j) {
+    for (int j = tk.j0; j < tk.j1; ++j) {
       const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
       u64 y;
       if (t >= lo && t < hi)
-        y = csub(shoup(__ldg(d + (size_t)t * N + n), mi.r1, mi.r1s, mi.m), mi.m);
+        y = csub(shoup(__ldg(jp.d + (size_t)t * N + n), mi.r1, mi.r1s, mi.m), mi.m);
       else
-        y = __ldg(tmp + (size_t)(j * smap.sj + t * smap.st + smap.base) * N + n);
-      mac128(s0, y, __ldg(evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + n));
-      mac128(s1, y, __ldg(evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + n));
+        y = __ldg(tmp + (size_t)(j * tk.sm.sj + t * tk.sm.st + tk.sm.base) * N + n);
+      mac128(s0, y, __ldg(jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + n));
+      mac128(s1, y, __ldg(jp.evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + n));
     }
     u64 r0v = csub(redc(s0, mi.m, mi.minv), mi.m);
     u64 r1v = csub(redc(s1, mi.m, mi.minv), mi.m);
     u64 *a0 = acc + (size_t)t * N + n;
     u64 *a1 = acc + ((size_t)a.qp + t) * N + n;
-    if (!first) {
+    if (!tk.first) {
       r0v = addmod(r0v, *a0, mi.m);
       r1v = addmod(r1v, *a1, mi.m);
     }
@@ -108,17 +101,17 @@ __global__ void k_keymult(EArgs a, TaskList tl, int j0, int j1, SlotMap smap, in
   }
 }
 
-// out_c[i] = (acc_c[i] - zhat) * P^-1, task (i, c, slot of zhat).
-__global__ void k_moddown_scale(EArgs a, TaskList tl, const u64 *__restrict__ tmp2,
-                                const u64 *__restrict__ acc, u64 *out) {
-  const uint32_t w = tl.t[blockIdx.y];
+// out_c[i] = (acc_c[i] - zhat) * P^-1, TASK_DOWN item (i, c, slot of zhat).
+__global__ void k_moddown_scale(EArgs a, JobSet js, WsOff wo, Tasks tk) {
+  const JobPtr jp = js.j[blockIdx.z];
+  const uint32_t w = decode(a, tk, blockIdx.y);
   const int i = task_limb(w), c = task_dig(w);
   const u64 m = a.tab.mod[i].m;
   const ulonglong2 pv = a.tab.pinv[i];
   const size_t N = a.N;
-  const u64 *z = tmp2 + (size_t)task_slot(w) * N;
-  const u64 *ac = acc + ((size_t)c * a.qp + i) * N;
-  u64 *o = out + ((size_t)c * a.nq + i) * N;
+  const u64 *z = jp.ws + wo.tmp2 + (size_t)task_slot(w) * N;
+  const u64 *ac = jp.ws + wo.acc + ((size_t)c * a.qp + i) * N;
+  u64 *o = jp.out + ((size_t)c * a.nq + i) * N;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
        n += (size_t)gridDim.x * blockDim.x)
     o[n] = csub(shoup(__ldg(ac + n) + m - __ldg(z + n), pv.x, pv.y, m), m);
@@ -190,33 +183,32 @@ int ew_blocks(size_t N) {
 
 }  // namespace
 
-cudaError_t launch_bconv_up(const ks_context *c, const TaskList &tl, const u64 *v, u64 *tmp,
-                            cudaStream_t s) {
-  if (tl.n == 0) return cudaSuccess;
-  k_bconv_up<<<dim3(ew_blocks(c->N), tl.n), 256, 0, s>>>(eargs(c), tl, v, tmp);
+cudaError_t launch_bconv_up(const ks_context *c, const JobSet &js, const WsOff &o,
+                            const Tasks &tk, int count, cudaStream_t s) {
+  if (count == 0 || js.n == 0) return cudaSuccess;
+  k_bconv_up<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bconv_down(const ks_context *c, const TaskList &tl, const u64 *vp,
-                              u64 *tmp2, cudaStream_t s) {
-  if (tl.n == 0) return cudaSuccess;
-  k_bconv_down<<<dim3(ew_blocks(c->N), tl.n), 256, 0, s>>>(eargs(c), tl, vp, tmp2);
+cudaError_t launch_bconv_down(const ks_context *c, const JobSet &js, const WsOff &o,
+                              const Tasks &tk, int count, cudaStream_t s) {
+  if (count == 0 || js.n == 0) return cudaSuccess;
+  k_bconv_down<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
   return cudaGetLastError();
 }
 
-cudaError_t launch_keymult(const ks_context *c, const TaskList &targets, int j0, int j1,
-                           SlotMap sm, bool first, const u64 *d, const u64 *tmp,
-                           const u64 *evk, u64 *acc, cudaStream_t s) {
-  if (targets.n == 0) return cudaSuccess;
-  k_keymult<<<dim3(ew_blocks(c->N), targets.n), 256, 0, s>>>(eargs(c), targets, j0, j1, sm,
-                                                             first ? 1 : 0, d, tmp, evk, acc);
+cudaError_t launch_keymult(const ks_context *c, const JobSet &js, const WsOff &o,
+                           const Tasks &tk, cudaStream_t s) {
+  const int count = tk.t1 - tk.t0;
+  if (count <= 0 || js.n == 0) return cudaSuccess;
+  k_keymult<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
   return cudaGetLastError();
 }
 
-cudaError_t launch_moddown_scale(const ks_context *c, const TaskList &tl, const u64 *tmp2,
-                                 const u64 *acc, u64 *out, cudaStream_t s) {
-  if (tl.n == 0) return cudaSuccess;
-  k_moddown_scale<<<dim3(ew_blocks(c->N), tl.n), 256, 0, s>>>(eargs(c), tl, tmp2, acc, out);
+cudaError_t launch_moddown_scale(const ks_context *c, const JobSet &js, const WsOff &o,
+                                 const Tasks &tk, int count, cudaStream_t s) {
+  if (count == 0 || js.n == 0) return cudaSuccess;
+  k_moddown_scale<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
   return cudaGetLastError();
 }
 

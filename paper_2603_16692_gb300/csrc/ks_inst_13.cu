@@ -1,6 +1,7 @@
-// Kernel instantiations for N = 2^LOGN, LOGN in { 13 }.
+// Kernel instantiations for N = 2^LOGN, LOGN in { 13 }, radix 8 and 4.
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_13() { return kern::Launch<13>::table(); }
+const LaunchTable &launch_table_13_3() { return kern::Launch<13, 3>::table(); }
+const LaunchTable &launch_table_13_2() { return kern::Launch<13, 2>::table(); }
 }  // namespace ks

@@ -1,6 +1,7 @@
-// Kernel instantiations for N = 2^LOGN, LOGN in { 14 }.
+// Kernel instantiations for N = 2^LOGN, LOGN in { 14 }, radix 8 and 4.
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_14() { return kern::Launch<14>::table(); }
+const LaunchTable &launch_table_14_3() { return kern::Launch<14, 3>::table(); }
+const LaunchTable &launch_table_14_2() { return kern::Launch<14, 2>::table(); }
 }  // namespace ks

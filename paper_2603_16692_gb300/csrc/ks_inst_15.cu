@@ -1,6 +1,7 @@
-// Kernel instantiations for N = 2^LOGN, LOGN in { 15 }.
+// Kernel instantiations for N = 2^LOGN, LOGN in { 15 }, radix 8 and 4.
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_15() { return kern::Launch<15>::table(); }
+const LaunchTable &launch_table_15_3() { return kern::Launch<15, 3>::table(); }
+const LaunchTable &launch_table_15_2() { return kern::Launch<15, 2>::table(); }
 }  // namespace ks

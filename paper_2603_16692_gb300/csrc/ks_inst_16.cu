@@ -1,6 +1,7 @@
-// Kernel instantiations for N = 2^LOGN, LOGN in { 16 }.
+// Kernel instantiations for N = 2^LOGN, LOGN in { 16 }, radix 8 and 4.
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_16() { return kern::Launch<16>::table(); }
+const LaunchTable &launch_table_16_3() { return kern::Launch<16, 3>::table(); }
+const LaunchTable &launch_table_16_2() { return kern::Launch<16, 2>::table(); }
 }  // namespace ks

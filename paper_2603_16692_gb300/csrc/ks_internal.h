@@ -12,7 +12,6 @@ typedef unsigned long long u64;
 
 namespace ks {
 
-constexpr int kMaxTasks = 1536;  // tasks per launch (kernel parameter list)
 constexpr int kMaxLimbs = 256;   // QP limit (L+1 <= 128, alpha <= 128)
 
 // Per-modulus constants (device).
@@ -24,13 +23,9 @@ struct ModInfo {
   u64 r2;    // 2^128 mod m
 };
 
-// Work items of one launch. Each entry packs: bits 0-7 target limb, bits 8-15
-// digit (ModUp) or polynomial index c (ModDown), bits 16-31 buffer slot.
-struct TaskList {
-  int n;
-  uint32_t t[kMaxTasks];
-};
-
+// Work items of one launch, decoded from blockIdx.y (see ks_kern.cuh, decode()).
+// A decoded item packs: bits 0-7 limb, bits 8-15 digit (ModUp) or polynomial
+// index c (ModDown), bits 16-31 buffer slot.
 __host__ __device__ inline uint32_t pack_task(int limb, int dig, int slot) {
   return (uint32_t)limb | ((uint32_t)dig << 8) | ((uint32_t)slot << 16);
 }
@@ -38,8 +33,44 @@ __host__ __device__ inline int task_limb(uint32_t w) { return (int)(w & 0xff); }
 __host__ __device__ inline int task_dig(uint32_t w) { return (int)((w >> 8) & 0xff); }
 __host__ __device__ inline int task_slot(uint32_t w) { return (int)(w >> 16); }
 
-// Device-resident constant tables of one context (all pointers into one
-// allocation).
+struct SlotMap {
+  int sj, st, base;  // slot = j*sj + t*st + base
+};
+
+// Task descriptors. TASK_UP: pairs (digit j, target t) with j in [j0, j1),
+// t in [t0, t1) minus digit j's own limbs, slot by `sm`. TASK_TARGET: targets
+// t in [t0, t1). TASK_DOWN: pairs (c, i), c in {0, 1}, i in [i0, i1), slot
+// c*span + i - ibase. TASK_DOWN1: limbs i in [i0, i1) (both c in one CTA).
+// TASK_LINEAR: limbs y in [0, n), prime y % qp, slot y.
+enum { TASK_UP = 0, TASK_TARGET = 1, TASK_DOWN = 2, TASK_DOWN1 = 3, TASK_LINEAR = 4 };
+struct Tasks {
+  int mode;
+  int t0, t1, j0, j1;
+  SlotMap sm;
+  int first;  // key multiply: 1 = write acc, 0 = add into acc
+  int i0, i1, span, ibase;
+  int n;      // TASK_LINEAR count
+};
+
+// Per-job device pointers; the job is blockIdx.z.
+constexpr int kMaxBatch = 16;
+struct JobPtr {
+  const u64 *d;    // [L+1][N] input
+  const u64 *evk;  // [beta][2][QP][N]
+  u64 *out;        // [2][L+1][N]
+  u64 *ws;         // this job's workspace
+};
+struct JobSet {
+  int n;
+  JobPtr j[kMaxBatch];
+};
+// Word offsets of the workspace pieces.
+struct WsOff {
+  long long v, tmp, acc, vp, tmp2;
+};
+// Which workspace piece a plain NTT pass works on.
+enum { BUF_TMP = 0, BUF_TMP2 = 1 };
+
 struct Tables {
   ModInfo *mod;          // [QP]
   ulonglong2 *twc_f;     // [QP][N1]  column-pass forward twiddles (w, w')
@@ -63,7 +94,8 @@ struct ks_context {
   int dnum, logn, L, alpha, beta, nq, np, qp;
   int N;
   int loga, logb, loggr;  // two-pass split N = 2^loga * 2^logb; rows per row tile 2^loggr
-  const ks::LaunchTable *lt = nullptr;
+  const ks::LaunchTable *lt = nullptr;   // radix-8 kernels
+  const ks::LaunchTable *lt4 = nullptr;  // radix-4 kernels (twice the threads per tile)
   int run_up = 1, run_down = 1;  // max terms per exact 128-bit BConv sum
   std::vector<u64> mods;  // host copy, Q then P
   void *table_mem = nullptr;
@@ -74,6 +106,9 @@ struct ks_context {
   std::mutex ws_mu;
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  // timing-based choice of the dataflow (ks_tune); 0 = not tuned
+  int tuned_variant = 0, tuned_chunks = 0, tuned_batch = 0;
+  float tuned_ms = 0;
   // staging buffers for ks_switch_host
   void *stage = nullptr;
   size_t stage_bytes = 0;
@@ -85,50 +120,53 @@ namespace ks {
 int build_tables(ks_context *ctx);
 bool is_prime_u64(u64 n);
 
-struct SlotMap {
-  int sj, st, base;  // slot = j*sj + t*st + base
-};
-
-// Per-N launchers of the templated NTT kernels (ks_kern.cuh, ks_inst_*.cu).
+// Per-N launchers of the templated NTT kernels (ks_kern.cuh, ks_inst_*.cu). Every
+// launch covers the jobs of `js` (grid z) and the work items of `tk` (grid y).
 struct LaunchTable {
-  // iNTT of `outer` x `inner` limbs: src + (o*src_outer + i)*N -> dst + (o*dst_outer + i)*N,
-  // limb i modulo prime prime_base + i, scaled by scale[i] (Shoup pair). Row pass
-  // first (src -> dst), then the column pass in place on dst (none when N <= 4096).
-  cudaError_t (*intt_row)(const ks_context *, const u64 *src, int src_outer, u64 *dst,
-                          int dst_outer, int outer, int inner, int prime_base,
-                          const ulonglong2 *scale, cudaStream_t);
-  cudaError_t (*intt_col)(const ks_context *, u64 *dst, int dst_outer, int outer, int inner,
-                          int prime_base, const ulonglong2 *scale, cudaStream_t);
-  // ModUp column pass: tasks (t, j, slot): BConv of digit j onto limb t + first NTT pass.
-  cudaError_t (*modup_col)(const ks_context *, const TaskList &, const u64 *v, u64 *tmp,
+  // Opt in to the dynamic shared memory of every kernel of this N (once).
+  cudaError_t (*prepare)();
+  // Number of work items a descriptor decodes to (grid y).
+  int (*count)(const ks_context *, const Tasks &);
+  // iNTT of the L+1 input limbs (which = 0: d -> v, scaled by N^-1 Qhat^-1) or of the
+  // alpha P-limbs of both accumulators (which = 1: acc -> vp, scaled by N^-1 Phat^-1).
+  // Row pass (src -> dst), then the column pass in place (none when N <= 4096).
+  cudaError_t (*intt_row)(const ks_context *, const JobSet &, const WsOff &, int which,
+                          cudaStream_t);
+  cudaError_t (*intt_col)(const ks_context *, const JobSet &, const WsOff &, int which,
+                          cudaStream_t);
+  // ModUp column pass (TASK_UP): BConv of digit j onto limb t + first NTT pass -> tmp.
+  cudaError_t (*modup_col)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
                            cudaStream_t);
-  // ModUp row pass + key multiply: tasks (t): digits j0..j1-1 into acc.
-  cudaError_t (*modup_row)(const ks_context *, const TaskList &, int j0, int j1, SlotMap,
-                           bool first, const u64 *d, const u64 *v, const u64 *tmp,
-                           const u64 *evk, u64 *acc, cudaStream_t);
-  // ModDown column pass: tasks (i, c, slot): BConv of the P-limbs of c onto q_i + NTT pass.
-  cudaError_t (*moddown_col)(const ks_context *, const TaskList &, const u64 *vp, u64 *tmp2,
+  // ModUp row pass + key multiply (TASK_TARGET): digits j0..j1-1 into acc.
+  cudaError_t (*modup_row)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
+                           cudaStream_t);
+  // ModDown column pass (TASK_DOWN): BConv of the P-limbs of c onto q_i + NTT pass -> tmp2.
+  cudaError_t (*moddown_col)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
                              cudaStream_t);
-  // ModDown row pass + scaling: tasks (i, -, slot of c=0); c = 1 uses slot + span.
-  cudaError_t (*moddown_row)(const ks_context *, const TaskList &, int span, const u64 *vp,
-                             const u64 *tmp2, const u64 *acc, u64 *out, cudaStream_t);
-  // Plain forward NTT in place of buf[slot] for tasks (t, -, slot): column pass (none
-  // when N <= 4096), then row pass with canonical output.
-  cudaError_t (*ntt_col)(const ks_context *, const TaskList &, u64 *buf, cudaStream_t);
-  cudaError_t (*ntt_row)(const ks_context *, const TaskList &, u64 *buf, cudaStream_t);
+  // ModDown row pass + scaling (TASK_DOWN1): out = (acc - NTT(.)) * P^-1.
+  cudaError_t (*moddown_row)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
+                             cudaStream_t);
+  // Plain forward NTT, in place on workspace piece `buf` (BUF_TMP / BUF_TMP2) for the
+  // items of `tk` (TASK_UP, TASK_DOWN or TASK_LINEAR): column pass, then row pass with
+  // canonical output.
+  cudaError_t (*ntt_col)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
+                         int buf, cudaStream_t);
+  cudaError_t (*ntt_row)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
+                         int buf, cudaStream_t);
 };
-const LaunchTable *launch_table(int logn);
+// rl = log2 of the radix of the register rounds (3: 8 points per thread, 2: 4 points
+// per thread, twice the threads per tile).
+const LaunchTable *launch_table(int logn, int rl);
 
 // Element-wise kernels (ks_elem.cu): the unfused building blocks and keygen.
-cudaError_t launch_bconv_up(const ks_context *c, const TaskList &tl, const u64 *v, u64 *tmp,
-                            cudaStream_t s);
-cudaError_t launch_bconv_down(const ks_context *c, const TaskList &tl, const u64 *vp,
-                              u64 *tmp2, cudaStream_t s);
-cudaError_t launch_keymult(const ks_context *c, const TaskList &targets, int j0, int j1,
-                           SlotMap sm, bool first, const u64 *d, const u64 *tmp,
-                           const u64 *evk, u64 *acc, cudaStream_t s);
-cudaError_t launch_moddown_scale(const ks_context *c, const TaskList &tl, const u64 *tmp2,
-                                 const u64 *acc, u64 *out, cudaStream_t s);
+cudaError_t launch_bconv_up(const ks_context *c, const JobSet &js, const WsOff &o,
+                            const Tasks &tk, int count, cudaStream_t s);
+cudaError_t launch_bconv_down(const ks_context *c, const JobSet &js, const WsOff &o,
+                              const Tasks &tk, int count, cudaStream_t s);
+cudaError_t launch_keymult(const ks_context *c, const JobSet &js, const WsOff &o,
+                           const Tasks &tk, cudaStream_t s);
+cudaError_t launch_moddown_scale(const ks_context *c, const JobSet &js, const WsOff &o,
+                                 const Tasks &tk, int count, cudaStream_t s);
 cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
                                const int32_t *e, u64 *polys, cudaStream_t s);
 cudaError_t launch_keygen_combine(const ks_context *c, const u64 *polys, const u64 *a,

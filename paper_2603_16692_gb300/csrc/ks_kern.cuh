@@ -9,6 +9,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ks_arith.cuh"
 #include "ks_internal.h"
 #include "ks_ntt.cuh"
@@ -36,6 +38,52 @@ inline KArgs make_args(const ks_context *c) {
   a.run_up = c->run_up;
   a.run_down = c->run_down;
   return a;
+}
+
+// Work item y of a task descriptor (see Tasks in ks_internal.h).
+__device__ __forceinline__ uint32_t decode(const KArgs &a, const Tasks &tk, int y) {
+  if (tk.mode == TASK_UP) {
+    for (int j = tk.j0; j < tk.j1; ++j) {
+      const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
+      const int ovl = max(lo, tk.t0), ov = max(0, min(hi, tk.t1) - ovl);
+      const int cnt = (tk.t1 - tk.t0) - ov;
+      if (y < cnt) {
+        int t = tk.t0 + y;
+        if (ov > 0 && t >= ovl) t += ov;
+        return pack_task(t, j, j * tk.sm.sj + t * tk.sm.st + tk.sm.base);
+      }
+      y -= cnt;
+    }
+    return 0;
+  }
+  if (tk.mode == TASK_TARGET) return pack_task(tk.t0 + y, 0, 0);
+  if (tk.mode == TASK_DOWN) {
+    const int n = tk.i1 - tk.i0, c = y / n, i = tk.i0 + y % n;
+    return pack_task(i, c, c * tk.span + i - tk.ibase);
+  }
+  if (tk.mode == TASK_DOWN1) {
+    const int i = tk.i0 + y;
+    return pack_task(i, 0, i - tk.ibase);
+  }
+  return pack_task(y % a.qp, 0, y);
+}
+
+inline int count_tasks(const ks_context *c, const Tasks &tk) {
+  switch (tk.mode) {
+    case TASK_UP: {
+      int n = 0;
+      for (int j = tk.j0; j < tk.j1; ++j) {
+        const int lo = j * c->alpha, hi = std::min(lo + c->alpha, c->nq);
+        const int ov = std::max(0, std::min(hi, tk.t1) - std::max(lo, tk.t0));
+        n += (tk.t1 - tk.t0) - ov;
+      }
+      return n;
+    }
+    case TASK_TARGET: return tk.t1 - tk.t0;
+    case TASK_DOWN: return 2 * (tk.i1 - tk.i0);
+    case TASK_DOWN1: return tk.i1 - tk.i0;
+    default: return tk.n;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -237,28 +285,61 @@ __device__ __forceinline__ u64 *tile_ptr(unsigned char *raw) {
 }
 
 // ---------------------------------------------------------------------------
-// Inverse NTT, row pass (global stages logN-1 .. logN1), for `outer` polynomials
-// of the same limb (src + (o*src_outer + ii)*N). grid (N1/GR, inner). With a
-// single pass (N1 == 1) it also applies the per-limb scale (canonical output).
-template <int LOGN>
-__global__ void __launch_bounds__(GeoT<LOGN>::NT)
-    k_inv_row(KArgs a, const u64 *src, int src_outer, u64 *dst, int dst_outer, int outer,
-              int prime_base, const ulonglong2 *__restrict__ scale) {
-  using GT = GeoT<LOGN>;
+// Kernels. grid (tiles, work items, jobs); the job's pointers are js.j[blockIdx.z].
+
+// iNTT limb set `which`: 0 = the L+1 input limbs (d -> v), 1 = the P-limbs of both
+// accumulators (acc -> vp). Returns (src, src_outer, dst, dst_outer, outer, prime_base,
+// scale) for the current job.
+struct InttSet {
+  const u64 *src;
+  u64 *dst;
+  int src_outer, dst_outer, outer, prime_base;
+  const ulonglong2 *scale;
+};
+__device__ __forceinline__ InttSet intt_set(const KArgs &a, const JobPtr &jp, const WsOff &o,
+                                            int which) {
+  InttSet r;
+  if (which == 0) {
+    r.src = jp.d;
+    r.dst = jp.ws + o.v;
+    r.src_outer = r.dst_outer = 0;
+    r.outer = 1;
+    r.prime_base = 0;
+    r.scale = a.tab.iscale_q;
+  } else {
+    r.src = jp.ws + o.acc + (size_t)a.nq * a.N;
+    r.dst = jp.ws + o.vp;
+    r.src_outer = a.qp;
+    r.dst_outer = a.np;
+    r.outer = 2;
+    r.prime_base = a.nq;
+    r.scale = a.tab.iscale_p;
+  }
+  return r;
+}
+
+// Inverse NTT, row pass (global stages logN-1 .. logN1), all `outer` polynomials of
+// limb blockIdx.y in one CTA (shared twiddles). With a single pass (N1 == 1) it also
+// applies the per-limb scale (canonical output).
+template <int LOGN, int RL>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_inv_row(KArgs a, JobSet js, WsOff wo, int which) {
+  using GT = GeoT<LOGN, RL>;
   extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const int ii = blockIdx.y, prime = prime_base + ii, blk = blockIdx.x;
+  const InttSet is = intt_set(a, js.j[blockIdx.z], wo, which);
+  const int ii = blockIdx.y, prime = is.prime_base + ii, blk = blockIdx.x;
   const int r0 = blk * GT::GR;
   const u64 m = a.tab.mod[prime].m;
   const size_t N = a.N;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_i, prime, blk), GT::TWR);
-  const ulonglong2 sc = scale[ii];
-  for (int o = 0; o < outer; ++o) {
-    load_rows<GT>(sm, src + ((size_t)o * src_outer + ii) * N, r0);
+  const ulonglong2 sc = is.scale[ii];
+  for (int o = 0; o < is.outer; ++o) {
+    load_rows<GT>(sm, is.src + ((size_t)o * is.src_outer + ii) * N, r0);
     __syncthreads();
-    tile_inv<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true>(sm, tws, m);
-    u64 *d = dst + ((size_t)o * dst_outer + ii) * N;
+    tile_inv<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
+    u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * N;
     if (GT::LOGA == 0) {
 #pragma unroll
       for (int k = 0; k < GT::EPT; ++k) {
@@ -274,25 +355,25 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT)
 }
 
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
-// per-limb scale. grid (N2/GC, inner).
-template <int LOGN>
-__global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 2)
-    k_inv_col(KArgs a, u64 *dst, int dst_outer, int outer, int prime_base,
-              const ulonglong2 *__restrict__ scale) {
-  using GT = GeoT<LOGN>;
+// per-limb scale.
+template <int LOGN, int RL>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (1024 / GeoT<LOGN, RL>::NT) > 0 ? 1024 / GeoT<LOGN, RL>::NT : 1)
+    k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
+  using GT = GeoT<LOGN, RL>;
   extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
-  const int ii = blockIdx.y, prime = prime_base + ii;
+  const InttSet is = intt_set(a, js.j[blockIdx.z], wo, which);
+  const int ii = blockIdx.y, prime = is.prime_base + ii;
   const int c0 = blockIdx.x * GT::GC;
   const u64 m = a.tab.mod[prime].m;
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_i, prime), GT::TWC);
-  const ulonglong2 sc = scale[ii];
-  for (int o = 0; o < outer; ++o) {
-    u64 *d = dst + ((size_t)o * dst_outer + ii) * (size_t)a.N;
+  const ulonglong2 sc = is.scale[ii];
+  for (int o = 0; o < is.outer; ++o) {
+    u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * (size_t)a.N;
     load_cols<GT>(sm, d, c0);
     __syncthreads();
-    tile_inv<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false>(sm, tws, m);
+    tile_inv<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false, RL>(sm, tws, m);
     constexpr int TILE = GT::N1 * GT::GC;
 #pragma unroll
     for (int k = 0; k < (TILE + GT::NT - 1) / GT::NT; ++k) {
@@ -307,63 +388,87 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 2)
   }
 }
 
-// Forward NTT, column pass (global stages 0 .. logN1-1) with a tile producer;
-// the lazy ([0, 4m)) result goes to buf[slot]. grid (N2/GC, tasks).
-template <int LOGN, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN>::NT)
-    k_fwd_col(KArgs a, TaskList tl, const u64 *__restrict__ v, u64 *buf) {
-  using GT = GeoT<LOGN>;
+// Buffers of a forward pass for job jp: the BConv sources and the output buffer.
+template <int PRO>
+__device__ __forceinline__ void fwd_bufs(const JobPtr &jp, const WsOff &wo, int buf,
+                                         const u64 *&src, u64 *&dst) {
+  if (PRO == PRO_UP) {
+    src = jp.ws + wo.v;
+    dst = jp.ws + wo.tmp;
+  } else if (PRO == PRO_DOWN) {
+    src = jp.ws + wo.vp;
+    dst = jp.ws + wo.tmp2;
+  } else {
+    src = nullptr;
+    dst = jp.ws + (buf == BUF_TMP ? wo.tmp : wo.tmp2);
+  }
+}
+
+// Forward NTT, column pass (global stages 0 .. logN1-1) with a tile producer; the
+// lazy ([0, 4m)) result goes to the output buffer's slot.
+template <int LOGN, int RL, int PRO>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_fwd_col(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
+  using GT = GeoT<LOGN, RL>;
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
-  const uint32_t w = tl.t[blockIdx.y];
+  const u64 *src;
+  u64 *dst;
+  fwd_bufs<PRO>(js.j[blockIdx.z], wo, buf, src, dst);
+  const uint32_t w = decode(a, tk, blockIdx.y);
   const int t = task_limb(w);
   const int c0 = blockIdx.x * GT::GC;
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_f, t), GT::TWC);
-  produce<GT, PRO, true>(a, sm, cst, w, v, buf, c0);
+  produce<GT, PRO, true>(a, sm, cst, w, src, dst, c0);
   __syncthreads();
-  tile_fwd<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false>(sm, tws, a.tab.mod[t].m);
-  store_cols<GT>(buf + (size_t)task_slot(w) * a.N, sm, c0);
+  tile_fwd<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false, RL>(sm, tws, a.tab.mod[t].m);
+  store_cols<GT>(dst + (size_t)task_slot(w) * a.N, sm, c0);
 }
 
-// Plain forward row pass: canonical result back to buf[slot]. grid (N1/GR, tasks).
-template <int LOGN>
-__global__ void __launch_bounds__(GeoT<LOGN>::NT) k_fwd_row_store(KArgs a, TaskList tl, u64 *buf) {
-  using GT = GeoT<LOGN>;
+// Plain forward row pass: canonical result back in place.
+template <int LOGN, int RL>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_fwd_row_store(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
+  using GT = GeoT<LOGN, RL>;
   extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const uint32_t w = tl.t[blockIdx.y];
+  const u64 *src;
+  u64 *dst;
+  fwd_bufs<PRO_LOAD>(js.j[blockIdx.z], wo, buf, src, dst);
+  const uint32_t w = decode(a, tk, blockIdx.y);
   const int t = task_limb(w), blk = blockIdx.x, r0 = blk * GT::GR;
   const u64 m = a.tab.mod[t].m;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
-  u64 *b = buf + (size_t)task_slot(w) * a.N;
+  u64 *b = dst + (size_t)task_slot(w) * a.N;
   load_rows<GT>(sm, b, r0);
   __syncthreads();
-  tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true>(sm, tws, m);
+  tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
   store_rows<GT>(b, sm, r0, m, 1);
 }
 
 // ModUp row pass fused with the key multiply. One CTA = one row tile of one
-// target limb t, over digits j0..j1-1:
+// target limb t (TASK_TARGET), over digits j0..j1-1:
 //   acc_c[t] (+)= sum_j ext_j[t] * evk[j][c][t],  c = 0, 1,
 // with ext_j[t] = NTT(BConv_j)[t] (Montgomery-scaled) or, on digit j's own limbs,
 // the input d_t (put in Montgomery form here), so that REDC of each exact
 // 128-bit product is the plain product mod m. The row twiddles of (t, tile) are
 // staged once.
-template <int LOGN, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 8 * 3)
-    k_fwd_row_keymult(KArgs a, TaskList tl, int j0, int j1, SlotMap smap, int first,
-                      const u64 *__restrict__ d, const u64 *__restrict__ v,
-                      const u64 *__restrict__ tmp, const u64 *__restrict__ evk, u64 *acc) {
-  using GT = GeoT<LOGN>;
+template <int LOGN, int RL, int PRO>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (768 / GeoT<LOGN, RL>::NT) > 0 ? 768 / GeoT<LOGN, RL>::NT : 1)
+    k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
+  using GT = GeoT<LOGN, RL>;
   constexpr int EPT = GT::EPT;
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const int t = task_limb(tl.t[blockIdx.y]);
+  const JobPtr jp = js.j[blockIdx.z];
+  const u64 *v = jp.ws + wo.v, *tmp = jp.ws + wo.tmp;
+  u64 *acc = jp.ws + wo.acc;
+  const int t = task_limb(decode(a, tk, blockIdx.y));
   const ModInfo mi = a.tab.mod[t];
   const int blk = blockIdx.x, r0 = blk * GT::GR;
   const size_t N = a.N;
@@ -374,13 +479,13 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 8 * 3)
   const u64 m2 = 2 * mi.m;
 #pragma unroll
   for (int k = 0; k < EPT; ++k) s0[k] = s1[k] = 0;
-  for (int j = j0; j < j1; ++j) {
+  for (int j = tk.j0; j < tk.j1; ++j) {
     const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
     const bool own = t >= lo && t < hi;
-    const u64 *e0 = evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + off0;
-    const u64 *e1 = evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + off0;
+    const u64 *e0 = jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + off0;
+    const u64 *e1 = jp.evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + off0;
     if (own) {
-      const u64 *dt = d + (size_t)t * N + off0;
+      const u64 *dt = jp.d + (size_t)t * N + off0;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = threadIdx.x + k * GT::NT;
@@ -395,13 +500,13 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 8 * 3)
         }
       }
     } else {
-      const int slot = j * smap.sj + t * smap.st + smap.base;
+      const int slot = j * tk.sm.sj + t * tk.sm.st + tk.sm.base;
       if (GT::LOGA == 0)
         produce<GT, PRO, false>(a, sm, cst, pack_task(t, j, slot), v, tmp, r0);
       else
         produce<GT, PRO_LOAD, false>(a, sm, cst, pack_task(t, j, slot), v, tmp, r0);
       __syncthreads();
-      tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true>(sm, tws, mi.m);
+      tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, mi.m);
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = threadIdx.x + k * GT::NT;
@@ -427,7 +532,7 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 8 * 3)
     if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
     u64 r0v = csub(s0[k], mi.m);
     u64 r1v = csub(s1[k], mi.m);
-    if (!first) {
+    if (!tk.first) {
       r0v = addmod(r0v, a0[e], mi.m);
       r1v = addmod(r1v, a1[e], mi.m);
     }
@@ -437,19 +542,19 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT, 2048 / GeoT<LOGN>::NT / 8 * 3)
 }
 
 // ModDown row pass fused with the final scaling, both polynomials c = 0, 1 of
-// limb i in one CTA (shared twiddles):
+// limb i (TASK_DOWN1) in one CTA (shared twiddles):
 //   out_c[i] = (acc_c[i] - NTT(BConv_{P->Q}(c))[i]) * P^-1 mod q_i.
-// Task = (i, slot of c = 0); polynomial c uses slot + c*span.
-template <int LOGN, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN>::NT)
-    k_fwd_row_moddown(KArgs a, TaskList tl, int span, const u64 *__restrict__ vp,
-                      const u64 *__restrict__ tmp2, const u64 *__restrict__ acc, u64 *out) {
-  using GT = GeoT<LOGN>;
+template <int LOGN, int RL, int PRO>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
+  using GT = GeoT<LOGN, RL>;
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const uint32_t w = tl.t[blockIdx.y];
+  const JobPtr jp = js.j[blockIdx.z];
+  const u64 *vp = jp.ws + wo.vp, *tmp2 = jp.ws + wo.tmp2, *acc = jp.ws + wo.acc;
+  const uint32_t w = decode(a, tk, blockIdx.y);
   const int i = task_limb(w), blk = blockIdx.x, r0 = blk * GT::GR;
   const u64 m = a.tab.mod[i].m;
   const ulonglong2 pv = a.tab.pinv[i];
@@ -457,15 +562,15 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT)
   const size_t off0 = (size_t)r0 << GT::LOGB;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
   for (int c = 0; c < 2; ++c) {
-    const uint32_t wc = pack_task(i, c, task_slot(w) + c * span);
+    const uint32_t wc = pack_task(i, c, task_slot(w) + c * tk.span);
     if (GT::LOGA == 0)
       produce<GT, PRO, false>(a, sm, cst, wc, vp, tmp2, r0);
     else
       produce<GT, PRO_LOAD, false>(a, sm, cst, wc, vp, tmp2, r0);
     __syncthreads();
-    tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true>(sm, tws, m);
+    tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
     const u64 *ac = acc + ((size_t)c * a.qp + i) * N + off0;
-    u64 *o = out + ((size_t)c * a.nq + i) * N + off0;
+    u64 *o = jp.out + ((size_t)c * a.nq + i) * N + off0;
 #pragma unroll
     for (int k = 0; k < GT::EPT; ++k) {
       const int e = threadIdx.x + k * GT::NT;
@@ -479,11 +584,8 @@ __global__ void __launch_bounds__(GeoT<LOGN>::NT)
 }
 
 // ---------------------------------------------------------------------------
-// Launchers for one N.
+// Launchers for one N and radix.
 
-// Opt in to the kernel's dynamic shared memory (static shared memory such as the
-// BConv constants comes on top of it) and to the largest shared-memory carveout,
-// once per kernel.
 cudaError_t smem_opt_in(const void *kernel, int bytes);
 
 template <class K>
@@ -491,109 +593,106 @@ inline cudaError_t smem_attr(K kernel, int bytes) {
   return smem_opt_in(reinterpret_cast<const void *>(kernel), bytes);
 }
 
-template <class F>
-inline cudaError_t for_each_part(const TaskList &tl, F f) {
-  if (tl.n <= 0) return cudaSuccess;
-  if (tl.n <= kMaxTasks) {
-    f(tl);
-    return cudaGetLastError();
-  }
-  return cudaErrorInvalidValue;
-}
+inline KArgs args_of(const ks_context *c) { return make_args(c); }
 
-template <int LOGN>
+template <int LOGN, int RL>
 struct Launch {
-  using GT = GeoT<LOGN>;
+  using GT = GeoT<LOGN, RL>;
   static constexpr int GRID_COL = GT::LOGA == 0 ? 1 : GT::N2 / GT::GC;
   static constexpr int GRID_ROW = GT::N1 / GT::GR;
+  static constexpr int PRO_ROW_UP = GT::LOGA == 0 ? PRO_UP : PRO_LOAD;
+  static constexpr int PRO_ROW_DOWN = GT::LOGA == 0 ? PRO_DOWN : PRO_LOAD;
 
-  static cudaError_t intt_row(const ks_context *c, const u64 *src, int src_outer, u64 *dst,
-                              int dst_outer, int outer, int inner, int prime_base,
-                              const ulonglong2 *scale, cudaStream_t s) {
-    if (outer * inner == 0) return cudaSuccess;
-    const KArgs a = make_args(c);
-    cudaError_t e = smem_attr(k_inv_row<LOGN>, GT::SMEM_ROW);
-    if (e) return e;
-    k_inv_row<LOGN><<<dim3(GRID_ROW, inner), GT::NT, GT::SMEM_ROW, s>>>(
-        a, src, src_outer, dst, dst_outer, outer, prime_base, scale);
+  static cudaError_t prepare() {
+    cudaError_t e;
+    if ((e = smem_attr(k_inv_row<LOGN, RL>, GT::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_store<LOGN, RL>, GT::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, GT::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, GT::SMEM_ROW))) return e;
+    if (GT::LOGA > 0) {
+      if ((e = smem_attr(k_inv_col<LOGN, RL>, GT::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_LOAD>, GT::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_UP>, GT::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_DOWN>, GT::SMEM_COL))) return e;
+    }
+    return cudaSuccess;
+  }
+
+  static int count(const ks_context *c, const Tasks &tk) { return count_tasks(c, tk); }
+
+  static cudaError_t intt_row(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
+                              cudaStream_t s) {
+    const int inner = which == 0 ? c->nq : c->np;
+    if (inner == 0 || js.n == 0) return cudaSuccess;
+    k_inv_row<LOGN, RL><<<dim3(GRID_ROW, inner, js.n), GT::NT, GT::SMEM_ROW, s>>>(
+        args_of(c), js, wo, which);
     return cudaGetLastError();
   }
 
-  static cudaError_t intt_col(const ks_context *c, u64 *dst, int dst_outer, int outer, int inner,
-                              int prime_base, const ulonglong2 *scale, cudaStream_t s) {
-    if (GT::LOGA == 0 || outer * inner == 0) return cudaSuccess;
-    const KArgs a = make_args(c);
-    cudaError_t e = smem_attr(k_inv_col<LOGN>, GT::SMEM_COL);
-    if (e) return e;
-    k_inv_col<LOGN><<<dim3(GRID_COL, inner), GT::NT, GT::SMEM_COL, s>>>(a, dst, dst_outer, outer,
-                                                                          prime_base, scale);
+  static cudaError_t intt_col(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
+                              cudaStream_t s) {
+    const int inner = which == 0 ? c->nq : c->np;
+    if (GT::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
+    k_inv_col<LOGN, RL><<<dim3(GRID_COL, inner, js.n), GT::NT, GT::SMEM_COL, s>>>(
+        args_of(c), js, wo, which);
     return cudaGetLastError();
   }
 
   template <int PRO>
-  static cudaError_t col(const ks_context *c, const TaskList &tl, const u64 *v, u64 *buf,
-                         cudaStream_t s) {
-    if (GT::LOGA == 0) return cudaSuccess;
-    const KArgs a = make_args(c);
-    cudaError_t e = smem_attr(k_fwd_col<LOGN, PRO>, GT::SMEM_COL);
-    if (e) return e;
-    return for_each_part(tl, [&](const TaskList &p) {
-      k_fwd_col<LOGN, PRO><<<dim3(GRID_COL, p.n), GT::NT, GT::SMEM_COL, s>>>(a, p, v, buf);
-    });
-  }
-
-  static cudaError_t modup_col(const ks_context *c, const TaskList &tl, const u64 *v, u64 *tmp,
-                               cudaStream_t s) {
-    return col<PRO_UP>(c, tl, v, tmp, s);
-  }
-
-  static cudaError_t moddown_col(const ks_context *c, const TaskList &tl, const u64 *vp,
-                                 u64 *tmp2, cudaStream_t s) {
-    return col<PRO_DOWN>(c, tl, vp, tmp2, s);
-  }
-
-  static cudaError_t modup_row(const ks_context *c, const TaskList &tl, int j0, int j1,
-                               SlotMap sm, bool first, const u64 *d, const u64 *v,
-                               const u64 *tmp, const u64 *evk, u64 *acc, cudaStream_t s) {
-    if (tl.n == 0) return cudaSuccess;
-    const KArgs a = make_args(c);
-    constexpr int PRO = GT::LOGA == 0 ? PRO_UP : PRO_LOAD;
-    cudaError_t e = smem_attr(k_fwd_row_keymult<LOGN, PRO>, GT::SMEM_ROW);
-    if (e) return e;
-    k_fwd_row_keymult<LOGN, PRO><<<dim3(GRID_ROW, tl.n), GT::NT, GT::SMEM_ROW, s>>>(
-        a, tl, j0, j1, sm, first ? 1 : 0, d, v, tmp, evk, acc);
+  static cudaError_t col(const ks_context *c, const JobSet &js, const WsOff &wo,
+                         const Tasks &tk, int buf, cudaStream_t s) {
+    const int n = count_tasks(c, tk);
+    if (GT::LOGA == 0 || n == 0 || js.n == 0) return cudaSuccess;
+    k_fwd_col<LOGN, RL, PRO><<<dim3(GRID_COL, n, js.n), GT::NT, GT::SMEM_COL, s>>>(
+        args_of(c), js, wo, tk, buf);
     return cudaGetLastError();
   }
 
-  static cudaError_t moddown_row(const ks_context *c, const TaskList &tl, int span,
-                                 const u64 *vp, const u64 *tmp2, const u64 *acc, u64 *out,
-                                 cudaStream_t s) {
-    const KArgs a = make_args(c);
-    constexpr int PRO = GT::LOGA == 0 ? PRO_DOWN : PRO_LOAD;
-    cudaError_t e = smem_attr(k_fwd_row_moddown<LOGN, PRO>, GT::SMEM_ROW);
-    if (e) return e;
-    return for_each_part(tl, [&](const TaskList &p) {
-      k_fwd_row_moddown<LOGN, PRO><<<dim3(GRID_ROW, p.n), GT::NT, GT::SMEM_ROW, s>>>(
-          a, p, span, vp, tmp2, acc, out);
-    });
+  static cudaError_t modup_col(const ks_context *c, const JobSet &js, const WsOff &wo,
+                               const Tasks &tk, cudaStream_t s) {
+    return col<PRO_UP>(c, js, wo, tk, BUF_TMP, s);
   }
 
-  static cudaError_t ntt_col(const ks_context *c, const TaskList &tl, u64 *buf, cudaStream_t s) {
-    return col<PRO_LOAD>(c, tl, nullptr, buf, s);
+  static cudaError_t moddown_col(const ks_context *c, const JobSet &js, const WsOff &wo,
+                                 const Tasks &tk, cudaStream_t s) {
+    return col<PRO_DOWN>(c, js, wo, tk, BUF_TMP2, s);
   }
 
-  static cudaError_t ntt_row(const ks_context *c, const TaskList &tl, u64 *buf, cudaStream_t s) {
-    const KArgs a = make_args(c);
-    cudaError_t e = smem_attr(k_fwd_row_store<LOGN>, GT::SMEM_ROW);
-    if (e) return e;
-    return for_each_part(tl, [&](const TaskList &p) {
-      k_fwd_row_store<LOGN><<<dim3(GRID_ROW, p.n), GT::NT, GT::SMEM_ROW, s>>>(a, p, buf);
-    });
+  static cudaError_t modup_row(const ks_context *c, const JobSet &js, const WsOff &wo,
+                               const Tasks &tk, cudaStream_t s) {
+    const int n = count_tasks(c, tk);
+    if (n == 0 || js.n == 0) return cudaSuccess;
+    k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW, s>>>(
+        args_of(c), js, wo, tk);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t moddown_row(const ks_context *c, const JobSet &js, const WsOff &wo,
+                                 const Tasks &tk, cudaStream_t s) {
+    const int n = count_tasks(c, tk);
+    if (n == 0 || js.n == 0) return cudaSuccess;
+    k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW,
+                                                s>>>(args_of(c), js, wo, tk);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t ntt_col(const ks_context *c, const JobSet &js, const WsOff &wo,
+                             const Tasks &tk, int buf, cudaStream_t s) {
+    return col<PRO_LOAD>(c, js, wo, tk, buf, s);
+  }
+
+  static cudaError_t ntt_row(const ks_context *c, const JobSet &js, const WsOff &wo,
+                             const Tasks &tk, int buf, cudaStream_t s) {
+    const int n = count_tasks(c, tk);
+    if (n == 0 || js.n == 0) return cudaSuccess;
+    k_fwd_row_store<LOGN, RL><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW, s>>>(
+        args_of(c), js, wo, tk, buf);
+    return cudaGetLastError();
   }
 
   static const LaunchTable &table() {
-    static const LaunchTable t = {&intt_row, &intt_col,    &modup_col, &modup_row,
-                                  &moddown_col, &moddown_row, &ntt_col,  &ntt_row};
+    static const LaunchTable t = {&prepare, &count,       &intt_row,    &intt_col, &modup_col,
+                                  &modup_row, &moddown_col, &moddown_row, &ntt_col,  &ntt_row};
     return t;
   }
 };

@@ -34,15 +34,17 @@ __host__ __device__ constexpr int geo_loggr(int logn) {
   return geo_tile_log(logn) - (logn - geo_loga(logn));
 }
 
-template <int LOGN>
+// RL: log2 of the radix of the register rounds; a thread holds 2^RL points.
+template <int LOGN, int RL_ = 3>
 struct GeoT {
+  static constexpr int RL = RL_;
   static constexpr int LOGA = geo_loga(LOGN);  // log N1
   static constexpr int LOGB = LOGN - LOGA;     // log N2
   static constexpr int TILE_LOG = geo_tile_log(LOGN);
   static constexpr int LOGGC = LOGA == 0 ? 0 : TILE_LOG - LOGA;  // columns per column tile
   static constexpr int LOGGR = TILE_LOG - LOGB;                  // rows per row tile
   static constexpr int TILE = 1 << TILE_LOG;
-  static constexpr int NT = TILE / 8 < 32 ? 32 : TILE / 8;  // threads: one radix-8 group each
+  static constexpr int NT = (TILE >> RL) < 32 ? 32 : (TILE >> RL);  // one group per thread
   static constexpr int EPT = (TILE + NT - 1) / NT;           // tile elements per thread
   static constexpr int GC = 1 << LOGGC, GR = 1 << LOGGR;
   static constexpr int PC = GC == 1 ? 1 : GC + 1;
@@ -121,27 +123,29 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
   }
 }
 
-// Forward stages 0..LOGM-1 of every sub-transform in the tile. Inputs in
-// [0, 4m), outputs in [0, 4m). Caller syncs before; each round syncs after.
-template <int LOGM, int LOGG, int P, int NT, bool ROW, int LS0 = 0>
+// Forward stages 0..LOGM-1 of every sub-transform in the tile, in rounds of at
+// most RM stages. Inputs in [0, 4m), outputs in [0, 4m). Caller syncs before;
+// each round syncs after.
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3, int LS0 = 0>
 __device__ __forceinline__ void tile_fwd(u64 *s, const ulonglong2 *tw, u64 m) {
   if constexpr (LS0 < LOGM) {
-    constexpr int R = (LOGM - LS0) >= 3 ? 3 : (LOGM - LS0);
+    constexpr int R = (LOGM - LS0) >= RM ? RM : (LOGM - LS0);
     ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R>(s, tw, m);
     __syncthreads();
-    tile_fwd<LOGM, LOGG, P, NT, ROW, LS0 + R>(s, tw, m);
+    tile_fwd<LOGM, LOGG, P, NT, ROW, RM, LS0 + R>(s, tw, m);
   }
 }
 
 // Inverse stages LOGM-1..0. Inputs in [0, 2m), outputs in [0, 2m).
-template <int LOGM, int LOGG, int P, int NT, bool ROW, int K = (LOGM + 2) / 3 - 1>
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3,
+          int K = (LOGM + RM - 1) / RM - 1>
 __device__ __forceinline__ void tile_inv(u64 *s, const ulonglong2 *tw, u64 m) {
   if constexpr (K >= 0 && LOGM > 0) {
-    constexpr int LS0 = 3 * K;
-    constexpr int R = (LOGM - LS0) >= 3 ? 3 : (LOGM - LS0);
+    constexpr int LS0 = RM * K;
+    constexpr int R = (LOGM - LS0) >= RM ? RM : (LOGM - LS0);
     ntt_round<LOGM, LOGG, P, NT, ROW, true, LS0, R>(s, tw, m);
     __syncthreads();
-    tile_inv<LOGM, LOGG, P, NT, ROW, K - 1>(s, tw, m);
+    tile_inv<LOGM, LOGG, P, NT, ROW, RM, K - 1>(s, tw, m);
   }
 }
 

@@ -16,6 +16,7 @@ from . import build as _build
 KS_OK, KS_EINVAL, KS_EPRIME, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_EALIGN = 0, -1, -2, -3, -4, -5, -6
 KS_AUTO, KS_DSOB, KS_DPOB, KS_DSOC, KS_DPOC = 0, 1, 2, 3, 4
 KS_UNFUSED = 0x100
+KS_RADIX4 = 0x200
 KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE = 0x1, 0x2
 VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
 
@@ -39,7 +40,9 @@ class ks_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
                 ("QP", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("np", ctypes.c_uint32),
                 ("evk_words", ctypes.c_size_t), ("in_words", ctypes.c_size_t),
-                ("out_words", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t)]
+                ("out_words", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t),
+                ("tuned_variant", ctypes.c_int), ("tuned_chunks", ctypes.c_int),
+                ("tuned_batch", ctypes.c_int), ("tuned_ms", ctypes.c_float)]
 
 
 class ks_kernel_stat(ctypes.Structure):
@@ -59,7 +62,7 @@ _lock = threading.Lock()
 SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_keygen",
            "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
            "ks_sync_status", "ks_strerror", "ks_cuda_error_string", "ks_profile_begin",
-           "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc")
+           "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune")
 
 
 def lib_path() -> str:
@@ -86,6 +89,7 @@ def load(build: bool = True):
         l.ks_switch.argtypes = [vp, vp, vp, vp, i, i, vp, sz, vp]
         l.ks_switch_host.argtypes = [vp, vp, vp, vp, i, i, vp]
         l.ks_switch_batch.argtypes = [ctypes.POINTER(ks_job), i, i, vp]
+        l.ks_tune.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp]
         l.ks_sync_status.argtypes = [vp, vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
@@ -214,6 +218,27 @@ def ks_profile_end() -> list:
     _check(load().ks_profile_end(arr, 64, ctypes.byref(n)), "ks_profile_end")
     return [{"name": arr[k].name.decode(), "launches": arr[k].launches, "ms": arr[k].ms,
              "bytes": arr[k].bytes, "ops": arr[k].ops} for k in range(min(n.value, 64))]
+
+
+def ks_tune(ctx: int, d, evk, out, batch: int = 1, stream=None):
+    """Times the dataflows on this job and makes the fastest the context's KS_AUTO plan.
+    Returns (variant, chunks)."""
+    v, c = ctypes.c_int(), ctypes.c_int()
+    _check(load().ks_tune(ctx, _ptr(d), _ptr(evk), _ptr(out), batch, ctypes.byref(v),
+                          ctypes.byref(c), _stream(stream)), "ks_tune")
+    return v.value, c.value
+
+
+def variant_name(v: int, chunks: int = 0) -> str:
+    names = {KS_DSOB: "DSOB", KS_DPOB: "DPOB", KS_DSOC: "DSOC", KS_DPOC: "DPOC"}
+    s = names.get(v & 0xff, "AUTO")
+    if (v & 0xff) in (KS_DSOC, KS_DPOC):
+        s += f"-c{chunks or 2}"
+    if v & KS_RADIX4:
+        s += "-r4"
+    if v & KS_UNFUSED:
+        s += "-unfused"
+    return s
 
 
 def ks_sync_status(ctx: int, stream=None) -> int:
