@@ -39,6 +39,30 @@ __device__ __forceinline__ u64 shoup(u64 y, u64 w, u64 wp, u64 m) {
 
 __device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }
 
+// High 64 bits of y*wp, under-estimated by at most 2: yh*wh plus the high words of
+// the two cross products; the low x low product and the carry out of the low words
+// of the cross products are dropped (each worth at most 1).
+__device__ __forceinline__ u64 mulhi_approx(u64 y, u64 wp) {
+  const uint32_t yl = (uint32_t)y, yh = (uint32_t)(y >> 32);
+  const uint32_t wl = (uint32_t)wp, wh = (uint32_t)(wp >> 32);
+  u64 t1, t2, h;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(t1) : "r"(yl), "r"(wh));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(t2) : "r"(yh), "r"(wl));
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(h) : "r"(yh), "r"(wh), "l"((t1 >> 32) + (t2 >> 32)));
+  return h;
+}
+
+// y * w mod m in [0, 4m) with the approximate quotient (Shoup's bound 2m plus 2m).
+__device__ __forceinline__ u64 shoup4(u64 y, u64 w, u64 wp, u64 m) {
+  return y * w - mulhi_approx(y, wp) * m;
+}
+
+// x mod m for any x < 2^64 (Barrett with mu = floor(2^64 / m)), canonical.
+__device__ __forceinline__ u64 reduce_full(u64 x, u64 m, u64 mu) {
+  const u64 r = x - __umul64hi(x, mu) * m;  // in [0, 2m)
+  return r >= m ? r - m : r;
+}
+
 // [0, 4m) -> [0, m)
 __device__ __forceinline__ u64 canon4(u64 x, u64 m) { return csub(csub(x, 2 * m), m); }
 

@@ -144,6 +144,7 @@ int build_tables(ks_context *c) {
     mi.r1 = (u64)(((u128)1 << 64) % m);
     mi.r1s = shoup_of(mi.r1, m);
     mi.r2 = mulm(mi.r1, mi.r1, m);
+    mi.mu = (u64)((((u128)1) << 64) / m);
     mod[t] = mi;
     const u64 psi = root_2n(m, logn);
     const u64 psi_inv = invm(psi, m);

@@ -21,7 +21,12 @@ struct ModInfo {
   u64 r1;    // 2^64 mod m
   u64 r1s;   // Shoup companion of r1
   u64 r2;    // 2^128 mod m
+  u64 mu;    // floor(2^64 / m)
 };
+
+// Moduli below this take the fast butterflies (no per-stage reduction, approximate
+// Shoup quotients); the bounds they rely on are stated in ks_ntt.cuh.
+constexpr u64 kFastModulus = (u64)1 << 51;
 
 // Work items of one launch, decoded from blockIdx.y (see ks_kern.cuh, decode()).
 // A decoded item packs: bits 0-7 limb, bits 8-15 digit (ModUp) or polynomial

@@ -107,8 +107,8 @@ __device__ __forceinline__ void load_rows(u64 *s, const u64 *src, int r0) {
 }
 
 template <class GT>
-__device__ __forceinline__ void store_rows(u64 *dst, const u64 *s, int r0, u64 m, int mode) {
-  // mode 0: as is; 1: [0,4m) -> canonical
+__device__ __forceinline__ void store_rows(u64 *dst, const u64 *s, int r0, u64 m, u64 mu) {
+  // lazy values -> canonical
   constexpr int TILE = GT::TILE, LOGB = GT::LOGB, P = GT::PR;
   ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst + ((size_t)r0 << LOGB));
 #pragma unroll
@@ -117,12 +117,8 @@ __device__ __forceinline__ void store_rows(u64 *dst, const u64 *s, int r0, u64 m
     if ((TILE / 2) % GT::NT != 0 && e2 >= TILE / 2) break;
     const int e = 2 * e2, g = e >> LOGB, x = e & ((1 << LOGB) - 1);
     ulonglong2 val;
-    val.x = s[x * P + g];
-    val.y = s[(x + 1) * P + g];
-    if (mode == 1) {
-      val.x = canon4(val.x, m);
-      val.y = canon4(val.y, m);
-    }
+    val.x = reduce_full(s[x * P + g], m, mu);
+    val.y = reduce_full(s[(x + 1) * P + g], m, mu);
     d2[e2] = val;
   }
 }
@@ -331,7 +327,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   const InttSet is = intt_set(a, js.j[blockIdx.z], wo, which);
   const int ii = blockIdx.y, prime = is.prime_base + ii, blk = blockIdx.x;
   const int r0 = blk * GT::GR;
-  const u64 m = a.tab.mod[prime].m;
+  const u64 m = a.tab.mod[prime].m, mu = a.tab.mod[prime].mu;
   const size_t N = a.N;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_i, prime, blk), GT::TWR);
   const ulonglong2 sc = is.scale[ii];
@@ -348,7 +344,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
         d[e] = csub(shoup(sm[e], sc.x, sc.y, m), m);
       }
     } else {
-      store_rows<GT>(d, sm, r0, m, 0);
+      store_rows<GT>(d, sm, r0, m, mu);
     }
     __syncthreads();
   }
@@ -446,7 +442,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   load_rows<GT>(sm, b, r0);
   __syncthreads();
   tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
-  store_rows<GT>(b, sm, r0, m, 1);
+  store_rows<GT>(b, sm, r0, m, a.tab.mod[t].mu);
 }
 
 // ModUp row pass fused with the key multiply. One CTA = one row tile of one
@@ -512,7 +508,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (768 / GeoT<LOGN, RL>::NT)
         const int e = threadIdx.x + k * GT::NT;
         if (GT::TILE % GT::NT == 0 || e < GT::TILE) {
           const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
-          const u64 y = canon4(sm[x * GT::PR + g], mi.m);
+          const u64 y = reduce_full(sm[x * GT::PR + g], mi.m, mi.mu);
           U128 p0 = {0, 0}, p1 = {0, 0};
           mac128(p0, y, __ldg(e0 + e));
           mac128(p1, y, __ldg(e1 + e));
@@ -556,7 +552,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   const u64 *vp = jp.ws + wo.vp, *tmp2 = jp.ws + wo.tmp2, *acc = jp.ws + wo.acc;
   const uint32_t w = decode(a, tk, blockIdx.y);
   const int i = task_limb(w), blk = blockIdx.x, r0 = blk * GT::GR;
-  const u64 m = a.tab.mod[i].m;
+  const u64 m = a.tab.mod[i].m, mu = a.tab.mod[i].mu;
   const ulonglong2 pv = a.tab.pinv[i];
   const size_t N = a.N;
   const size_t off0 = (size_t)r0 << GT::LOGB;
@@ -576,7 +572,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
       const int e = threadIdx.x + k * GT::NT;
       if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
       const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
-      const u64 z = canon4(sm[x * GT::PR + g], m);
+      const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
       o[e] = csub(shoup(__ldg(ac + e) + m - z, pv.x, pv.y, m), m);
     }
     __syncthreads();

@@ -21,6 +21,7 @@
 // stages there (radix-2^R), and writes them back; every offset is a constant.
 #pragma once
 #include "ks_arith.cuh"
+#include "ks_internal.h"
 
 namespace ks {
 
@@ -71,11 +72,33 @@ __device__ __forceinline__ void bfly_inv(u64 &a, u64 &b, const ulonglong2 w, u64
   b = shoup(X - Y + m2, w.x, w.y, m);
 }
 
-template <int LOGM, int LOGG, int P, int NT, bool ROW, bool INV, int LS0, int R>
+// Fast butterflies for m < kFastModulus (2^51). Forward: no reduction of the
+// upper input, approximate Shoup product T in [0, 4m): each stage raises the
+// bound by 4m, so a column pass (<= 8 stages) starting below 2m ends below 34m
+// and the row pass (<= 9 stages) below 70m (12 single-pass stages: below 50m).
+__device__ __forceinline__ void bfly_fwd_fast(u64 &a, u64 &b, const ulonglong2 w, u64 m,
+                                              u64 m4) {
+  const u64 X = a;
+  const u64 T = shoup4(b, w.x, w.y, m);
+  a = X + T;
+  b = X - T + m4;
+}
+// Inverse: canonical inputs; the k-th processed stage adds without reduction and
+// biases the difference by B_k = m 2^(k+1) (>= the bound of both inputs); the
+// product is taken with the approximate quotient, in [0, 4m). After K stages all
+// values are below m 2^(K+1) <= 2^13 m < 2^64.
+__device__ __forceinline__ void bfly_inv_fast(u64 &a, u64 &b, const ulonglong2 w, u64 m,
+                                              u64 bias) {
+  const u64 X = a, Y = b;
+  a = X + Y;
+  b = shoup4(X - Y + bias, w.x, w.y, m);
+}
+
+template <int LOGM, int LOGG, int P, int NT, bool ROW, bool INV, int LS0, int R, bool FAST>
 __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
   constexpr int SUB = LOGM - LS0 - R;
   constexpr int NG = 1 << (LOGM - R + LOGG);
-  const u64 m2 = 2 * m;
+  const u64 m2 = 2 * m, m4 = 4 * m;
 #pragma unroll
   for (int it = 0; it < (NG + NT - 1) / NT; ++it) {
     const int grp = threadIdx.x + it * NT;
@@ -100,7 +123,10 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
         for (int u = 0; u < (1 << R); ++u) {
           if (u & half) continue;
           const ulonglong2 w = twq[ROW ? ((u >> (R - q)) << LOGG) : (u >> (R - q))];
-          bfly_fwd(v[u], v[u + half], w, m, m2);
+          if (FAST)
+            bfly_fwd_fast(v[u], v[u + half], w, m, m4);
+          else
+            bfly_fwd(v[u], v[u + half], w, m, m2);
         }
       }
     } else {
@@ -110,11 +136,16 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
         const ulonglong2 *twq =
             ROW ? tw + ((((1 << (LS0 + q)) - 1 + (hi << q)) << LOGG) + g)
                 : tw + (1 << (LS0 + q)) + (hi << q);
+        // processed-stage index k = LOGM-1-ls, bias m 2^(k+1)
+        const u64 bias = m << (LOGM - (LS0 + q));
 #pragma unroll
         for (int u = 0; u < (1 << R); ++u) {
           if (u & half) continue;
           const ulonglong2 w = twq[ROW ? ((u >> (R - q)) << LOGG) : (u >> (R - q))];
-          bfly_inv(v[u], v[u + half], w, m, m2);
+          if (FAST)
+            bfly_inv_fast(v[u], v[u + half], w, m, bias);
+          else
+            bfly_inv(v[u], v[u + half], w, m, m2);
         }
       }
     }
@@ -126,27 +157,47 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
 // Forward stages 0..LOGM-1 of every sub-transform in the tile, in rounds of at
 // most RM stages. Inputs in [0, 4m), outputs in [0, 4m). Caller syncs before;
 // each round syncs after.
-template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3, int LS0 = 0>
-__device__ __forceinline__ void tile_fwd(u64 *s, const ulonglong2 *tw, u64 m) {
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM, bool FAST, int LS0 = 0>
+__device__ __forceinline__ void tile_fwd_t(u64 *s, const ulonglong2 *tw, u64 m) {
   if constexpr (LS0 < LOGM) {
     constexpr int R = (LOGM - LS0) >= RM ? RM : (LOGM - LS0);
-    ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R>(s, tw, m);
+    ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R, FAST>(s, tw, m);
     __syncthreads();
-    tile_fwd<LOGM, LOGG, P, NT, ROW, RM, LS0 + R>(s, tw, m);
+    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, FAST, LS0 + R>(s, tw, m);
   }
 }
 
+// Forward stages on the tile; fast butterflies when m < kFastModulus. Outputs are
+// lazy (below 70m fast, 4m exact): reduce with reduce_full before use.
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3>
+__device__ __forceinline__ void tile_fwd(u64 *s, const ulonglong2 *tw, u64 m) {
+  if (m < kFastModulus)
+    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, true>(s, tw, m);
+  else
+    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, false>(s, tw, m);
+}
+
 // Inverse stages LOGM-1..0. Inputs in [0, 2m), outputs in [0, 2m).
-template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3,
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM, bool FAST,
           int K = (LOGM + RM - 1) / RM - 1>
-__device__ __forceinline__ void tile_inv(u64 *s, const ulonglong2 *tw, u64 m) {
+__device__ __forceinline__ void tile_inv_t(u64 *s, const ulonglong2 *tw, u64 m) {
   if constexpr (K >= 0 && LOGM > 0) {
     constexpr int LS0 = RM * K;
     constexpr int R = (LOGM - LS0) >= RM ? RM : (LOGM - LS0);
-    ntt_round<LOGM, LOGG, P, NT, ROW, true, LS0, R>(s, tw, m);
+    ntt_round<LOGM, LOGG, P, NT, ROW, true, LS0, R, FAST>(s, tw, m);
     __syncthreads();
-    tile_inv<LOGM, LOGG, P, NT, ROW, RM, K - 1>(s, tw, m);
+    tile_inv_t<LOGM, LOGG, P, NT, ROW, RM, FAST, K - 1>(s, tw, m);
   }
+}
+
+// Inverse stages; inputs canonical (fast) or below 2m (exact). Outputs lazy (below
+// 2^13 m fast, 2m exact): reduce with reduce_full or a Shoup scaling before use.
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3>
+__device__ __forceinline__ void tile_inv(u64 *s, const ulonglong2 *tw, u64 m) {
+  if (m < kFastModulus)
+    tile_inv_t<LOGM, LOGG, P, NT, ROW, RM, true>(s, tw, m);
+  else
+    tile_inv_t<LOGM, LOGG, P, NT, ROW, RM, false>(s, tw, m);
 }
 
 }  // namespace ks
