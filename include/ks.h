@@ -160,6 +160,8 @@ typedef struct {
   const uint64_t *d_dev;   /* [L+1][N] */
   const uint64_t *evk_dev; /* [beta][2][QP][N] */
   uint64_t *out_dev;       /* [2][L+1][N] */
+  int variant;             /* dataflow for this job (as in ks_switch); 0 = KS_AUTO */
+  int chunks;              /* OutputChunked groups (0 = the context's or 2) */
 } ks_job;
 
 #define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph, replay it on later
@@ -186,6 +188,30 @@ int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uin
 /* Reads and clears the context's sticky device error word (bounded waits that
  * gave up). Synchronizes `stream`. Returns KS_OK or KS_ETIMEOUT. */
 int ks_sync_status(ks_context *ctx, void *stream);
+
+/* Dataflow selector: an MLP 6 -> 64 -> 64 -> 4 (ReLU, FP32) that maps workload
+ * features to the predicted log-latency of the four dataflows. The paper motivates
+ * it (parameter-aware choice of the dataflow, Sec. V) but gives no model; it never
+ * touches the KeySwitch arithmetic. Parameters: KS_MLP_PARAMS floats,
+ *   W1[6][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
+ * (W[i][j]: input i to output j). x [batch][6], y / t / mask [batch][4], all device
+ * float arrays, batch <= KS_MLP_MAX_BATCH. Asynchronous on `stream`. */
+#define KS_MLP_PARAMS 4868
+#define KS_MLP_MAX_BATCH 256
+int ks_mlp_forward(const float *params_dev, const float *x_dev, int batch, float *y_dev,
+                   void *stream);
+/* Gradient of the masked mean-squared loss sum(mask (y - t)^2) / sum(mask) with
+ * respect to every parameter (grad_dev: KS_MLP_PARAMS floats), and the loss. */
+int ks_mlp_grad(const float *params_dev, const float *x_dev, const float *t_dev,
+                const float *mask_dev, int batch, float *grad_dev, float *loss_dev,
+                void *stream);
+/* `steps` full-batch Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on params_dev in
+ * place; adam_m / adam_v: moment buffers (KS_MLP_PARAMS floats each, zero at the start),
+ * step0: steps already taken (bias correction), grad_scratch: KS_MLP_PARAMS floats,
+ * loss_dev: `steps` floats, the loss before each update. One launch. */
+int ks_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev, float *grad_scratch,
+                 const float *x_dev, const float *t_dev, const float *mask_dev, int batch,
+                 int steps, float lr, int step0, float *loss_dev, void *stream);
 
 /* Per-kernel timing with CUDA events, for measurement. Between ks_profile_begin and
  * ks_profile_end every kernel launch made by ks_switch on this thread is bracketed

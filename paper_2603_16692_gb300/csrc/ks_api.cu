@@ -337,8 +337,9 @@ void forget_graphs(ks_context *c) {
   std::lock_guard<std::mutex> lk(g_batch.mu);
   for (auto it = g_batch.graphs.begin(); it != g_batch.graphs.end();) {
     bool uses = false;
-    for (size_t k = 2; k + 3 < it->first.size(); k += 4)
-      if (it->first[k] == (uintptr_t)c) uses = true;
+    const size_t nj = it->first.empty() ? 0 : (size_t)it->first[0];
+    for (size_t k = 0; k < nj && 2 + 5 * k < it->first.size(); ++k)
+      if (it->first[2 + 5 * k] == (uintptr_t)c) uses = true;
     if (uses) {
       cudaGraphExecDestroy(it->second);
       it = g_batch.graphs.erase(it);
@@ -582,14 +583,18 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       return KS_EALIGN;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  // Groups of jobs sharing a context, in order of first appearance.
+  // Groups of jobs sharing a context and a plan, in order of first appearance.
   std::vector<ks_context *> ctxs;
+  std::vector<std::pair<int, int>> gplan;  // requested (variant, chunks)
   std::vector<std::vector<int>> members;
   for (int k = 0; k < njobs; ++k) {
     size_t g = 0;
-    while (g < ctxs.size() && ctxs[g] != jobs[k].ctx) ++g;
+    while (g < ctxs.size() && !(ctxs[g] == jobs[k].ctx && gplan[g].first == jobs[k].variant &&
+                                gplan[g].second == jobs[k].chunks))
+      ++g;
     if (g == ctxs.size()) {
       ctxs.push_back(jobs[k].ctx);
+      gplan.emplace_back(jobs[k].variant, jobs[k].chunks);
       members.emplace_back();
     }
     members[g].push_back(k);
@@ -597,21 +602,21 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
   if (flags & KS_BATCH_AUTOTUNE) {
     for (size_t g = 0; g < ctxs.size(); ++g) {
       ks_context *c = ctxs[g];
+      if ((gplan[g].first & 0xff) != KS_AUTO) continue;  // the job names its plan
       if (c->tuned_batch == std::min<int>(kMaxBatch, (int)members[g].size()) &&
           c->tuned_variant > 0)
         continue;
       const ks_job &jb = jobs[members[g][0]];
       int v = 0, ch = 0;
       int rc = ks_tune(c, jb.d_dev, jb.evk_dev, jb.out_dev,
-                       std::min<int>(kMaxBatch, (int)members[g].size()), &v, &ch,
-                       stream);
+                       std::min<int>(kMaxBatch, (int)members[g].size()), &v, &ch, stream);
       if (rc) return rc;
     }
   }
   std::vector<Plan> plans(ctxs.size());
   size_t total = 0;
   for (size_t g = 0; g < ctxs.size(); ++g) {
-    int rc = make_plan(ctxs[g], KS_AUTO, 0, &plans[g]);
+    int rc = make_plan(ctxs[g], gplan[g].first, gplan[g].second, &plans[g]);
     if (rc) return rc;
     total += plans[g].total * 8 * members[g].size();
   }
@@ -640,6 +645,7 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       key.push_back((uintptr_t)jobs[k].d_dev);
       key.push_back((uintptr_t)jobs[k].evk_dev);
       key.push_back((uintptr_t)jobs[k].out_dev);
+      key.push_back(((uintptr_t)(uint32_t)jobs[k].variant << 32) | (uint32_t)jobs[k].chunks);
     }
     for (size_t g = 0; g < ctxs.size(); ++g) {
       key.push_back((uintptr_t)ctxs[g]->tuned_variant);

@@ -52,7 +52,8 @@ class ks_kernel_stat(ctypes.Structure):
 
 class ks_job(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("d_dev", ctypes.c_void_p),
-                ("evk_dev", ctypes.c_void_p), ("out_dev", ctypes.c_void_p)]
+                ("evk_dev", ctypes.c_void_p), ("out_dev", ctypes.c_void_p),
+                ("variant", ctypes.c_int), ("chunks", ctypes.c_int)]
 
 
 _lib = None
@@ -62,7 +63,8 @@ _lock = threading.Lock()
 SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_keygen",
            "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
            "ks_sync_status", "ks_strerror", "ks_cuda_error_string", "ks_profile_begin",
-           "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune")
+           "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune",
+           "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train")
 
 
 def lib_path() -> str:
@@ -90,6 +92,9 @@ def load(build: bool = True):
         l.ks_switch_host.argtypes = [vp, vp, vp, vp, i, i, vp]
         l.ks_switch_batch.argtypes = [ctypes.POINTER(ks_job), i, i, vp]
         l.ks_tune.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp]
+        l.ks_mlp_forward.argtypes = [vp, vp, i, vp, vp]
+        l.ks_mlp_grad.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
+        l.ks_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, ctypes.c_float, i, vp, vp]
         l.ks_sync_status.argtypes = [vp, vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
@@ -200,10 +205,12 @@ def ks_switch_host(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO, chun
 
 
 def ks_switch_batch(jobs, flags: int = 0, stream=None):
-    """jobs: sequence of (ctx, d, evk, out) with device tensors."""
+    """jobs: sequence of (ctx, d, evk, out[, variant, chunks]) with device tensors."""
     arr = (ks_job * len(jobs))()
-    for k, (ctx, d, evk, out) in enumerate(jobs):
-        arr[k] = ks_job(ctx, _ptr(d), _ptr(evk), _ptr(out))
+    for k, jb in enumerate(jobs):
+        ctx, d, evk, out = jb[:4]
+        v, c = (jb[4], jb[5]) if len(jb) > 4 else (0, 0)
+        arr[k] = ks_job(ctx, _ptr(d), _ptr(evk), _ptr(out), v, c)
     _check(load().ks_switch_batch(arr, len(jobs), flags, _stream(stream)), "ks_switch_batch")
 
 
@@ -239,6 +246,25 @@ def variant_name(v: int, chunks: int = 0) -> str:
     if v & KS_UNFUSED:
         s += "-unfused"
     return s
+
+
+KS_MLP_PARAMS, KS_MLP_MAX_BATCH = 4868, 256
+
+
+def ks_mlp_forward(params, x, y, stream=None):
+    _check(load().ks_mlp_forward(_ptr(params), _ptr(x), x.shape[0], _ptr(y), _stream(stream)),
+           "ks_mlp_forward")
+
+
+def ks_mlp_grad(params, x, t, mask, grad, loss, stream=None):
+    _check(load().ks_mlp_grad(_ptr(params), _ptr(x), _ptr(t), _ptr(mask), x.shape[0], _ptr(grad),
+                              _ptr(loss), _stream(stream)), "ks_mlp_grad")
+
+
+def ks_mlp_train(params, adam_m, adam_v, grad, x, t, mask, steps, lr, step0, loss, stream=None):
+    _check(load().ks_mlp_train(_ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(grad), _ptr(x),
+                               _ptr(t), _ptr(mask), x.shape[0], steps, lr, step0, _ptr(loss),
+                               _stream(stream)), "ks_mlp_train")
 
 
 def ks_sync_status(ctx: int, stream=None) -> int:

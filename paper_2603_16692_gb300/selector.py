@@ -1,0 +1,232 @@
+"""Learned dataflow selector (the parameter-aware choice the paper proposes in Sec. V).
+
+A 6 -> 64 -> 64 -> 4 FP32 MLP predicts the log-latency of the four dataflows
+(DSOB, DPOB, DSOC with 2 chunks, DPOC with 4 chunks: the chunk counts the paper
+found best most often, Sec. IV-D) from workload features; the selected dataflow
+is the argmin. Training and inference run in the library's CUDA kernels
+(ks_mlp_train, ks_mlp_forward). Exhaustive timing stays the fallback and judges
+the regret. The selector never touches the KeySwitch arithmetic.
+
+Features of (dnum, N, L) on a GPU with L2 bytes: log2 N, L+1, dnum, and log2 of
+(DPOB footprint / L2), (DSOB footprint / L2), (evk bytes / L2), where the
+footprints are the ModUp working sets of Table III (beta*QP*N*8 and QP*N*8 bytes).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from . import ks
+from . import workload as W
+
+CANDS = [("DSOB", ks.KS_DSOB, 0), ("DPOB", ks.KS_DPOB, 0), ("DSOC-c2", ks.KS_DSOC, 2),
+         ("DPOC-c4", ks.KS_DPOC, 4)]
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+def footprints(prm) -> dict:
+    """ModUp working-set bytes of each candidate (Table III: O(dNL), O(NL), O(NL/c), O(dNL/c))."""
+    n8 = prm.N * 8
+    return {"DPOB": prm.beta * prm.QP * n8, "DSOB": prm.QP * n8,
+            "DSOC-c2": -(-prm.QP // 2) * n8, "DPOC-c4": prm.beta * -(-prm.QP // 4) * n8}
+
+
+def features(prm, l2: int) -> list:
+    fp = footprints(prm)
+    evk = 2 * prm.beta * prm.QP * prm.N * 8
+    return [prm.logn, prm.L + 1, prm.dnum, math.log2(fp["DPOB"] / l2), math.log2(fp["DSOB"] / l2),
+            math.log2(evk / l2)]
+
+
+def footprint_rule(prm, l2: int) -> int:
+    """The paper's rule (Sec. IV-B): the best strategy moves to the next smaller footprint
+    once L2 is below about twice the footprint. Candidates by decreasing footprint; the
+    first with 2 x footprint <= L2, else the smallest."""
+    fp = footprints(prm)
+    order = sorted(range(len(CANDS)), key=lambda k: -fp[CANDS[k][0]])
+    for k in order:
+        if 2 * fp[CANDS[k][0]] <= l2:
+            return k
+    return order[-1]
+
+
+# ---------------------------------------------------------------------------
+# Sweep: time every candidate on each point through the library.
+
+def sweep(points, reps: int = 5, seed: int = 0, log=print) -> dict:
+    import torch
+    dev = torch.device("cuda")
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+
+    def rand_limbs(mods, lead, n):
+        t = torch.empty((*lead, len(mods), n), dtype=torch.int64, device=dev)
+        for i, m in enumerate(mods):
+            t[..., i, :] = torch.randint(0, m, (*lead, n), generator=gen, device=dev,
+                                         dtype=torch.int64)
+        return t.view(torch.uint64)
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for k, cfg in enumerate(points):
+        prm = W.make_params(*cfg)
+        ctx = ks.Context(prm)
+        d = rand_limbs(prm.q, (), prm.N)
+        evk = rand_limbs(prm.mods, (prm.beta, 2), prm.N)
+        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device=dev)
+        row = []
+        for name, v, c in CANDS:
+            for _ in range(2):
+                ks.ks_switch(ctx.h, d, evk, out, v, c, None, stream)
+            ts = []
+            for _ in range(reps):
+                e0.record(stream)
+                ks.ks_switch(ctx.h, d, evk, out, v, c, None, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            row.append(float(np.median(ts)))
+        ms.append(row)
+        ctx.close()
+        del d, evk, out
+        if log and (k % 20 == 0 or k == len(points) - 1):
+            log(f"sweep {k + 1}/{len(points)} {cfg}: " +
+                " ".join(f"{n}={t:.3f}ms" for (n, _, _), t in zip(CANDS, row)))
+    torch.cuda.empty_cache()
+    return {"device": torch.cuda.get_device_name(dev), "l2": int(l2), "reps": reps,
+            "cands": [n for n, _, _ in CANDS], "points": [list(p) for p in points], "ms": ms}
+
+
+def split(n: int, n_test: int = 40, seed: int = 0):
+    """Seeded split of the sweep into train and held-out indices."""
+    g = W.rng(seed, 5)
+    perm = g.permutation(n)
+    return sorted(perm[n_test:].tolist()), sorted(perm[:n_test].tolist())
+
+
+# ---------------------------------------------------------------------------
+# Model
+
+class Selector:
+    def __init__(self, params, x_mean, x_std, t_mean, t_std, l2):
+        self.params = np.asarray(params, dtype=np.float32)
+        self.x_mean = np.asarray(x_mean, dtype=np.float64)
+        self.x_std = np.asarray(x_std, dtype=np.float64)
+        self.t_mean, self.t_std, self.l2 = float(t_mean), float(t_std), int(l2)
+
+    def norm_x(self, feats) -> np.ndarray:
+        return ((np.asarray(feats, dtype=np.float64) - self.x_mean) / self.x_std).astype(np.float32)
+
+    def predict_ms(self, prms) -> np.ndarray:
+        """Predicted latency (ms) of each candidate, on the GPU (ks_mlp_forward)."""
+        import torch
+        x = torch.from_numpy(self.norm_x([features(p, self.l2) for p in prms])).cuda()
+        p = torch.from_numpy(self.params).cuda()
+        y = torch.empty((len(prms), 4), dtype=torch.float32, device="cuda")
+        for s in range(0, len(prms), ks.KS_MLP_MAX_BATCH):
+            xs = x[s:s + ks.KS_MLP_MAX_BATCH].contiguous()
+            ys = torch.empty((xs.shape[0], 4), dtype=torch.float32, device="cuda")
+            ks.ks_mlp_forward(p, xs, ys)
+            y[s:s + xs.shape[0]] = ys
+        torch.cuda.synchronize()
+        return np.exp(y.cpu().numpy().astype(np.float64) * self.t_std + self.t_mean)
+
+    def choose(self, prms) -> list:
+        return [int(k) for k in np.argmin(self.predict_ms(prms), axis=1)]
+
+    def to_json(self) -> dict:
+        return {"params": self.params.tolist(), "x_mean": self.x_mean.tolist(),
+                "x_std": self.x_std.tolist(), "t_mean": self.t_mean, "t_std": self.t_std,
+                "l2": self.l2, "cands": [n for n, _, _ in CANDS]}
+
+    @staticmethod
+    def from_json(d) -> "Selector":
+        return Selector(d["params"], d["x_mean"], d["x_std"], d["t_mean"], d["t_std"], d["l2"])
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-style initialisation of the 6-64-64-4 layout (seeded)."""
+    g = np.random.default_rng(seed)
+    parts = [g.normal(0, math.sqrt(2 / 6), 6 * 64), np.zeros(64),
+             g.normal(0, math.sqrt(2 / 64), 64 * 64), np.zeros(64),
+             g.normal(0, math.sqrt(1 / 64), 64 * 4), np.zeros(4)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
+    """Fit the MLP on the sweep rows `idx` with the library's CUDA training kernel.
+    Returns (Selector, per-step losses)."""
+    import torch
+    prms = [W.make_params(*p) for p in data["points"]]
+    l2 = data["l2"]
+    X = np.array([features(prms[i], l2) for i in idx], dtype=np.float64)
+    T = np.log(np.array([data["ms"][i] for i in idx], dtype=np.float64))
+    x_mean, x_std = X.mean(0), X.std(0) + 1e-9
+    t_mean, t_std = T.mean(), T.std() + 1e-9
+    sel = Selector(init_params(seed), x_mean, x_std, t_mean, t_std, l2)
+    dev = torch.device("cuda")
+    x = torch.from_numpy(sel.norm_x(X)).to(dev)
+    t = torch.from_numpy(((T - t_mean) / t_std).astype(np.float32)).to(dev)
+    mask = torch.ones_like(t)
+    p = torch.from_numpy(sel.params.copy()).to(dev)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    g = torch.zeros_like(p)
+    loss = torch.zeros(steps, dtype=torch.float32, device=dev)
+    ks.ks_mlp_train(p, m, v, g, x, t, mask, steps, lr, 0, loss)
+    torch.cuda.synchronize()
+    sel.params = p.cpu().numpy()
+    return sel, loss.cpu().numpy()
+
+
+def evaluate(data: dict, sel: Selector, test_idx, train_idx) -> dict:
+    """Regret t(chosen)/t(best) - 1 on test_idx for the MLP, the best single fixed
+    dataflow (chosen on train_idx) and the paper's footprint rule."""
+    prms = [W.make_params(*p) for p in data["points"]]
+    ms = np.array(data["ms"], dtype=np.float64)
+    best = ms.min(1)
+    fixed = int(np.argmin(ms[train_idx].sum(0)))
+    choice_mlp = sel.choose([prms[i] for i in test_idx])
+    out = {}
+    for name, ch in (("mlp", choice_mlp), ("fixed_" + data["cands"][fixed], [fixed] * len(test_idx)),
+                     ("footprint_rule", [footprint_rule(prms[i], data["l2"]) for i in test_idx])):
+        r = np.array([ms[i, c] / best[i] - 1 for i, c in zip(test_idx, ch)])
+        out[name] = {"mean_regret": float(r.mean()), "max_regret": float(r.max()),
+                     "total_ms": float(sum(ms[i, c] for i, c in zip(test_idx, ch)))}
+    out["exhaustive_total_ms"] = float(best[test_idx].sum())
+    return out
+
+
+def load_json(path):
+    with open(path) as f:
+        return json.load(f)
+
+
+def save_json(path, obj):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(obj, f)
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="selector sweep / training")
+    ap.add_argument("cmd", choices=["sweep", "train"])
+    ap.add_argument("--points", type=int, default=200)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--data", default=os.path.join(DATA, "sweep_gb300.json"))
+    ap.add_argument("--model", default=os.path.join(DATA, "selector_gb300.json"))
+    a = ap.parse_args()
+    if a.cmd == "sweep":
+        save_json(a.data, sweep(W.selector_points(0, a.points), a.reps))
+    else:
+        data = load_json(a.data)
+        tr, te = split(len(data["points"]))
+        sel, losses = train(data, tr)
+        save_json(a.model, sel.to_json())
+        print(json.dumps({"final_loss": float(losses[-1]), **evaluate(data, sel, te, tr)}))

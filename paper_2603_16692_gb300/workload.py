@@ -161,3 +161,15 @@ def batch_jobs(seed: int, count: int = 64):
         dnum = int(g.integers(2, 11))
         jobs.append((dnum, logn, L))
     return jobs
+
+
+def selector_points(seed: int = 0, count: int = 200):
+    """Seeded (dnum, log2N, L) points for the selector sweep, over the batch ranges;
+    the largest workload (10, 2^17, 60) is always included."""
+    g = rng(seed, 4)
+    pts = [(10, 17, 60)]
+    while len(pts) < count:
+        p = (int(g.integers(2, 11)), int(g.integers(13, 18)), int(g.integers(4, 61)))
+        if p not in pts:
+            pts.append(p)
+    return pts

@@ -1,0 +1,40 @@
+"""Pins of the selector-MLP oracle: its gradient equals central finite differences of
+its loss (float64), and its layout matches the library's constant."""
+import numpy as np
+
+from oracle import mlp_oracle as M
+
+
+def _case(seed, b=24):
+    g = np.random.default_rng(seed)
+    p = g.normal(0, 0.3, size=M.NP)
+    x = g.normal(0, 1, size=(b, M.IN))
+    t = g.normal(0, 1, size=(b, M.OUT))
+    mask = (g.random((b, M.OUT)) < 0.8).astype(np.float64)
+    return p, x, t, mask
+
+
+def test_layout_size():
+    assert M.NP == 4868
+
+
+def test_gradient_matches_finite_differences():
+    p, x, t, mask = _case(0)
+    L, g = M.loss_and_grad(p, x, t, mask)
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([rng.choice(M.NP, 200, replace=False),
+                          [0, 383, 384, 447, 448, 4543, 4544, 4607, 4608, 4863, 4864, 4867]])
+    h = 1e-6
+    for k in idx:
+        e = np.zeros(M.NP)
+        e[k] = h
+        fd = (M.loss_and_grad(p + e, x, t, mask)[0] - M.loss_and_grad(p - e, x, t, mask)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 + 1e-5 * abs(fd), (k, fd, g[k])
+
+
+def test_masked_entries_do_not_contribute():
+    p, x, t, mask = _case(2)
+    mask[:, 1] = 0
+    t2 = t.copy()
+    t2[:, 1] += 100.0
+    assert np.allclose(M.loss_and_grad(p, x, t, mask)[1], M.loss_and_grad(p, x, t2, mask)[1])

@@ -1,0 +1,97 @@
+"""The selector MLP on the GPU: forward pass and gradients of the library's CUDA
+kernels against the float64 CPU oracle, training, and the regret the trained
+network gains over the methods without it (best fixed dataflow, the paper's
+footprint rule), on the held-out points of the committed GB300 sweep."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from paper_2603_16692_gb300 import ks
+from paper_2603_16692_gb300 import selector as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(seed, b):
+    g = np.random.default_rng(seed)
+    p = (g.normal(0, 0.3, size=M.NP)).astype(np.float32)
+    x = g.normal(0, 1, size=(b, 6)).astype(np.float32)
+    t = g.normal(0, 1, size=(b, 4)).astype(np.float32)
+    mask = (g.random((b, 4)) < 0.9).astype(np.float32)
+    return p, x, t, mask
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("b", [1, 7, 160, 256])
+def test_mlp_forward_and_gradient_match_oracle(b):
+    import torch
+    p, x, t, mask = _case(b, b)
+    y = torch.empty((b, 4), dtype=torch.float32, device="cuda")
+    ks.ks_mlp_forward(_dev(p), _dev(x), y)
+    g = torch.empty(M.NP, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    ks.ks_mlp_grad(_dev(p), _dev(x), _dev(t), _dev(mask), g, loss)
+    torch.cuda.synchronize()
+    y_ref, _ = M.forward(p, x)
+    L_ref, g_ref = M.loss_and_grad(p, x, t, mask)
+    assert np.allclose(y.cpu().numpy(), y_ref, rtol=1e-4, atol=1e-5)
+    assert abs(float(loss.item()) - L_ref) <= 1e-5 + 1e-4 * abs(L_ref)
+    gg = g.cpu().numpy().astype(np.float64)
+    bad = np.abs(gg - g_ref) > 1e-5 + 1e-3 * np.abs(g_ref)
+    assert not bad.any(), f"{bad.sum()} gradient entries off, first {np.argwhere(bad)[:3].ravel()}"
+
+
+def test_mlp_training_step_is_adam_on_oracle_gradient():
+    """One ks_mlp_train step equals Adam applied to the oracle's gradient."""
+    import torch
+    p, x, t, mask = _case(3, 64)
+    dp, m, v, g = _dev(p.copy()), _dev(np.zeros(M.NP, np.float32)), \
+        _dev(np.zeros(M.NP, np.float32)), _dev(np.zeros(M.NP, np.float32))
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    ks.ks_mlp_train(dp, m, v, g, _dev(x), _dev(t), _dev(mask), 1, 1e-2, 0, loss)
+    torch.cuda.synchronize()
+    _, gr = M.loss_and_grad(p, x, t, mask)
+    mh = 0.1 * gr / (1 - 0.9)
+    vh = 0.001 * gr * gr / (1 - 0.999)
+    want = p - 1e-2 * mh / (np.sqrt(vh) + 1e-8)
+    assert np.allclose(dp.cpu().numpy(), want, rtol=1e-4, atol=2e-6)
+
+
+def test_mlp_training_fits_a_smooth_target():
+    import torch
+    g = np.random.default_rng(5)
+    x = g.normal(0, 1, size=(200, 6)).astype(np.float32)
+    t = np.stack([np.sin(x[:, 0]) + x[:, 1], x[:, 2] * x[:, 3], np.abs(x[:, 4]), x[:, 5] ** 2],
+                 1).astype(np.float32)
+    p = _dev(S.init_params(0))
+    z = lambda: _dev(np.zeros(M.NP, np.float32))  # noqa: E731
+    loss = torch.empty(3000, dtype=torch.float32, device="cuda")
+    ks.ks_mlp_train(p, z(), z(), z(), _dev(x), _dev(t), _dev(np.ones_like(t)), 3000, 3e-3, 0, loss)
+    torch.cuda.synchronize()
+    ls = loss.cpu().numpy()
+    assert ls[-1] < 0.05 * ls[0] and ls[-1] < 0.05
+
+
+SWEEP = os.path.join(S.DATA, "sweep_gb300.json")
+
+
+@pytest.mark.skipif(not os.path.exists(SWEEP), reason="no committed GB300 sweep")
+def test_selector_gain_on_held_out_points():
+    data = S.load_json(SWEEP)
+    tr, te = S.split(len(data["points"]))
+    assert len(te) == 40 and len(tr) == len(data["points"]) - 40
+    sel, losses = S.train(data, tr)
+    assert losses[-1] < losses[0]
+    ev = S.evaluate(data, sel, te, tr)
+    fixed = [k for k in ev if k.startswith("fixed_")][0]
+    mlp = ev["mlp"]["mean_regret"]
+    # what the network gains over the methods without it
+    assert mlp <= ev[fixed]["mean_regret"] + 1e-12
+    assert mlp <= ev["footprint_rule"]["mean_regret"] + 1e-12
+    assert mlp <= 0.05, ev
