@@ -237,6 +237,27 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
             for h, d, evk, out in arg:
                 ks.ks_switch(h, d, evk, out, v, c, None, stream)
         plain[name] = len(jobs) / (timed(run_plain, max(2, args.batch_steps // 4)) / 1e3)
+    # learned selector: per-job plans from the MLP (trained on the library's GB300 sweep
+    # with the CUDA training kernel), whole batch as one CUDA graph
+    from paper_2603_16692_gb300 import selector as S
+    sel_info = None
+    try:
+        data = S.load_json(os.path.join(S.DATA, "sweep_gb300.json"))
+        tr, te = S.split(len(data["points"]))
+        sel, losses = S.train(data, tr)
+        sel_info = S.evaluate(data, sel, te, tr)
+        sel_info["train_final_loss"] = float(losses[-1])
+        sel_info["sweep"] = f"{len(data['points'])} points x {len(data['cands'])} plans, " \
+                            f"{len(tr)} train / {len(te)} held out"
+        picks = sel.choose([W.make_params(*cfg) for cfg in jobs])
+        arg_sel = [(h, d, evk, out, S.CANDS[k][1], S.CANDS[k][2])
+                   for (h, d, evk, out), k in zip(arg, picks)]
+        ms_sel = timed(lambda: ks.ks_switch_batch(arg_sel, ks.KS_BATCH_GRAPH, stream),
+                       args.batch_steps)
+        sel_info["batch_value"] = len(jobs) / (ms_sel / 1e3)
+        sel_info["batch_picks"] = {S.CANDS[k][0]: picks.count(k) for k in set(picks)}
+    except (OSError, ValueError, KeyError) as ex:
+        sel_info = {"error": str(ex)}
     flags = ks.KS_BATCH_GRAPH | ks.KS_BATCH_AUTOTUNE
     ms = timed(lambda: ks.ks_switch_batch(arg, flags, stream), args.batch_steps)
     value = len(jobs) / (ms / 1e3)
@@ -255,7 +276,9 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
            "speedup_vs_best_fixed": value / plain[best_name],
            "speedup_vs_dsob": value / plain["DSOB"],
            "algo_bytes_per_batch": algo, "hbm_frac": algo / (ms / 1e3) / 1e9 / hbm,
-           "tuned_plans": tuned}
+           "tuned_plans": tuned, "selector": sel_info}
+    if sel_info and "batch_value" in sel_info:
+        out["selector_speedup_vs_best_fixed"] = sel_info["batch_value"] / plain[best_name]
     for c in ctxs.values():
         c.close()
     return out

@@ -1,11 +1,13 @@
 """Learned dataflow selector (the parameter-aware choice the paper proposes in Sec. V).
 
-A 6 -> 64 -> 64 -> 4 FP32 MLP predicts the log-latency of the four dataflows
-(DSOB, DPOB, DSOC with 2 chunks, DPOC with 4 chunks: the chunk counts the paper
-found best most often, Sec. IV-D) from workload features; the selected dataflow
-is the argmin. Training and inference run in the library's CUDA kernels
-(ks_mlp_train, ks_mlp_forward). Exhaustive timing stays the fallback and judges
-the regret. The selector never touches the KeySwitch arithmetic.
+A 6 -> 64 -> 64 -> 4 FP32 MLP predicts the log-latency of four candidate plans
+from workload features; the selected plan is the argmin. The candidates are the
+plans that compete on GB300 in the library's own sweep of ten plans (four
+dataflows x radix 8 / radix 4, OutputChunked with 2 and 4 chunks): DSOB, DPOB,
+DPOB with radix-4 rounds, and DPOC with 2 chunks. Training and inference run in
+the library's CUDA kernels (ks_mlp_train, ks_mlp_forward). Exhaustive timing of
+all ten plans stays the fallback and judges the regret. The selector never
+touches the KeySwitch arithmetic.
 
 Features of (dnum, N, L) on a GPU with L2 bytes: log2 N, L+1, dnum, and log2 of
 (DPOB footprint / L2), (DSOB footprint / L2), (evk bytes / L2), where the
@@ -22,16 +24,17 @@ import numpy as np
 from . import ks
 from . import workload as W
 
-CANDS = [("DSOB", ks.KS_DSOB, 0), ("DPOB", ks.KS_DPOB, 0), ("DSOC-c2", ks.KS_DSOC, 2),
-         ("DPOC-c4", ks.KS_DPOC, 4)]
+CANDS = [("DSOB", ks.KS_DSOB, 0), ("DPOB", ks.KS_DPOB, 0),
+         ("DPOB-r4", ks.KS_DPOB | ks.KS_RADIX4, 0), ("DPOC-c2", ks.KS_DPOC, 2)]
 DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 
 
 def footprints(prm) -> dict:
-    """ModUp working-set bytes of each candidate (Table III: O(dNL), O(NL), O(NL/c), O(dNL/c))."""
+    """ModUp working-set bytes of each dataflow (Table III: O(dNL), O(NL), O(NL/c), O(dNL/c))."""
     n8 = prm.N * 8
     return {"DPOB": prm.beta * prm.QP * n8, "DSOB": prm.QP * n8,
-            "DSOC-c2": -(-prm.QP // 2) * n8, "DPOC-c4": prm.beta * -(-prm.QP // 4) * n8}
+            "DSOC-c2": -(-prm.QP // 2) * n8, "DPOC-c2": prm.beta * -(-prm.QP // 2) * n8,
+            "DPOC-c4": prm.beta * -(-prm.QP // 4) * n8}
 
 
 def features(prm, l2: int) -> list:
@@ -43,20 +46,32 @@ def features(prm, l2: int) -> list:
 
 def footprint_rule(prm, l2: int) -> int:
     """The paper's rule (Sec. IV-B): the best strategy moves to the next smaller footprint
-    once L2 is below about twice the footprint. Candidates by decreasing footprint; the
-    first with 2 x footprint <= L2, else the smallest."""
+    once L2 is below about twice the footprint. Over the candidate dataflows (radix 8),
+    by decreasing footprint: the first with 2 x footprint <= L2, else the smallest."""
     fp = footprints(prm)
-    order = sorted(range(len(CANDS)), key=lambda k: -fp[CANDS[k][0]])
+    ks_ = [k for k, (n, v, c) in enumerate(CANDS) if not v & ks.KS_RADIX4]
+    order = sorted(ks_, key=lambda k: -fp[CANDS[k][0]])
     for k in order:
         if 2 * fp[CANDS[k][0]] <= l2:
             return k
     return order[-1]
 
 
+def columns(data: dict) -> list:
+    """Indices of the candidate plans among the sweep's measured plans."""
+    return [data["cands"].index(n) for n, _, _ in CANDS]
+
+
 # ---------------------------------------------------------------------------
 # Sweep: time every candidate on each point through the library.
 
-def sweep(points, reps: int = 5, seed: int = 0, log=print) -> dict:
+ALL_PLANS = [(f"{n}{'-r4' if r4 else ''}", v | (ks.KS_RADIX4 if r4 else 0), c)
+             for n, v, c in [("DSOB", ks.KS_DSOB, 0), ("DPOB", ks.KS_DPOB, 0),
+                             ("DSOC-c2", ks.KS_DSOC, 2), ("DPOC-c2", ks.KS_DPOC, 2),
+                             ("DPOC-c4", ks.KS_DPOC, 4)] for r4 in (0, 1)]
+
+
+def sweep(points, reps: int = 5, seed: int = 0, log=print, cands=None) -> dict:
     import torch
     dev = torch.device("cuda")
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
@@ -80,7 +95,7 @@ def sweep(points, reps: int = 5, seed: int = 0, log=print) -> dict:
         evk = rand_limbs(prm.mods, (prm.beta, 2), prm.N)
         out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device=dev)
         row = []
-        for name, v, c in CANDS:
+        for name, v, c in (cands or CANDS):
             for _ in range(2):
                 ks.ks_switch(ctx.h, d, evk, out, v, c, None, stream)
             ts = []
@@ -96,10 +111,11 @@ def sweep(points, reps: int = 5, seed: int = 0, log=print) -> dict:
         del d, evk, out
         if log and (k % 20 == 0 or k == len(points) - 1):
             log(f"sweep {k + 1}/{len(points)} {cfg}: " +
-                " ".join(f"{n}={t:.3f}ms" for (n, _, _), t in zip(CANDS, row)))
+                " ".join(f"{n}={t:.3f}ms" for (n, _, _), t in zip(cands or CANDS, row)))
     torch.cuda.empty_cache()
     return {"device": torch.cuda.get_device_name(dev), "l2": int(l2), "reps": reps,
-            "cands": [n for n, _, _ in CANDS], "points": [list(p) for p in points], "ms": ms}
+            "cands": [n for n, _, _ in (cands or CANDS)], "points": [list(p) for p in points],
+            "ms": ms}
 
 
 def split(n: int, n_test: int = 40, seed: int = 0):
@@ -165,7 +181,8 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
     prms = [W.make_params(*p) for p in data["points"]]
     l2 = data["l2"]
     X = np.array([features(prms[i], l2) for i in idx], dtype=np.float64)
-    T = np.log(np.array([data["ms"][i] for i in idx], dtype=np.float64))
+    cols = columns(data)
+    T = np.log(np.array([data["ms"][i] for i in idx], dtype=np.float64)[:, cols])
     x_mean, x_std = X.mean(0), X.std(0) + 1e-9
     t_mean, t_std = T.mean(), T.std() + 1e-9
     sel = Selector(init_params(seed), x_mean, x_std, t_mean, t_std, l2)
@@ -185,15 +202,17 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
 
 
 def evaluate(data: dict, sel: Selector, test_idx, train_idx) -> dict:
-    """Regret t(chosen)/t(best) - 1 on test_idx for the MLP, the best single fixed
-    dataflow (chosen on train_idx) and the paper's footprint rule."""
+    """Regret t(chosen)/t(best) - 1 on test_idx, the best being the exhaustive minimum
+    over every measured plan, for the MLP, the best single fixed candidate (chosen on
+    train_idx) and the paper's footprint rule."""
     prms = [W.make_params(*p) for p in data["points"]]
-    ms = np.array(data["ms"], dtype=np.float64)
-    best = ms.min(1)
+    allms = np.array(data["ms"], dtype=np.float64)
+    best = allms.min(1)
+    ms = allms[:, columns(data)]
     fixed = int(np.argmin(ms[train_idx].sum(0)))
     choice_mlp = sel.choose([prms[i] for i in test_idx])
     out = {}
-    for name, ch in (("mlp", choice_mlp), ("fixed_" + data["cands"][fixed], [fixed] * len(test_idx)),
+    for name, ch in (("mlp", choice_mlp), ("fixed_" + CANDS[fixed][0], [fixed] * len(test_idx)),
                      ("footprint_rule", [footprint_rule(prms[i], data["l2"]) for i in test_idx])):
         r = np.array([ms[i, c] / best[i] - 1 for i, c in zip(test_idx, ch)])
         out[name] = {"mean_regret": float(r.mean()), "max_regret": float(r.max()),
@@ -223,7 +242,7 @@ if __name__ == "__main__":
     ap.add_argument("--model", default=os.path.join(DATA, "selector_gb300.json"))
     a = ap.parse_args()
     if a.cmd == "sweep":
-        save_json(a.data, sweep(W.selector_points(0, a.points), a.reps))
+        save_json(a.data, sweep(W.selector_points(0, a.points), a.reps, cands=ALL_PLANS))
     else:
         data = load_json(a.data)
         tr, te = split(len(data["points"]))
