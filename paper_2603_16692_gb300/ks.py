@@ -123,8 +123,12 @@ def _check(rc: int, where: str):
 
 
 def _ptr(t) -> int:
+    """Device pointer of a tensor; the C-ABI takes dense row-major arrays only."""
     if t is None:
         return None
+    if not t.is_contiguous():
+        raise ValueError("libks takes contiguous (row-major) tensors; got strides "
+                         f"{tuple(t.stride())} for shape {tuple(t.shape)}")
     return t.data_ptr()
 
 

@@ -141,7 +141,8 @@ class Selector:
     def predict_ms(self, prms) -> np.ndarray:
         """Predicted latency (ms) of each candidate, on the GPU (ks_mlp_forward)."""
         import torch
-        x = torch.from_numpy(self.norm_x([features(p, self.l2) for p in prms])).cuda()
+        x = torch.from_numpy(np.ascontiguousarray(
+            self.norm_x([features(p, self.l2) for p in prms]))).cuda()
         p = torch.from_numpy(self.params).cuda()
         y = torch.empty((len(prms), 4), dtype=torch.float32, device="cuda")
         for s in range(0, len(prms), ks.KS_MLP_MAX_BATCH):
@@ -187,8 +188,8 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
     t_mean, t_std = T.mean(), T.std() + 1e-9
     sel = Selector(init_params(seed), x_mean, x_std, t_mean, t_std, l2)
     dev = torch.device("cuda")
-    x = torch.from_numpy(sel.norm_x(X)).to(dev)
-    t = torch.from_numpy(((T - t_mean) / t_std).astype(np.float32)).to(dev)
+    x = torch.from_numpy(np.ascontiguousarray(sel.norm_x(X))).to(dev)
+    t = torch.from_numpy(np.ascontiguousarray(((T - t_mean) / t_std).astype(np.float32))).to(dev)
     mask = torch.ones_like(t)
     p = torch.from_numpy(sel.params.copy()).to(dev)
     m = torch.zeros_like(p)

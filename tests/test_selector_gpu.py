@@ -97,3 +97,12 @@ def test_selector_gain_on_held_out_points():
     assert mlp < ev["footprint_rule"]["mean_regret"], ev
     assert ev["mlp"]["total_ms"] < ev[fixed]["total_ms"], ev
     assert mlp <= 0.05, ev
+
+
+def test_binding_rejects_strided_tensors():
+    """A transposed view would be read in the wrong order by the kernels: refused."""
+    import torch
+    x = torch.zeros((4, 6), dtype=torch.float32, device="cuda").t()
+    y = torch.empty((6, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        ks.ks_mlp_forward(_dev(S.init_params(0)), x, y)
