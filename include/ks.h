@@ -60,6 +60,9 @@ extern "C" {
 /* OR-ed into the variant: register rounds of radix 4 (4 points per thread, twice the
  * threads per tile) instead of radix 8; more parallelism for small workloads. */
 #define KS_RADIX4 0x200
+/* OR-ed into the variant: register rounds of radix 16 (16 points per thread, half the
+ * threads per tile): fewer shared-memory round trips for large workloads. */
+#define KS_RADIX16 0x400
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -179,7 +182,7 @@ typedef struct {
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream);
 
 /* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
- * {radix 8, radix 4} on this job (replicated `batch` times, 1..16, in one launch set)
+ * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one launch set)
  * and stores the fastest as the context's KS_AUTO plan. Writes the switched result to
  * out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
 int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,

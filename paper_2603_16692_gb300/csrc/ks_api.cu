@@ -39,7 +39,8 @@ struct Plan {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
-  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4)) return KS_EINVAL;
+  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16)) return KS_EINVAL;
+  if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
     // the tuned choice for single KeySwitches, else DPOB fused radix 8
     const int tv = c->tuned_variant;
@@ -61,7 +62,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   }
   pl->base = base;
   pl->unfused = (variant & KS_UNFUSED) != 0;
-  pl->rl = (variant & KS_RADIX4) ? 2 : 3;
+  pl->rl = (variant & KS_RADIX4) ? 2 : (variant & KS_RADIX16) ? 4 : 3;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
   pl->clq = (c->nq + chunks - 1) / chunks;
@@ -154,7 +155,7 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
   const double BF_B = (double)N / 2 * c->logb * J;       // butterflies, row pass
   const double NJ = (double)N * J;
   const bool single = c->loga == 0;
-  const LaunchTable &L = pl.rl == 2 ? *c->lt4 : *c->lt;
+  const LaunchTable &L = pl.rl == 2 ? *c->lt4 : pl.rl == 4 ? *c->lt16 : *c->lt;
   WsOff wo;
   wo.v = (long long)pl.off_v;
   wo.tmp = (long long)pl.off_tmp;
@@ -410,7 +411,9 @@ int ks_context_create(const ks_params *prm, ks_context **out) {
   c->loggr = ks::geo_loggr(logn);
   c->lt = ks::launch_table(logn, 3);
   c->lt4 = ks::launch_table(logn, 2);
-  if (!c->lt || !c->lt4 || c->lt->prepare() != cudaSuccess || c->lt4->prepare() != cudaSuccess) {
+  c->lt16 = ks::launch_table(logn, 4);
+  if (!c->lt || !c->lt4 || !c->lt16 || c->lt->prepare() != cudaSuccess ||
+      c->lt4->prepare() != cudaSuccess || c->lt16->prepare() != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return KS_ECUDA;
@@ -729,11 +732,11 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
   cudaStream_t s = (cudaStream_t)stream;
   const int bases[][2] = {{KS_DPOB, 0}, {KS_DSOB, 0}, {KS_DPOC, 2}, {KS_DPOC, 4}, {KS_DSOC, 2}};
   size_t ws_max = 0;
+  const int radix[3] = {0, KS_RADIX4, KS_RADIX16};
   for (auto &b : bases)
-    for (int r4 = 0; r4 < 2; ++r4) {
+    for (int r : radix) {
       Plan pl;
-      if (make_plan(c, b[0] | (r4 ? KS_RADIX4 : 0), b[1], &pl) == KS_OK)
-        ws_max = std::max(ws_max, pl.total * 8);
+      if (make_plan(c, b[0] | r, b[1], &pl) == KS_OK) ws_max = std::max(ws_max, pl.total * 8);
     }
   const size_t out_b = (size_t)2 * c->nq * c->N * 8;
   void *mem = nullptr;
@@ -749,8 +752,8 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
   float best = 1e30f;
   int best_v = KS_DPOB, best_c = 0, rc = KS_OK;
   for (auto &b : bases) {
-    for (int r4 = 0; r4 < 2 && rc == KS_OK; ++r4) {
-      const int v = b[0] | (r4 ? KS_RADIX4 : 0);
+    for (int ri = 0; ri < 3 && rc == KS_OK; ++ri) {
+      const int v = b[0] | radix[ri];
       Plan pl;
       if (make_plan(c, v, b[1], &pl) != KS_OK) continue;
       JobSet js;

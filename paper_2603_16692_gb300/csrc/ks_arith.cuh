@@ -63,6 +63,12 @@ __device__ __forceinline__ u64 reduce_full(u64 x, u64 m, u64 mu) {
   return r >= m ? r - m : r;
 }
 
+// Bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) from global memory into
+// L2 by the TMA unit; no registers or shared memory are involved.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // [0, 4m) -> [0, m)
 __device__ __forceinline__ u64 canon4(u64 x, u64 m) { return csub(csub(x, 2 * m), m); }
 

@@ -101,6 +101,7 @@ struct ks_context {
   int loga, logb, loggr;  // two-pass split N = 2^loga * 2^logb; rows per row tile 2^loggr
   const ks::LaunchTable *lt = nullptr;   // radix-8 kernels
   const ks::LaunchTable *lt4 = nullptr;  // radix-4 kernels (twice the threads per tile)
+  const ks::LaunchTable *lt16 = nullptr; // radix-16 kernels (half the threads per tile)
   int run_up = 1, run_down = 1;  // max terms per exact 128-bit BConv sum
   std::vector<u64> mods;  // host copy, Q then P
   void *table_mem = nullptr;

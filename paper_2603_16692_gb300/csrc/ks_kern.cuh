@@ -210,14 +210,22 @@ __device__ __forceinline__ void bconv_tile(u64 *s, const u64 *__restrict__ src, 
       z[k] = 0;
     }
     int cnt = 0;
+    // loads of source limb i+1 are issued before the products of limb i
+    u64 x[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k)
+      x[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? __ldg(src + gi[k])
+                                                                           : 0;
     for (int i = 0; i < nsrc; ++i) {
       const u64 c = cst[i];
-      const u64 *si = src + (size_t)i * N;
-      u64 x[H];
+      u64 xn[H];
+      if (i + 1 < nsrc) {
+        const u64 *sn = src + (size_t)(i + 1) * N;
 #pragma unroll
-      for (int k = 0; k < H; ++k)
-        x[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? __ldg(si + gi[k])
-                                                                             : 0;
+        for (int k = 0; k < H; ++k)
+          xn[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? __ldg(sn + gi[k])
+                                                                               : 0;
+      }
 #pragma unroll
       for (int k = 0; k < H; ++k) mac128(acc[k], x[k], c);
       if (++cnt == run || i == nsrc - 1) {
@@ -228,6 +236,10 @@ __device__ __forceinline__ void bconv_tile(u64 *s, const u64 *__restrict__ src, 
           acc[k] = U128{0, 0};
         }
         cnt = 0;
+      }
+      if (i + 1 < nsrc) {
+#pragma unroll
+        for (int k = 0; k < H; ++k) x[k] = xn[k];
       }
     }
 #pragma unroll
@@ -282,6 +294,11 @@ __device__ __forceinline__ u64 *tile_ptr(unsigned char *raw) {
 
 // ---------------------------------------------------------------------------
 // Kernels. grid (tiles, work items, jobs); the job's pointers are js.j[blockIdx.z].
+
+// Minimum resident blocks for a target of `threads` threads per SM (register cap).
+__host__ __device__ constexpr int min_blocks(int nt, int threads) {
+  return threads / nt > 0 ? threads / nt : 1;
+}
 
 // iNTT limb set `which`: 0 = the L+1 input limbs (d -> v), 1 = the P-limbs of both
 // accumulators (acc -> vp). Returns (src, src_outer, dst, dst_outer, outer, prime_base,
@@ -353,7 +370,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
 // per-limb scale.
 template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (1024 / GeoT<LOGN, RL>::NT) > 0 ? 1024 / GeoT<LOGN, RL>::NT : 1)
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 512 : 768))
     k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
   using GT = GeoT<LOGN, RL>;
   extern __shared__ __align__(16) unsigned char raw[];
@@ -453,7 +470,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
 // 128-bit product is the plain product mod m. The row twiddles of (t, tile) are
 // staged once.
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (768 / GeoT<LOGN, RL>::NT) > 0 ? 768 / GeoT<LOGN, RL>::NT : 1)
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 384 : 768))
     k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   using GT = GeoT<LOGN, RL>;
   constexpr int EPT = GT::EPT;
@@ -469,6 +486,20 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (768 / GeoT<LOGN, RL>::NT)
   const int blk = blockIdx.x, r0 = blk * GT::GR;
   const size_t N = a.N;
   const size_t off0 = (size_t)r0 << GT::LOGB;  // the tile is contiguous from here
+  // One thread asks the TMA unit to pull each digit's tiles (two evk tiles and the
+  // ModUp intermediate, or d on the digit's own limbs) into L2 one digit ahead.
+  constexpr unsigned TB = GT::TILE * 8;
+  auto prefetch_digit = [&](int j) {
+    if (threadIdx.x != 0 || j >= tk.j1) return;
+    prefetch_l2(jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + off0, TB);
+    prefetch_l2(jp.evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + off0, TB);
+    const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
+    if (t >= lo && t < hi)
+      prefetch_l2(jp.d + (size_t)t * N + off0, TB);
+    else if (GT::LOGA != 0)
+      prefetch_l2(tmp + (size_t)(j * tk.sm.sj + t * tk.sm.st + tk.sm.base) * N + off0, TB);
+  };
+  prefetch_digit(tk.j0);
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
   // Per-digit products are reduced by REDC and summed lazily in [0, 2m).
   u64 s0[EPT], s1[EPT];
@@ -476,6 +507,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, (768 / GeoT<LOGN, RL>::NT)
 #pragma unroll
   for (int k = 0; k < EPT; ++k) s0[k] = s1[k] = 0;
   for (int j = tk.j0; j < tk.j1; ++j) {
+    prefetch_digit(j + 1);
     const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
     const bool own = t >= lo && t < hi;
     const u64 *e0 = jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + off0;
@@ -556,6 +588,8 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   const ulonglong2 pv = a.tab.pinv[i];
   const size_t N = a.N;
   const size_t off0 = (size_t)r0 << GT::LOGB;
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 2; ++c) prefetch_l2(acc + ((size_t)c * a.qp + i) * N + off0, GT::TILE * 8);
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
   for (int c = 0; c < 2; ++c) {
     const uint32_t wc = pack_task(i, c, task_slot(w) + c * tk.span);
@@ -621,7 +655,7 @@ struct Launch {
     const int inner = which == 0 ? c->nq : c->np;
     if (inner == 0 || js.n == 0) return cudaSuccess;
     k_inv_row<LOGN, RL><<<dim3(GRID_ROW, inner, js.n), GT::NT, GT::SMEM_ROW, s>>>(
-        args_of(c), js, wo, which);
+          args_of(c), js, wo, which);
     return cudaGetLastError();
   }
 
@@ -658,8 +692,8 @@ struct Launch {
                                const Tasks &tk, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
-    k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW, s>>>(
-        args_of(c), js, wo, tk);
+    k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW,
+                                                s>>>(args_of(c), js, wo, tk);
     return cudaGetLastError();
   }
 
@@ -668,7 +702,7 @@ struct Launch {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
     k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW,
-                                                s>>>(args_of(c), js, wo, tk);
+                                                  s>>>(args_of(c), js, wo, tk);
     return cudaGetLastError();
   }
 
@@ -682,7 +716,7 @@ struct Launch {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
     k_fwd_row_store<LOGN, RL><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW, s>>>(
-        args_of(c), js, wo, tk, buf);
+          args_of(c), js, wo, tk, buf);
     return cudaGetLastError();
   }
 

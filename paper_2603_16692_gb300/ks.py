@@ -17,6 +17,7 @@ KS_OK, KS_EINVAL, KS_EPRIME, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_EALIGN = 0, -1
 KS_AUTO, KS_DSOB, KS_DPOB, KS_DSOC, KS_DPOC = 0, 1, 2, 3, 4
 KS_UNFUSED = 0x100
 KS_RADIX4 = 0x200
+KS_RADIX16 = 0x400
 KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE = 0x1, 0x2
 VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
 
@@ -247,6 +248,8 @@ def variant_name(v: int, chunks: int = 0) -> str:
         s += f"-c{chunks or 2}"
     if v & KS_RADIX4:
         s += "-r4"
+    if v & KS_RADIX16:
+        s += "-r16"
     if v & KS_UNFUSED:
         s += "-unfused"
     return s

@@ -11,21 +11,24 @@ from tests.gpu_util import dev, first_mismatch, host, oracle_case
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("radix", [4, 16])
 @pytest.mark.parametrize("cfg", [(2, 5, 3), (3, 11, 7), (2, 13, 5), (4, 15, 9), (6, 16, 11),
-                                 (3, 17, 4)])
-def test_radix4_every_variant(cfg):
+                                 (3, 17, 4), (4, 14, 8)])
+def test_radix4_and_16_every_variant(cfg, radix):
     import torch
     prm, s_from, s_to, a, e, d, evk_o, out_o = oracle_case(cfg, 3)
     ctx = ks.Context(prm)
     try:
         evk, dd = dev(evk_o), dev(d)
+        rf = ks.KS_RADIX4 if radix == 4 else ks.KS_RADIX16
         for v in (ks.KS_DSOB, ks.KS_DPOB, ks.KS_DSOC, ks.KS_DPOC):
-            for c in ((0,) if v in (ks.KS_DSOB, ks.KS_DPOB) else (2, 3)):
-                out = ctx.switch(dd, evk, variant=v | ks.KS_RADIX4, chunks=c)
-                torch.cuda.synchronize()
-                got = host(out)
-                assert np.array_equal(got, out_o), f"{ks.variant_name(v | ks.KS_RADIX4, c)}: " + \
-                    first_mismatch(got, out_o)
+            for fu in (0, ks.KS_UNFUSED):
+                for c in ((0,) if v in (ks.KS_DSOB, ks.KS_DPOB) else (2, 3)):
+                    out = ctx.switch(dd, evk, variant=v | rf | fu, chunks=c)
+                    torch.cuda.synchronize()
+                    got = host(out)
+                    assert np.array_equal(got, out_o), f"{ks.variant_name(v | rf | fu, c)}: " + \
+                        first_mismatch(got, out_o)
     finally:
         ctx.close()
 
