@@ -261,6 +261,10 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
     flags = ks.KS_BATCH_GRAPH | ks.KS_BATCH_AUTOTUNE
     ms = timed(lambda: ks.ks_switch_batch(arg, flags, stream), args.batch_steps)
     value = len(jobs) / (ms / 1e3)
+    # one persistent launch for the whole batch (DPOB fused plans), replayed from a graph
+    pflags = ks.KS_BATCH_PERSISTENT | ks.KS_BATCH_GRAPH
+    ms_p = timed(lambda: ks.ks_switch_batch(arg, pflags, stream), args.batch_steps)
+    p_status = ks.ks_batch_status(stream)
     best_name = max(plain, key=plain.get)
     tuned = {}
     for c in ctxs.values():
@@ -276,7 +280,12 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
            "speedup_vs_best_fixed": value / plain[best_name],
            "speedup_vs_dsob": value / plain["DSOB"],
            "algo_bytes_per_batch": algo, "hbm_frac": algo / (ms / 1e3) / 1e9 / hbm,
-           "tuned_plans": tuned, "selector": sel_info}
+           "tuned_plans": tuned, "selector": sel_info,
+           "persistent": {"value": len(jobs) / (ms_p / 1e3), "ms_per_batch": ms_p,
+                          "status": ks.strerror(p_status),
+                          "speedup_vs_best_fixed": len(jobs) / (ms_p / 1e3) / plain[best_name],
+                          "form": "one persistent kernel launch (graph replay), stage-major "
+                                  "work list, bounded device-side waits"}}
     if sel_info and "batch_value" in sel_info:
         out["selector_speedup_vs_best_fixed"] = sel_info["batch_value"] / plain[best_name]
     for c in ctxs.values():

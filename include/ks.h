@@ -170,8 +170,20 @@ typedef struct {
 #define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph, replay it on later
                                  calls with the same jobs (same pointers) */
 #define KS_BATCH_AUTOTUNE 0x2 /* ks_tune each context first (once per group size) */
+#define KS_BATCH_PERSISTENT 0x4 /* run the whole batch in one persistent kernel (every
+                                   job's N in 2^13..2^17; plans DPOB, fused) */
+#define KS_BATCH_TEST_STALL 0x100 /* tests only, with KS_BATCH_PERSISTENT: make one
+                                     dependency unreachable so that the bounded wait
+                                     gives up and ks_batch_status reports KS_ETIMEOUT */
 
-/* Runs njobs independent KeySwitches on `stream` (asynchronous). Jobs sharing a
+/* With KS_BATCH_PERSISTENT, one kernel launch runs every stage of every job: each
+ * CTA of a co-resident grid claims work items (one tile of one stage of one job) in
+ * stage-major order and waits, with a bounded wait (about 2 s of device time), until
+ * the job's previous stage is complete. A wait that runs out sets a device error
+ * word and every CTA returns; ks_batch_status then reports KS_ETIMEOUT. The
+ * persistent grid assumes it has the GPU to itself while it runs.
+ *
+ * Runs njobs independent KeySwitches on `stream` (asynchronous). Jobs sharing a
  * context form a group: its jobs share every kernel launch (up to 16 jobs per
  * launch, grid z) with the context's tuned plan (KS_AUTO). Groups run concurrently on
  * internal streams forked from and joined back to `stream`. The scratch is a
@@ -180,6 +192,10 @@ typedef struct {
  * batches (issue them on one stream). With KS_BATCH_GRAPH the whole batch is one
  * CUDA graph launch after the first call. */
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream);
+
+/* Synchronizes `stream` and reads the error word of the last persistent batch
+ * launched by this process: KS_OK, or KS_ETIMEOUT if a bounded wait gave up. */
+int ks_batch_status(void *stream);
 
 /* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
  * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one launch set)

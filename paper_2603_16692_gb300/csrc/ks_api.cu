@@ -289,7 +289,16 @@ struct BatchState {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   size_t next_event = 0;
-  std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
+  struct Graph {
+    cudaGraphExec_t exec;
+    void *buf;          // persistent-batch image owned by this graph (or null)
+    size_t state_off;
+  };
+  std::map<std::vector<uintptr_t>, Graph> graphs;
+  void *pbuf = nullptr;  // image of the last non-graph persistent batch
+  size_t pbuf_bytes = 0;
+  const void *last_state_buf = nullptr;
+  size_t last_state_off = 0;
   cudaStream_t stream(int g) {
     const size_t k = (size_t)g % 16;
     while (streams.size() <= k) {
@@ -329,8 +338,12 @@ struct BatchState {
 BatchState g_batch;
 
 void clear_graphs_locked() {
-  for (auto &kv : g_batch.graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : g_batch.graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.buf) cudaFree(kv.second.buf);
+  }
   g_batch.graphs.clear();
+  g_batch.last_state_buf = nullptr;
 }
 
 // Drop the captured graphs that use context c (before c is freed).
@@ -342,7 +355,11 @@ void forget_graphs(ks_context *c) {
     for (size_t k = 0; k < nj && 2 + 5 * k < it->first.size(); ++k)
       if (it->first[2 + 5 * k] == (uintptr_t)c) uses = true;
     if (uses) {
-      cudaGraphExecDestroy(it->second);
+      cudaGraphExecDestroy(it->second.exec);
+      if (it->second.buf) {
+        if (g_batch.last_state_buf == it->second.buf) g_batch.last_state_buf = nullptr;
+        cudaFree(it->second.buf);
+      }
       it = g_batch.graphs.erase(it);
     } else {
       ++it;
@@ -350,9 +367,140 @@ void forget_graphs(ks_context *c) {
   }
 }
 
+// Device-time budget of one wait of the persistent batch kernel.
+constexpr unsigned long long kPersistWaitNs = 2000000000ull;
+
+int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
+  std::vector<const ks_context *> ctxs(njobs);
+  std::vector<Plan> plans(njobs);
+  size_t total = 0;
+  for (int k = 0; k < njobs; ++k) {
+    const ks_context *c = jobs[k].ctx;
+    if (!persist_supported(c)) return KS_EINVAL;
+    ctxs[k] = c;
+    const int v = KS_DPOB | (persist_radix(c->logn) == 2 ? KS_RADIX4 : 0);
+    int rc = make_plan(c, v, 0, &plans[k]);
+    if (rc) return rc;
+    total += plans[k].total * 8;
+  }
+  const bool graph = (flags & KS_BATCH_GRAPH) != 0, stall = (flags & KS_BATCH_TEST_STALL) != 0;
+  std::lock_guard<std::mutex> lk(g_batch.mu);
+  if (g_batch.arena_bytes < total) {
+    if (g_batch.arena) {
+      cudaDeviceSynchronize();
+      cudaFree(g_batch.arena);
+    }
+    clear_graphs_locked();
+    g_batch.arena = nullptr;
+    g_batch.arena_bytes = 0;
+    if (cudaMalloc(&g_batch.arena, total) != cudaSuccess) {
+      cudaGetLastError();
+      return KS_ENOMEM;
+    }
+    g_batch.arena_bytes = total;
+  }
+  std::vector<JobPtr> jp(njobs);
+  std::vector<WsOff> wo(njobs);
+  char *base = (char *)g_batch.arena;
+  for (int k = 0; k < njobs; ++k) {
+    jp[k].d = (const u64 *)jobs[k].d_dev;
+    jp[k].evk = (const u64 *)jobs[k].evk_dev;
+    jp[k].out = (u64 *)jobs[k].out_dev;
+    jp[k].ws = (u64 *)base;
+    base += plans[k].total * 8;
+    wo[k] = WsOff{(long long)plans[k].off_v, (long long)plans[k].off_tmp,
+                  (long long)plans[k].off_acc, (long long)plans[k].off_vp,
+                  (long long)plans[k].off_tmp2};
+  }
+  std::vector<uintptr_t> key;
+  if (graph && !stall) {
+    key.push_back((uintptr_t)njobs);
+    key.push_back((uintptr_t)s);
+    for (int k = 0; k < njobs; ++k) {
+      key.push_back((uintptr_t)jobs[k].ctx);
+      key.push_back((uintptr_t)jobs[k].d_dev);
+      key.push_back((uintptr_t)jobs[k].evk_dev);
+      key.push_back((uintptr_t)jobs[k].out_dev);
+      key.push_back((uintptr_t)0x7e5157e47ull);  // persistent marker
+    }
+    auto it = g_batch.graphs.find(key);
+    if (it != g_batch.graphs.end()) {
+      g_batch.last_state_buf = it->second.buf;
+      g_batch.last_state_off = it->second.state_off;
+      return g_batch.launch_ordered(it->second.exec, s);
+    }
+  }
+  PersistBatch *pb = persist_new();
+  persist_build(*pb, ctxs, jp, wo);
+  const size_t bytes = persist_bytes(*pb), soff = persist_state_offset(*pb);
+  int nj = 0, nw = 0;
+  persist_counts(*pb, &nj, &nw);
+  int rc = KS_OK;
+  void *buf = nullptr;
+  if (graph && !stall) {
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      persist_free(pb);
+      return KS_ENOMEM;
+    }
+  } else {
+    if (g_batch.pbuf_bytes < bytes) {
+      if (g_batch.pbuf) {
+        cudaDeviceSynchronize();
+        cudaFree(g_batch.pbuf);
+      }
+      g_batch.pbuf = nullptr;
+      g_batch.pbuf_bytes = 0;
+      if (cudaMalloc(&g_batch.pbuf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        persist_free(pb);
+        return KS_ENOMEM;
+      }
+      g_batch.pbuf_bytes = bytes;
+    }
+    buf = g_batch.pbuf;
+  }
+  rc = persist_upload(*pb, buf, s);
+  persist_free(pb);
+  if (rc) return rc;
+  if (!(graph && !stall)) {
+    rc = persist_launch(buf, nj, nw, soff, kPersistWaitNs, stall, s);
+    if (rc == KS_OK) {
+      g_batch.last_state_buf = buf;
+      g_batch.last_state_off = soff;
+    }
+    return rc;
+  }
+  cudaStream_t cs = g_batch.capture_stream();
+  KS_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  rc = persist_launch(buf, nj, nw, soff, kPersistWaitNs, false, cs);
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &gr);
+  if (rc == KS_OK && e != cudaSuccess) rc = cuda_rc(e);
+  cudaGraphExec_t exec = nullptr;
+  if (rc == KS_OK && (e = cudaGraphInstantiate(&exec, gr, 0)) != cudaSuccess) rc = cuda_rc(e);
+  if (gr) cudaGraphDestroy(gr);
+  if (rc != KS_OK) {
+    cudaGetLastError();
+    cudaFree(buf);
+    return rc;
+  }
+  g_batch.graphs[key] = BatchState::Graph{exec, buf, soff};
+  g_batch.last_state_buf = buf;
+  g_batch.last_state_off = soff;
+  return g_batch.launch_ordered(exec, s);
+}
+
 }  // namespace
 
 extern "C" {
+
+int ks_batch_status(void *stream) {
+  std::lock_guard<std::mutex> lk(g_batch.mu);
+  if (!g_batch.last_state_buf) return KS_OK;
+  return persist_status(g_batch.last_state_buf, g_batch.last_state_off, (cudaStream_t)stream);
+}
+
 
 const char *ks_strerror(int code) {
   switch (code) {
@@ -577,7 +725,8 @@ int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uin
 
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
   if (njobs < 0 || (njobs > 0 && !jobs)) return KS_EINVAL;
-  if (flags & ~(KS_BATCH_GRAPH | KS_BATCH_AUTOTUNE)) return KS_EINVAL;
+  if (flags & ~(KS_BATCH_GRAPH | KS_BATCH_AUTOTUNE | KS_BATCH_PERSISTENT | KS_BATCH_TEST_STALL))
+    return KS_EINVAL;
   if (njobs == 0) return KS_OK;
   for (int k = 0; k < njobs; ++k) {
     const ks_job &jb = jobs[k];
@@ -586,6 +735,8 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       return KS_EALIGN;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (flags & KS_BATCH_PERSISTENT) return batch_persistent(jobs, njobs, flags, s);
+  if (flags & KS_BATCH_TEST_STALL) return KS_EINVAL;
   // Groups of jobs sharing a context and a plan, in order of first appearance.
   std::vector<ks_context *> ctxs;
   std::vector<std::pair<int, int>> gplan;  // requested (variant, chunks)
@@ -655,7 +806,7 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       key.push_back((uintptr_t)ctxs[g]->tuned_chunks);
     }
     auto it = g_batch.graphs.find(key);
-    if (it != g_batch.graphs.end()) return g_batch.launch_ordered(it->second, s);
+    if (it != g_batch.graphs.end()) return g_batch.launch_ordered(it->second.exec, s);
   }
   // A graph is captured on an internal stream (the caller's may be the legacy default
   // stream, which cannot be captured) and launched ordered after `s`.
@@ -720,7 +871,7 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       cudaGetLastError();
       return rc;
     }
-    g_batch.graphs[key] = exec;
+    g_batch.graphs[key] = BatchState::Graph{exec, nullptr, 0};
     return g_batch.launch_ordered(exec, caller);
   }
   return rc;

@@ -173,6 +173,22 @@ cudaError_t launch_keymult(const ks_context *c, const JobSet &js, const WsOff &o
                            const Tasks &tk, cudaStream_t s);
 cudaError_t launch_moddown_scale(const ks_context *c, const JobSet &js, const WsOff &o,
                                  const Tasks &tk, int count, cudaStream_t s);
+// Persistent batch (ks_persist.cu).
+struct PersistBatch;
+bool persist_supported(const ks_context *c);
+int persist_radix(int logn);
+PersistBatch *persist_new();
+void persist_free(PersistBatch *pb);
+void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
+                   const std::vector<JobPtr> &jp, const std::vector<WsOff> &wo);
+size_t persist_bytes(const PersistBatch &pb);
+size_t persist_state_offset(const PersistBatch &pb);
+int persist_counts(const PersistBatch &pb, int *njobs, int *nwork);
+int persist_upload(const PersistBatch &pb, void *dev, cudaStream_t s);
+int persist_launch(void *dev, int njobs, int nwork, size_t state_offset,
+                   unsigned long long limit_ns, bool stall, cudaStream_t s);
+int persist_status(const void *dev, size_t state_offset, cudaStream_t s);
+
 cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
                                const int32_t *e, u64 *polys, cudaStream_t s);
 cudaError_t launch_keygen_combine(const ks_context *c, const u64 *polys, const u64 *a,

@@ -182,7 +182,7 @@ __device__ __forceinline__ void stage_consts(u64 *cst, const u64 *__restrict__ s
 // COL: column tile (element (y, g) = limb index y*N2 + base + g);
 // otherwise row tile (element (x, g) = limb index (base + g)*N2 + x).
 template <class GT, bool COL>
-__device__ __forceinline__ void bconv_tile(u64 *s, const u64 *__restrict__ src, size_t N,
+__device__ __forceinline__ void bconv_tile(u64 *s, const u64 *src, size_t N,
                                            int nsrc, const u64 *cst, int run, int base, u64 m,
                                            u64 minv) {
   constexpr int LOGG = COL ? GT::LOGGC : GT::LOGGR;
@@ -214,8 +214,7 @@ __device__ __forceinline__ void bconv_tile(u64 *s, const u64 *__restrict__ src, 
     u64 x[H];
 #pragma unroll
     for (int k = 0; k < H; ++k)
-      x[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? __ldg(src + gi[k])
-                                                                           : 0;
+      x[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? src[gi[k]] : 0;
     for (int i = 0; i < nsrc; ++i) {
       const u64 c = cst[i];
       u64 xn[H];
@@ -223,8 +222,7 @@ __device__ __forceinline__ void bconv_tile(u64 *s, const u64 *__restrict__ src, 
         const u64 *sn = src + (size_t)(i + 1) * N;
 #pragma unroll
         for (int k = 0; k < H; ++k)
-          xn[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? __ldg(sn + gi[k])
-                                                                               : 0;
+          xn[k] = (TILE % GT::NT == 0 || threadIdx.x + (k0 + k) * GT::NT < TILE) ? sn[gi[k]] : 0;
       }
 #pragma unroll
       for (int k = 0; k < H; ++k) mac128(acc[k], x[k], c);
@@ -335,14 +333,13 @@ __device__ __forceinline__ InttSet intt_set(const KArgs &a, const JobPtr &jp, co
 // limb blockIdx.y in one CTA (shared twiddles). With a single pass (N1 == 1) it also
 // applies the per-limb scale (canonical output).
 template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
-    k_inv_row(KArgs a, JobSet js, WsOff wo, int which) {
+__device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
+                                             int which, int bx, int by, unsigned char *raw) {
   using GT = GeoT<LOGN, RL>;
-  extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const InttSet is = intt_set(a, js.j[blockIdx.z], wo, which);
-  const int ii = blockIdx.y, prime = is.prime_base + ii, blk = blockIdx.x;
+  const InttSet is = intt_set(a, jp, wo, which);
+  const int ii = by, prime = is.prime_base + ii, blk = bx;
   const int r0 = blk * GT::GR;
   const u64 m = a.tab.mod[prime].m, mu = a.tab.mod[prime].mu;
   const size_t N = a.N;
@@ -367,18 +364,24 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   }
 }
 
+template <int LOGN, int RL>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_inv_row(KArgs a, JobSet js, WsOff wo, int which) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  inv_row_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
+}
+
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
 // per-limb scale.
 template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 512 : 768))
-    k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
+__device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
+                                             int which, int bx, int by, unsigned char *raw) {
   using GT = GeoT<LOGN, RL>;
-  extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
-  const InttSet is = intt_set(a, js.j[blockIdx.z], wo, which);
-  const int ii = blockIdx.y, prime = is.prime_base + ii;
-  const int c0 = blockIdx.x * GT::GC;
+  const InttSet is = intt_set(a, jp, wo, which);
+  const int ii = by, prime = is.prime_base + ii;
+  const int c0 = bx * GT::GC;
   const u64 m = a.tab.mod[prime].m;
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_i, prime), GT::TWC);
   const ulonglong2 sc = is.scale[ii];
@@ -401,6 +404,13 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>:
   }
 }
 
+template <int LOGN, int RL>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 512 : 768))
+    k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  inv_col_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
+}
+
 // Buffers of a forward pass for job jp: the BConv sources and the output buffer.
 template <int PRO>
 __device__ __forceinline__ void fwd_bufs(const JobPtr &jp, const WsOff &wo, int buf,
@@ -420,24 +430,31 @@ __device__ __forceinline__ void fwd_bufs(const JobPtr &jp, const WsOff &wo, int 
 // Forward NTT, column pass (global stages 0 .. logN1-1) with a tile producer; the
 // lazy ([0, 4m)) result goes to the output buffer's slot.
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
-    k_fwd_col(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
+__device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
+                                             const Tasks &tk, int buf, int bx, int by,
+                                             unsigned char *raw, u64 *cst) {
   using GT = GeoT<LOGN, RL>;
-  extern __shared__ __align__(16) unsigned char raw[];
-  __shared__ u64 cst[kMaxLimbs];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
   const u64 *src;
   u64 *dst;
-  fwd_bufs<PRO>(js.j[blockIdx.z], wo, buf, src, dst);
-  const uint32_t w = decode(a, tk, blockIdx.y);
+  fwd_bufs<PRO>(jp, wo, buf, src, dst);
+  const uint32_t w = decode(a, tk, by);
   const int t = task_limb(w);
-  const int c0 = blockIdx.x * GT::GC;
+  const int c0 = bx * GT::GC;
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_f, t), GT::TWC);
   produce<GT, PRO, true>(a, sm, cst, w, src, dst, c0);
   __syncthreads();
   tile_fwd<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false, RL>(sm, tws, a.tab.mod[t].m);
   store_cols<GT>(dst + (size_t)task_slot(w) * a.N, sm, c0);
+}
+
+template <int LOGN, int RL, int PRO>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_fwd_col(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __shared__ u64 cst[kMaxLimbs];
+  fwd_col_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, buf, blockIdx.x, blockIdx.y, raw, cst);
 }
 
 // Plain forward row pass: canonical result back in place.
@@ -470,20 +487,18 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
 // 128-bit product is the plain product mod m. The row twiddles of (t, tile) are
 // staged once.
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 384 : 768))
-    k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
+__device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
+                                             const Tasks &tk, int bx, int by,
+                                             unsigned char *raw, u64 *cst) {
   using GT = GeoT<LOGN, RL>;
   constexpr int EPT = GT::EPT;
-  extern __shared__ __align__(16) unsigned char raw[];
-  __shared__ u64 cst[kMaxLimbs];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const JobPtr jp = js.j[blockIdx.z];
   const u64 *v = jp.ws + wo.v, *tmp = jp.ws + wo.tmp;
   u64 *acc = jp.ws + wo.acc;
-  const int t = task_limb(decode(a, tk, blockIdx.y));
+  const int t = task_limb(decode(a, tk, by));
   const ModInfo mi = a.tab.mod[t];
-  const int blk = blockIdx.x, r0 = blk * GT::GR;
+  const int blk = bx, r0 = blk * GT::GR;
   const size_t N = a.N;
   const size_t off0 = (size_t)r0 << GT::LOGB;  // the tile is contiguous from here
   // One thread asks the TMA unit to pull each digit's tiles (two evk tiles and the
@@ -569,21 +584,27 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>:
   }
 }
 
+template <int LOGN, int RL, int PRO>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 384 : 768))
+    k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __shared__ u64 cst[kMaxLimbs];
+  keymult_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
+}
+
 // ModDown row pass fused with the final scaling, both polynomials c = 0, 1 of
 // limb i (TASK_DOWN1) in one CTA (shared twiddles):
 //   out_c[i] = (acc_c[i] - NTT(BConv_{P->Q}(c))[i]) * P^-1 mod q_i.
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
-    k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
+__device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
+                                             const Tasks &tk, int bx, int by,
+                                             unsigned char *raw, u64 *cst) {
   using GT = GeoT<LOGN, RL>;
-  extern __shared__ __align__(16) unsigned char raw[];
-  __shared__ u64 cst[kMaxLimbs];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
-  const JobPtr jp = js.j[blockIdx.z];
   const u64 *vp = jp.ws + wo.vp, *tmp2 = jp.ws + wo.tmp2, *acc = jp.ws + wo.acc;
-  const uint32_t w = decode(a, tk, blockIdx.y);
-  const int i = task_limb(w), blk = blockIdx.x, r0 = blk * GT::GR;
+  const uint32_t w = decode(a, tk, by);
+  const int i = task_limb(w), blk = bx, r0 = blk * GT::GR;
   const u64 m = a.tab.mod[i].m, mu = a.tab.mod[i].mu;
   const ulonglong2 pv = a.tab.pinv[i];
   const size_t N = a.N;
@@ -607,10 +628,18 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
       if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
       const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
       const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
-      o[e] = csub(shoup(__ldg(ac + e) + m - z, pv.x, pv.y, m), m);
+      o[e] = csub(shoup(ac[e] + m - z, pv.x, pv.y, m), m);
     }
     __syncthreads();
   }
+}
+
+template <int LOGN, int RL, int PRO>
+__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+    k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __shared__ u64 cst[kMaxLimbs];
+  moddown_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
 }
 
 // ---------------------------------------------------------------------------

@@ -18,7 +18,8 @@ KS_AUTO, KS_DSOB, KS_DPOB, KS_DSOC, KS_DPOC = 0, 1, 2, 3, 4
 KS_UNFUSED = 0x100
 KS_RADIX4 = 0x200
 KS_RADIX16 = 0x400
-KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE = 0x1, 0x2
+KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE, KS_BATCH_PERSISTENT = 0x1, 0x2, 0x4
+KS_BATCH_TEST_STALL = 0x100
 VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
 
 
@@ -65,7 +66,7 @@ SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_key
            "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
            "ks_sync_status", "ks_strerror", "ks_cuda_error_string", "ks_profile_begin",
            "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune",
-           "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train")
+           "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status")
 
 
 def lib_path() -> str:
@@ -97,6 +98,7 @@ def load(build: bool = True):
         l.ks_mlp_grad.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
         l.ks_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, ctypes.c_float, i, vp, vp]
         l.ks_sync_status.argtypes = [vp, vp]
+        l.ks_batch_status.argtypes = [vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
         l.ks_noalloc_scratch_bytes.argtypes = []
@@ -276,6 +278,12 @@ def ks_mlp_train(params, adam_m, adam_v, grad, x, t, mask, steps, lr, step0, los
 
 def ks_sync_status(ctx: int, stream=None) -> int:
     return load().ks_sync_status(ctx, _stream(stream))
+
+
+def ks_batch_status(stream=None) -> int:
+    """Error code of the last persistent batch (synchronizes the stream): KS_OK, or
+    KS_ETIMEOUT when one of its bounded waits gave up."""
+    return load().ks_batch_status(_stream(stream))
 
 
 class Context:
