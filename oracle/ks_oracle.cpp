@@ -260,21 +260,29 @@ void orc_bconv(const u64 *x, const u64 *src, int ns, const u64 *dst, int nd,
   bconv(xp.data(), src, ns, dst, nd, yp.data(), N, nthreads);
 }
 
-// ModDown (second phase of Fig. 1): acc[QP][N] in NTT form over Q u P ->
-// out[L+1][N] in NTT form over Q, out = (acc - NTT(BConv_{P->Q}(iNTT(acc_P)))) * P^{-1}.
+}  // extern "C"
+
+namespace {
+
+// ModDown (second phase of Fig. 1) at level l of basis B: acc[l+1+alpha][N] in NTT
+// form over q_0..q_l, p_0..p_{alpha-1} -> out[l+1][N] in NTT form over q_0..q_l:
+//   out = (acc - NTT(BConv_{P->Q_l}(iNTT(acc_P)))) * P^{-1}.
 // Floor variant (no +P/2 rounding).
-int orc_moddown(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
-                int np, const u64 *acc, u64 *out, int nthreads) {
-  Basis B;
-  if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
-  u64 N = B.N;
+void moddown_at(const Basis &B, int level, const u64 *acc, u64 *out, int nthreads) {
+  const u64 N = B.N;
+  const int nq = level + 1, np = B.np, logn = B.logn;
+  const u64 *q = B.mod.data(), *p = B.mod.data() + B.nq;
   std::vector<u64> cp((size_t)np * N);
   std::memcpy(cp.data(), acc + (size_t)nq * N, cp.size() * 8);
   parallel_for(np, nthreads, [&](int k) {
-    ntt_inv(cp.data() + (size_t)k * N, logn, p[k], B.pw[nq + k]);
+    ntt_inv(cp.data() + (size_t)k * N, logn, p[k], B.pw[B.nq + k]);
   });
   std::vector<u64> z((size_t)nq * N);
-  orc_bconv(cp.data(), p, np, q, nq, z.data(), logn, nthreads);
+  std::vector<const u64 *> xp(np);
+  std::vector<u64 *> yp(nq);
+  for (int k = 0; k < np; ++k) xp[k] = cp.data() + (size_t)k * N;
+  for (int i = 0; i < nq; ++i) yp[i] = z.data() + (size_t)i * N;
+  bconv(xp.data(), p, np, q, nq, yp.data(), N, nthreads);
   parallel_for(nq, nthreads, [&](int i) {
     u64 *zi = z.data() + (size_t)i * N;
     ntt_fwd(zi, logn, q[i], B.pw[i]);
@@ -285,6 +293,98 @@ int orc_moddown(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
     u64 *oi = out + (size_t)i * N;
     for (u64 n = 0; n < N; ++n) oi[n] = mmul(msub(ai[n], zi[n], q[i]), Pinv, q[i]);
   });
+}
+
+// Hybrid KeySwitch (Sec. II-A, Fig. 1) at level l <= L of basis B (built for level L).
+// At level l the input has l+1 limbs, the digits are D_j = [j alpha, min((j+1) alpha,
+// l+1)) with the top level's alpha, beta_l = ceil((l+1)/alpha), and the key is the
+// top level's: evk[beta][2][QP][N] whose limb t of Q_l is row t and whose P-limb k
+// is row L+1+k (its other rows belong to the dropped primes and are not read).
+//   d [l+1][N], out [2][l+1][N]; traces ext [beta_l][l+1+alpha][N], acc [2][l+1+alpha][N].
+void keyswitch_at(const Basis &B, int level, const u64 *d, const u64 *evk, u64 *out,
+                  u64 *ext_trace, u64 *acc_trace, int nthreads) {
+  const u64 N = B.N;
+  const int logn = B.logn, nq = level + 1, alpha = B.alpha;
+  const int QP = nq + alpha, beta = (nq + alpha - 1) / alpha;
+  // moduli of level l: q_0..q_l then p_0..p_{alpha-1}; their rows in B and in evk
+  std::vector<int> row(QP);
+  for (int t = 0; t < QP; ++t) row[t] = t < nq ? t : B.nq + (t - nq);
+  std::vector<u64> mod(QP);
+  for (int t = 0; t < QP; ++t) mod[t] = B.mod[row[t]];
+  // Step 1: iNTT of the l+1 input limbs.
+  std::vector<u64> x((size_t)nq * N);
+  std::memcpy(x.data(), d, x.size() * 8);
+  parallel_for(nq, nthreads, [&](int i) {
+    ntt_inv(x.data() + (size_t)i * N, logn, mod[i], B.pw[i]);
+  });
+  // Steps 2-4: per digit, ModUp = BConv onto (Q_l u P) \ D_j then NTT; the
+  // digit's own limbs are the input limbs themselves.
+  std::vector<u64> ext((size_t)beta * QP * N);
+  for (int j = 0; j < beta; ++j) {
+    const int lo = j * alpha, hi = std::min((j + 1) * alpha, nq);
+    std::vector<u64> src(mod.begin() + lo, mod.begin() + hi);
+    std::vector<int> tgt;
+    for (int t = 0; t < QP; ++t)
+      if (t < lo || t >= hi) tgt.push_back(t);
+    std::vector<u64> dst;
+    for (int t : tgt) dst.push_back(mod[t]);
+    u64 *ej = ext.data() + (size_t)j * QP * N;
+    std::vector<const u64 *> xp;
+    for (int i = lo; i < hi; ++i) xp.push_back(x.data() + (size_t)i * N);
+    std::vector<u64 *> yp;
+    for (int t : tgt) yp.push_back(ej + (size_t)t * N);
+    bconv(xp.data(), src.data(), (int)src.size(), dst.data(), (int)dst.size(),
+          yp.data(), N, nthreads);
+    parallel_for((int)tgt.size(), nthreads, [&](int k) {
+      int t = tgt[k];
+      ntt_fwd(ej + (size_t)t * N, logn, mod[t], B.pw[row[t]]);
+    });
+    for (int i = lo; i < hi; ++i)
+      std::memcpy(ej + (size_t)i * N, d + (size_t)i * N, N * 8);
+  }
+  // Step 5: key multiply, accumulated over the digits.
+  std::vector<u64> acc((size_t)2 * QP * N);
+  parallel_for(2 * QP, nthreads, [&](int ct) {
+    int c = ct / QP, t = ct % QP;
+    u64 m = mod[t];
+    u64 *a = acc.data() + ((size_t)c * QP + t) * N;
+    for (u64 n = 0; n < N; ++n) {
+      u64 s = 0;
+      for (int j = 0; j < beta; ++j) {
+        u64 e = ext[((size_t)j * QP + t) * N + n];
+        u64 k = evk[(((size_t)j * 2 + c) * B.qp + row[t]) * N + n];
+        s = madd(s, mmul(e, k, m), m);
+      }
+      a[n] = s;
+    }
+  });
+  // Steps 6-8: ModDown of both polynomials.
+  for (int c = 0; c < 2; ++c)
+    moddown_at(B, level, acc.data() + (size_t)c * QP * N, out + (size_t)c * nq * N, nthreads);
+  if (ext_trace) std::memcpy(ext_trace, ext.data(), ext.size() * 8);
+  if (acc_trace) std::memcpy(acc_trace, acc.data(), acc.size() * 8);
+}
+
+// The automorphism sigma_k(a)(x) = a(x^k) of one coefficient-form limb mod m:
+// x^n goes to x^(nk mod 2N), and x^e = -x^(e-N) for e >= N (x^N = -1).
+void automorphism(const u64 *a, u64 *out, u64 N, u64 k, u64 m) {
+  for (u64 n = 0; n < N; ++n) {
+    u64 e = (n * k) % (2 * N);
+    if (e < N) out[e] = a[n];
+    else out[e - N] = a[n] ? m - a[n] : 0;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// ModDown of acc[QP][N] at the top level L (see moddown_at).
+int orc_moddown(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
+                int np, const u64 *acc, u64 *out, int nthreads) {
+  Basis B;
+  if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
+  moddown_at(B, L, acc, out, nthreads);
   return 0;
 }
 
@@ -299,64 +399,116 @@ int orc_keyswitch(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
                   u64 *acc_trace, int nthreads) {
   Basis B;
   if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
-  const u64 N = B.N;
-  const int QP = B.qp;
-  // Step 1: iNTT of the L+1 input limbs.
-  std::vector<u64> x((size_t)nq * N);
-  std::memcpy(x.data(), d, x.size() * 8);
-  parallel_for(nq, nthreads, [&](int i) {
-    ntt_inv(x.data() + (size_t)i * N, logn, q[i], B.pw[i]);
-  });
-  // Steps 2-4: per digit, ModUp = BConv onto (Q u P) \ D_j then NTT; the
-  // digit's own limbs are the input limbs themselves.
-  std::vector<u64> ext((size_t)B.beta * QP * N);
-  for (int j = 0; j < B.beta; ++j) {
-    int lo = digit_lo(B, j), hi = digit_hi(B, j);
-    std::vector<u64> src(B.mod.begin() + lo, B.mod.begin() + hi);
-    std::vector<int> tgt;
-    for (int t = 0; t < QP; ++t)
-      if (t < lo || t >= hi) tgt.push_back(t);
-    std::vector<u64> dst;
-    for (int t : tgt) dst.push_back(B.mod[t]);
-    u64 *ej = ext.data() + (size_t)j * QP * N;
-    std::vector<const u64 *> xp;
-    for (int i = lo; i < hi; ++i) xp.push_back(x.data() + (size_t)i * N);
-    std::vector<u64 *> yp;
-    for (int t : tgt) yp.push_back(ej + (size_t)t * N);
-    bconv(xp.data(), src.data(), (int)src.size(), dst.data(), (int)dst.size(),
-          yp.data(), N, nthreads);
-    parallel_for((int)tgt.size(), nthreads, [&](int k) {
-      int t = tgt[k];
-      ntt_fwd(ej + (size_t)t * N, logn, B.mod[t], B.pw[t]);
-    });
-    for (int i = lo; i < hi; ++i)
-      std::memcpy(ej + (size_t)i * N, d + (size_t)i * N, N * 8);
-  }
-  // Step 5: key multiply, accumulated over the digits.
-  std::vector<u64> acc((size_t)2 * QP * N);
-  parallel_for(2 * QP, nthreads, [&](int ct) {
-    int c = ct / QP, t = ct % QP;
-    u64 m = B.mod[t];
-    u64 *a = acc.data() + ((size_t)c * QP + t) * N;
-    for (u64 n = 0; n < N; ++n) {
-      u64 s = 0;
-      for (int j = 0; j < B.beta; ++j) {
-        u64 e = ext[((size_t)j * QP + t) * N + n];
-        u64 k = evk[(((size_t)j * 2 + c) * QP + t) * N + n];
-        s = madd(s, mmul(e, k, m), m);
-      }
-      a[n] = s;
-    }
-  });
-  // Steps 6-8: ModDown of both polynomials.
-  for (int c = 0; c < 2; ++c) {
-    int rc = orc_moddown(dnum, logn, L, q, nq, p, np, acc.data() + (size_t)c * QP * N,
-                         out + (size_t)c * nq * N, nthreads);
-    if (rc) return rc;
-  }
-  if (ext_trace) std::memcpy(ext_trace, ext.data(), ext.size() * 8);
-  if (acc_trace) std::memcpy(acc_trace, acc.data(), acc.size() * 8);
+  keyswitch_at(B, L, d, evk, out, ext_trace, acc_trace, nthreads);
   return 0;
+}
+
+// KeySwitch at level `level` (0..L) with the key of the level-L basis (see
+// keyswitch_at): d [level+1][N], out [2][level+1][N].
+int orc_keyswitch_level(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
+                        int np, int level, const u64 *d, const u64 *evk, u64 *out,
+                        int nthreads) {
+  Basis B;
+  if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
+  if (level < 0 || level > L) return -1;
+  keyswitch_at(B, level, d, evk, out, nullptr, nullptr, nthreads);
+  return 0;
+}
+
+// HMUL (Sec. II-A) at level `level`: ct1 = (x0, x1), ct2 = (y0, y1), each
+// [2][level+1][N] in NTT form over Q_level:
+//   out = (x0 y0, x0 y1 + x1 y0) + KS(x1 y1)   (no rescaling)
+// with KS under the relinearisation key rlk (s_from = s^2, s_to = s) of the level-L basis.
+int orc_hmul(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p, int np,
+             int level, const u64 *ct1, const u64 *ct2, const u64 *rlk, u64 *out,
+             int nthreads) {
+  Basis B;
+  if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
+  if (level < 0 || level > L) return -1;
+  const u64 N = B.N;
+  const size_t P = (size_t)(level + 1) * N;
+  std::vector<u64> d2(P), ks(2 * P);
+  std::vector<u64> t0(P), t1(P);
+  for (int i = 0; i <= level; ++i) {
+    const u64 m = q[i];
+    for (u64 n = 0; n < N; ++n) {
+      const size_t k = (size_t)i * N + n;
+      const u64 x0 = ct1[k], x1 = ct1[P + k], y0 = ct2[k], y1 = ct2[P + k];
+      t0[k] = mmul(x0, y0, m);
+      t1[k] = madd(mmul(x0, y1, m), mmul(x1, y0, m), m);
+      d2[k] = mmul(x1, y1, m);
+    }
+  }
+  keyswitch_at(B, level, d2.data(), rlk, ks.data(), nullptr, nullptr, nthreads);
+  for (int i = 0; i <= level; ++i)
+    for (u64 n = 0; n < N; ++n) {
+      const size_t k = (size_t)i * N + n;
+      out[k] = madd(t0[k], ks[k], q[i]);
+      out[P + k] = madd(t1[k], ks[P + k], q[i]);
+    }
+  return 0;
+}
+
+// Galois automorphism x -> x^k (k odd) of limbs a[count][N] in NTT form mod mods[c]:
+// inverse NTT, the coefficient map of `automorphism`, forward NTT.
+void orc_automorph_ntt(const u64 *a, u64 *out, const u64 *mods, int count, int logn, u64 k,
+                       int nthreads) {
+  const u64 N = (u64)1 << logn;
+  parallel_for(count, nthreads, [&](int c) {
+    auto pw = psi_powers(mods[c], logn);
+    std::vector<u64> x(a + (size_t)c * N, a + (size_t)(c + 1) * N);
+    ntt_inv(x.data(), logn, mods[c], pw);
+    automorphism(x.data(), out + (size_t)c * N, N, k, mods[c]);
+    ntt_fwd(out + (size_t)c * N, logn, mods[c], pw);
+  });
+}
+
+// HROT (Sec. II-A) at level `level`: ct = (c0, c1) [2][level+1][N] NTT form,
+//   out = (sigma_k(c0), 0) + KS(sigma_k(c1))
+// with KS under the rotation key rtk (s_from = sigma_k(s), s_to = s).
+int orc_hrot(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p, int np,
+             int level, const u64 *ct, u64 k, const u64 *rtk, u64 *out, int nthreads) {
+  Basis B;
+  if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
+  if (level < 0 || level > L || (k & 1) == 0 || k >= 2 * B.N) return -1;
+  const u64 N = B.N;
+  const size_t P = (size_t)(level + 1) * N;
+  std::vector<u64> r(2 * P), ks(2 * P);
+  orc_automorph_ntt(ct, r.data(), q, level + 1, logn, k, nthreads);
+  orc_automorph_ntt(ct + P, r.data() + P, q, level + 1, logn, k, nthreads);
+  keyswitch_at(B, level, r.data() + P, rtk, ks.data(), nullptr, nullptr, nthreads);
+  for (int i = 0; i <= level; ++i)
+    for (u64 n = 0; n < N; ++n) {
+      const size_t kk = (size_t)i * N + n;
+      out[kk] = madd(r[kk], ks[kk], q[i]);
+      out[P + kk] = ks[P + kk];
+    }
+  return 0;
+}
+
+// Product of two integer polynomials mod x^N + 1 (schoolbook, negacyclic wrap);
+// used for s^2 of a small key. |coefficients| stay far below 2^63 for keys.
+void orc_negacyclic_mul_i64(const int64_t *a, const int64_t *b, int64_t *out, int logn) {
+  const int64_t N = (int64_t)1 << logn;
+  for (int64_t n = 0; n < N; ++n) out[n] = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (a[i] == 0) continue;
+    for (int64_t j = 0; j < N; ++j) {
+      const int64_t v = a[i] * b[j];
+      if (i + j < N) out[i + j] += v;
+      else out[i + j - N] -= v;
+    }
+  }
+}
+
+// sigma_k of an integer polynomial (coefficient form).
+void orc_automorphism_i64(const int64_t *a, int64_t *out, int logn, u64 k) {
+  const u64 N = (u64)1 << logn;
+  for (u64 n = 0; n < N; ++n) {
+    u64 e = (n * k) % (2 * N);
+    if (e < N) out[e] = a[n];
+    else out[e - N] = -a[n];
+  }
 }
 
 // Evaluation-key generation from given randomness (the method's random draws
@@ -365,9 +517,23 @@ int orc_keyswitch(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
 // where g_j = 1 mod the primes of D_j and 0 mod every other prime, so
 // [P*g_j]_{q_i} = P mod q_i for i in D_j, else 0; and [P*g_j]_{p_k} = 0.
 //   s_from, s_to [N] ternary, a [beta][QP][N] NTT form, e [beta][N] small ints.
+int orc_keygen_poly(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
+                    int np, const int64_t *s_from, const int8_t *s_to, const u64 *a,
+                    const int32_t *e, u64 *evk, int nthreads);
+
 int orc_keygen(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
                int np, const int8_t *s_from, const int8_t *s_to, const u64 *a,
                const int32_t *e, u64 *evk, int nthreads) {
+  if (logn < 1 || logn > 17) return -1;
+  std::vector<int64_t> sf(s_from, s_from + ((size_t)1 << logn));
+  return orc_keygen_poly(dnum, logn, L, q, nq, p, np, sf.data(), s_to, a, e, evk, nthreads);
+}
+
+// As orc_keygen with s_from any integer polynomial (|s_from[n]| < 2^62): the
+// relinearisation key takes s_from = s^2, a rotation key s_from = sigma_k(s).
+int orc_keygen_poly(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
+                    int np, const int64_t *s_from, const int8_t *s_to, const u64 *a,
+                    const int32_t *e, u64 *evk, int nthreads) {
   Basis B;
   if (make_basis(B, dnum, logn, L, q, nq, p, np, nthreads)) return -1;
   const u64 N = B.N;
@@ -376,7 +542,7 @@ int orc_keygen(int dnum, int logn, int L, const u64 *q, int nq, const u64 *p,
     u64 m = B.mod[t];
     std::vector<u64> sf(N), st(N), ej(N);
     for (u64 n = 0; n < N; ++n) {
-      sf[n] = s_from[n] >= 0 ? (u64)s_from[n] : m - (u64)(-s_from[n]);
+      sf[n] = s_from[n] >= 0 ? (u64)s_from[n] % m : msub(0, (u64)(-s_from[n]) % m, m);
       st[n] = s_to[n] >= 0 ? (u64)s_to[n] : m - (u64)(-s_to[n]);
     }
     ntt_fwd(sf.data(), logn, m, B.pw[t]);

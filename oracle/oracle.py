@@ -62,6 +62,31 @@ def lib():
                 u64p, ctypes.c_int, u64p, ctypes.c_int,
                 ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int8), u64p,
                 ctypes.POINTER(ctypes.c_int32), u64p, ctypes.c_int]
+            l.orc_keygen_poly.restype = ctypes.c_int
+            l.orc_keygen_poly.argtypes = [ctypes.c_int] * 3 + [
+                u64p, ctypes.c_int, u64p, ctypes.c_int,
+                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int8), u64p,
+                ctypes.POINTER(ctypes.c_int32), u64p, ctypes.c_int]
+            l.orc_keyswitch_level.restype = ctypes.c_int
+            l.orc_keyswitch_level.argtypes = [ctypes.c_int] * 3 + [
+                u64p, ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int, u64p, u64p, u64p,
+                ctypes.c_int]
+            l.orc_hmul.restype = ctypes.c_int
+            l.orc_hmul.argtypes = [ctypes.c_int] * 3 + [
+                u64p, ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int, u64p, u64p, u64p, u64p,
+                ctypes.c_int]
+            l.orc_hrot.restype = ctypes.c_int
+            l.orc_hrot.argtypes = [ctypes.c_int] * 3 + [
+                u64p, ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_uint64,
+                u64p, u64p, ctypes.c_int]
+            l.orc_automorph_ntt.restype = None
+            l.orc_automorph_ntt.argtypes = [u64p, u64p, u64p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_uint64, ctypes.c_int]
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            l.orc_negacyclic_mul_i64.restype = None
+            l.orc_negacyclic_mul_i64.argtypes = [i64p, i64p, i64p, ctypes.c_int]
+            l.orc_automorphism_i64.restype = None
+            l.orc_automorphism_i64.argtypes = [i64p, i64p, ctypes.c_int, ctypes.c_uint64]
             _lib = l
     return _lib
 
@@ -78,6 +103,8 @@ def _p(a: np.ndarray):
         return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
     if a.dtype == np.int32:
         return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if a.dtype == np.int64:
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     raise TypeError(a.dtype)
 
 
@@ -162,3 +189,85 @@ def keygen(prm, s_from: np.ndarray, s_to: np.ndarray, a: np.ndarray, e: np.ndarr
     if rc:
         raise ValueError("orc_keygen: bad parameters")
     return evk
+
+
+def keygen_poly(prm, s_from: np.ndarray, s_to: np.ndarray, a: np.ndarray, e: np.ndarray,
+                nthreads: int | None = None) -> np.ndarray:
+    """keygen with s_from any int64 polynomial (s^2 for relinearisation, sigma_k(s) for
+    rotation)."""
+    q, p = _u64(prm.q), _u64(prm.p)
+    s_from = np.ascontiguousarray(s_from, dtype=np.int64)
+    s_to = np.ascontiguousarray(s_to, dtype=np.int8)
+    a = _u64(a)
+    e = np.ascontiguousarray(e, dtype=np.int32)
+    evk = np.zeros((prm.beta, 2, prm.QP, prm.N), dtype=np.uint64)
+    rc = lib().orc_keygen_poly(prm.dnum, prm.logn, prm.L, _p(q), len(q), _p(p), len(p),
+                               _p(s_from), _p(s_to), _p(a), _p(e), _p(evk),
+                               nthreads or default_threads())
+    if rc:
+        raise ValueError("orc_keygen_poly: bad parameters")
+    return evk
+
+
+def keyswitch_level(prm, level: int, d: np.ndarray, evk: np.ndarray,
+                    nthreads: int | None = None) -> np.ndarray:
+    """KeySwitch at level `level` of d[level+1][N] with the level-L key of prm."""
+    q, p = _u64(prm.q), _u64(prm.p)
+    d, evk = _u64(d), _u64(evk)
+    out = np.zeros((2, level + 1, prm.N), dtype=np.uint64)
+    rc = lib().orc_keyswitch_level(prm.dnum, prm.logn, prm.L, _p(q), len(q), _p(p), len(p),
+                                   level, _p(d), _p(evk), _p(out), nthreads or default_threads())
+    if rc:
+        raise ValueError("orc_keyswitch_level: bad parameters")
+    return out
+
+
+def hmul(prm, level: int, ct1: np.ndarray, ct2: np.ndarray, rlk: np.ndarray,
+         nthreads: int | None = None) -> np.ndarray:
+    """HMUL of ciphertexts [2][level+1][N] (NTT form) under the relinearisation key."""
+    q, p = _u64(prm.q), _u64(prm.p)
+    ct1, ct2, rlk = _u64(ct1), _u64(ct2), _u64(rlk)
+    out = np.zeros((2, level + 1, prm.N), dtype=np.uint64)
+    rc = lib().orc_hmul(prm.dnum, prm.logn, prm.L, _p(q), len(q), _p(p), len(p), level,
+                        _p(ct1), _p(ct2), _p(rlk), _p(out), nthreads or default_threads())
+    if rc:
+        raise ValueError("orc_hmul: bad parameters")
+    return out
+
+
+def hrot(prm, level: int, ct: np.ndarray, k: int, rtk: np.ndarray,
+         nthreads: int | None = None) -> np.ndarray:
+    """HROT of ct [2][level+1][N] (NTT form) by the Galois element k under rtk."""
+    q, p = _u64(prm.q), _u64(prm.p)
+    ct, rtk = _u64(ct), _u64(rtk)
+    out = np.zeros((2, level + 1, prm.N), dtype=np.uint64)
+    rc = lib().orc_hrot(prm.dnum, prm.logn, prm.L, _p(q), len(q), _p(p), len(p), level,
+                        _p(ct), k, _p(rtk), _p(out), nthreads or default_threads())
+    if rc:
+        raise ValueError("orc_hrot: bad parameters")
+    return out
+
+
+def automorph_ntt(a: np.ndarray, mods, logn: int, k: int,
+                  nthreads: int | None = None) -> np.ndarray:
+    """sigma_k of NTT-form limbs a[count][N] (through the coefficient domain)."""
+    a, mods = _u64(a), _u64(mods)
+    out = np.zeros_like(a)
+    lib().orc_automorph_ntt(_p(a), _p(out), _p(mods), len(mods), logn, k,
+                            nthreads or default_threads())
+    return out
+
+
+def negacyclic_mul_i64(a: np.ndarray, b: np.ndarray, logn: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    out = np.zeros(1 << logn, dtype=np.int64)
+    lib().orc_negacyclic_mul_i64(_p(a), _p(b), _p(out), logn)
+    return out
+
+
+def automorphism_i64(a: np.ndarray, logn: int, k: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    out = np.zeros(1 << logn, dtype=np.int64)
+    lib().orc_automorphism_i64(_p(a), _p(out), logn, k)
+    return out
