@@ -76,7 +76,8 @@ typedef struct {
 
 typedef struct {
   uint32_t N, alpha, beta, QP, nq, np;
-  size_t evk_words; /* beta*2*QP*N */
+  size_t evk_words; /* words of the key that a KeySwitch reads: beta*2*QP_top*N, the
+                       first beta digit pairs of the top level's key */
   size_t in_words;  /* (L+1)*N */
   size_t out_words; /* 2*(L+1)*N */
   size_t table_bytes; /* device bytes held by the context's constant tables */
@@ -84,6 +85,8 @@ typedef struct {
   int tuned_chunks;
   int tuned_batch;    /* batch size it was tuned for */
   float tuned_ms;     /* its time per KeySwitch in the tuning run */
+  int L;              /* level of this context (nq = L+1) */
+  int top_L;          /* level of the context whose keys it reads (= L unless a level view) */
 } ks_info;
 
 typedef struct ks_context ks_context;
@@ -99,6 +102,17 @@ void ks_context_destroy(ks_context *ctx);
 
 int ks_context_info(const ks_context *ctx, ks_info *info);
 
+/* A level view of `top` for KeySwitches at level `level` (0 <= level <= top's L):
+ * Q = q_0..q_level, the same alpha special primes, digits of alpha limbs
+ * (beta = ceil((level+1)/alpha)), and the top level's keys: a KeySwitch on the view
+ * reads the first beta digit pairs of a key made for `top`, with its limbs at the
+ * top level's positions. The level falls by one per multiplication and the best
+ * dataflow changes with it (Sec. II-A on levels; Sec. V on switching the dataflow
+ * as L changes within a workload): each view has its own plan and tuner state.
+ * The view owns its own tables; `top` may be destroyed first. Key generation on a
+ * view returns KS_EINVAL (keys are made at the top level). */
+int ks_context_at_level(const ks_context *top, int level, ks_context **out);
+
 /* Evaluation keys from given randomness (the random draws are inputs):
  *   evk_j = (b_j, a_j), b_j = -a_j*s_to + e_j + [P*g_j]*s_from over Q u P,
  * with g_j = 1 mod the primes of digit j, 0 mod every other prime.
@@ -110,6 +124,18 @@ int ks_context_info(const ks_context *ctx, ks_info *info);
 int ks_keygen(ks_context *ctx, const int8_t *s_from_dev, const int8_t *s_to_dev,
               const uint64_t *a_dev, const int32_t *e_dev, uint64_t *evk_dev,
               void *stream);
+
+/* Relinearisation key for HMUL (Sec. II-A): ks_keygen with s_from = s^2 (the
+ * square in the ring, formed on the device) and s_to = s. Same a, e and evk layout. */
+int ks_keygen_relin(ks_context *ctx, const int8_t *s_dev, const uint64_t *a_dev,
+                    const int32_t *e_dev, uint64_t *evk_dev, void *stream);
+
+/* Rotation key for HROT (Sec. II-A): ks_keygen with s_from = s(x^k), the Galois
+ * automorphism of s for the odd element k in [1, 2N) (rotation by r slots:
+ * k = 5^r mod 2N; conjugation: k = 2N - 1), and s_to = s. */
+int ks_keygen_galois(ks_context *ctx, const int8_t *s_dev, uint32_t galois_elt,
+                     const uint64_t *a_dev, const int32_t *e_dev, uint64_t *evk_dev,
+                     void *stream);
 
 /* Device bytes of scratch that ks_switch needs for (variant, chunks). */
 int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *bytes);
@@ -128,6 +154,39 @@ int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *by
 int ks_switch(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev,
               uint64_t *out_dev, int variant, int chunks, void *workspace_dev,
               size_t workspace_bytes, void *stream);
+
+/* Operations for ks_eval_workspace_size. */
+#define KS_OP_SWITCH 0
+#define KS_OP_HMUL 1
+#define KS_OP_HROT 2
+
+/* Device bytes of scratch that ks_switch / ks_hmul / ks_hrot need. */
+int ks_eval_workspace_size(const ks_context *ctx, int op, int variant, int chunks,
+                           size_t *bytes);
+
+/* HMUL (Sec. II-A): for ciphertexts ct1 = (x0, x1), ct2 = (y0, y1) over Q in NTT form,
+ *   out = (x0 y0, x0 y1 + x1 y0) + KS(x1 y1)
+ * with KS under the relinearisation key rlk (ks_keygen_relin). No rescaling.
+ *   ct1_dev, ct2_dev, out_dev  [2][L+1][N] uint64 device, canonical residues;
+ *   out may alias ct1 or ct2.  rlk_dev as evk_dev of ks_switch.
+ * The tensor product is one element-wise kernel (x1 y1 into the workspace); the
+ * final additions are folded into the KeySwitch's last kernel. variant, chunks,
+ * ws, ws_bytes and stream as for ks_switch (ws: ks_eval_workspace_size KS_OP_HMUL). */
+int ks_hmul(ks_context *ctx, const uint64_t *ct1_dev, const uint64_t *ct2_dev,
+            const uint64_t *rlk_dev, uint64_t *out_dev, int variant, int chunks, void *ws,
+            size_t ws_bytes, void *stream);
+
+/* HROT (Sec. II-A): rotation of ct = (c0, c1) by the Galois element k,
+ *   out = (sigma_k(c0), 0) + KS(sigma_k(c1)),  sigma_k(a)(x) = a(x^k),
+ * with KS under the rotation key rtk (ks_keygen_galois with the same k). The
+ * paper's formula swaps the roles of c0 and c1 relative to its HMUL; this follows
+ * the HMUL's convention (decryption c0 + c1 s). In the NTT domain sigma_k is a
+ * permutation of the slots (one gather kernel).
+ *   ct_dev, out_dev [2][L+1][N] uint64 device (out may alias ct); k odd in [1, 2N).
+ * Other arguments as for ks_hmul (ws: KS_OP_HROT). */
+int ks_hrot(ks_context *ctx, const uint64_t *ct_dev, uint32_t galois_elt,
+            const uint64_t *rtk_dev, uint64_t *out_dev, int variant, int chunks, void *ws,
+            size_t ws_bytes, void *stream);
 
 /* ks_switch with host buffers: copies d_host to the device, switches, copies the
  * result to out_host, and synchronizes `stream` before returning. Pinned host
@@ -177,7 +236,7 @@ typedef struct {
                                      gives up and ks_batch_status reports KS_ETIMEOUT */
 
 /* With KS_BATCH_PERSISTENT, one kernel launch runs every stage of every job: each
- * CTA of a co-resident grid claims work items (one tile of one stage of one job) in
+ * CTA of the grid claims work items (one tile of one stage of one job) in
  * stage-major order and waits, with a bounded wait (about 2 s of device time), until
  * the job's previous stage is complete. A wait that runs out sets a device error
  * word and every CTA returns; ks_batch_status then reports KS_ETIMEOUT. The

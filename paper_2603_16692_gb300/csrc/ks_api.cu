@@ -367,6 +367,140 @@ void forget_graphs(ks_context *c) {
   }
 }
 
+// A context for Q = q[0..L], P = p[0..alpha); `top` (or null) is the context whose
+// keys this one reads (a level view: same P and alpha, key layout of the top level).
+int create_context(int dnum, int logn, int L, const u64 *q, const u64 *p, int alpha,
+                   const ks_context *top, ks_context **out) {
+  const int nq = L + 1;
+  const int beta = (nq + alpha - 1) / alpha;
+  const int qp = nq + alpha;
+  if (qp > kMaxLimbs) return KS_EINVAL;
+  std::vector<u64> mods(q, q + nq);
+  mods.insert(mods.end(), p, p + alpha);
+  const u64 two_n = (u64)2 << logn;
+  u64 maxq = 0, maxp = 0, maxm = 0;
+  for (int t = 0; t < qp; ++t) {
+    const u64 m = mods[t];
+    if (m >= ((u64)1 << 62) || m % two_n != 1 || !ks::is_prime_u64(m)) return KS_EPRIME;
+    for (int k = 0; k < t; ++k)
+      if (mods[k] == m) return KS_EPRIME;
+    if (t < nq) maxq = std::max(maxq, m); else maxp = std::max(maxp, m);
+    maxm = std::max(maxm, m);
+  }
+  // Exact 128-bit sums must stay below m 2^64 for one REDC:
+  //   key multiply  beta * m^2 < m 2^64  <=>  beta * m < 2^64.
+  if ((unsigned __int128)beta * maxm >= ((unsigned __int128)1 << 64)) return KS_EINVAL;
+  ks_context *c = new (std::nothrow) ks_context();
+  if (!c) return KS_ENOMEM;
+  c->dnum = dnum;
+  c->logn = logn;
+  c->L = L;
+  c->alpha = alpha;
+  c->beta = beta;
+  c->nq = nq;
+  c->np = alpha;
+  c->qp = qp;
+  c->eqp = top ? top->qp : qp;
+  c->epb = top ? top->nq : nq;
+  c->top_L = top ? top->L : -1;
+  c->N = 1 << logn;
+  c->loga = ks::geo_loga(logn);
+  c->logb = logn - c->loga;
+  c->loggr = ks::geo_loggr(logn);
+  c->lt = ks::launch_table(logn, 3);
+  c->lt4 = ks::launch_table(logn, 2);
+  c->lt16 = ks::launch_table(logn, 4);
+  if (!c->lt || !c->lt4 || !c->lt16 || c->lt->prepare() != cudaSuccess ||
+      c->lt4->prepare() != cudaSuccess || c->lt16->prepare() != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return KS_ECUDA;
+  }
+  c->mods = mods;
+  // basis-conversion sums: run * max_source * m < m 2^64
+  c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
+  c->run_down = (int)std::min<u64>(1 << 20, (~(u64)0) / maxp);
+  cudaGetDevice(&c->device);
+  int rc = ks::build_tables(c);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return KS_OK;
+}
+
+// Key generation for a top-level context: lift, NTT every limb, optionally square
+// s_from (relinearisation key), combine.
+int keygen_impl(ks_context *c, const int8_t *s_from, const int8_t *s_to, unsigned kinv,
+                bool square, const uint64_t *a, const int32_t *e, uint64_t *evk, void *stream) {
+  if (!c || !s_from || !s_to || !a || !e || !evk) return KS_EINVAL;
+  if (c->top_L >= 0) return KS_EINVAL;  // keys are made at the top level
+  if (!aligned16(a) || !aligned16(evk)) return KS_EALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = c->N;
+  const int npoly = 2 + c->beta;
+  u64 *polys = nullptr;
+  if (cudaMalloc(&polys, (size_t)npoly * c->qp * N * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return KS_ENOMEM;
+  }
+  int rc = KS_OK;
+  do {
+    cudaError_t err = launch_keygen_lift(c, s_from, s_to, e, kinv, polys, s);
+    if (err) { rc = cuda_rc(err); break; }
+    // transform every lifted limb in place
+    JobSet js = {};
+    js.n = 1;
+    js.j[0].ws = polys;
+    WsOff wo = {};
+    Tasks lin = {};
+    lin.mode = TASK_LINEAR;
+    lin.n = npoly * c->qp;
+    err = c->lt->ntt_col(c, js, wo, lin, BUF_TMP, s);
+    if (!err) err = c->lt->ntt_row(c, js, wo, lin, BUF_TMP, s);
+    if (!err && square) err = launch_keygen_square(c, polys, s);
+    if (err) { rc = cuda_rc(err); break; }
+    err = launch_keygen_combine(c, polys, (const u64 *)a, (u64 *)evk, s);
+    if (err) { rc = cuda_rc(err); break; }
+    err = cudaStreamSynchronize(s);
+    if (err) rc = cuda_rc(err);
+  } while (0);
+  cudaFree(polys);
+  return rc;
+}
+
+// Galois elements are odd residues k in [1, 2N).
+bool galois_ok(const ks_context *c, uint32_t k) {
+  return (k & 1) && (u64)k < (u64)2 * c->N;
+}
+
+// Runs fn(base) on the caller's workspace (if given and large enough) or on the
+// context's internal arena (grown as needed; held under its lock while fn enqueues).
+template <class F>
+int with_workspace(ks_context *c, void *ws, size_t ws_bytes, size_t need, F fn) {
+  if (ws) {
+    if (ws_bytes < need) return KS_EINVAL;
+    return fn((u64 *)ws);
+  }
+  std::lock_guard<std::mutex> lk(c->ws_mu);
+  if (c->ws_bytes < need) {
+    if (c->ws) {
+      // a smaller arena may still be in use by earlier work on any stream
+      cudaDeviceSynchronize();
+      cudaFree(c->ws);
+      c->ws = nullptr;
+      c->ws_bytes = 0;
+    }
+    if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return KS_ENOMEM;
+    }
+    c->ws_bytes = need;
+  }
+  return fn((u64 *)c->ws);
+}
+
 // Device-time budget of one wait of the persistent batch kernel.
 constexpr unsigned long long kPersistWaitNs = 2000000000ull;
 
@@ -524,60 +658,19 @@ int ks_context_create(const ks_params *prm, ks_context **out) {
   if (logn < 1 || logn > 17 || dnum < 1 || L < 0 || L + 1 > 128) return KS_EINVAL;
   const int nq = L + 1;
   const int alpha = (nq + dnum - 1) / dnum;
-  const int beta = (nq + alpha - 1) / alpha;
   if ((int)prm->nq != nq || (int)prm->np != alpha) return KS_EINVAL;
-  const int qp = nq + alpha;
-  if (qp > kMaxLimbs) return KS_EINVAL;
-  std::vector<u64> mods(prm->q, prm->q + nq);
-  mods.insert(mods.end(), prm->p, prm->p + alpha);
-  const u64 two_n = (u64)2 << logn;
-  u64 maxq = 0, maxp = 0, maxm = 0;
-  for (int t = 0; t < qp; ++t) {
-    const u64 m = mods[t];
-    if (m >= ((u64)1 << 62) || m % two_n != 1 || !ks::is_prime_u64(m)) return KS_EPRIME;
-    for (int k = 0; k < t; ++k)
-      if (mods[k] == m) return KS_EPRIME;
-    if (t < nq) maxq = std::max(maxq, m); else maxp = std::max(maxp, m);
-    maxm = std::max(maxm, m);
-  }
-  // Exact 128-bit sums must stay below m 2^64 for one REDC:
-  //   key multiply  beta * m^2 < m 2^64  <=>  beta * m < 2^64.
-  if ((unsigned __int128)beta * maxm >= ((unsigned __int128)1 << 64)) return KS_EINVAL;
-  ks_context *c = new (std::nothrow) ks_context();
-  if (!c) return KS_ENOMEM;
-  c->dnum = dnum;
-  c->logn = logn;
-  c->L = L;
-  c->alpha = alpha;
-  c->beta = beta;
-  c->nq = nq;
-  c->np = alpha;
-  c->qp = qp;
-  c->N = 1 << logn;
-  c->loga = ks::geo_loga(logn);
-  c->logb = logn - c->loga;
-  c->loggr = ks::geo_loggr(logn);
-  c->lt = ks::launch_table(logn, 3);
-  c->lt4 = ks::launch_table(logn, 2);
-  c->lt16 = ks::launch_table(logn, 4);
-  if (!c->lt || !c->lt4 || !c->lt16 || c->lt->prepare() != cudaSuccess ||
-      c->lt4->prepare() != cudaSuccess || c->lt16->prepare() != cudaSuccess) {
-    cudaGetLastError();
-    delete c;
-    return KS_ECUDA;
-  }
-  c->mods = mods;
-  // basis-conversion sums: run * max_source * m < m 2^64
-  c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
-  c->run_down = (int)std::min<u64>(1 << 20, (~(u64)0) / maxp);
-  cudaGetDevice(&c->device);
-  int rc = ks::build_tables(c);
-  if (rc) {
-    delete c;
-    return rc;
-  }
-  *out = c;
-  return KS_OK;
+  return create_context(dnum, logn, L, (const u64 *)prm->q, (const u64 *)prm->p, alpha, nullptr,
+                        out);
+}
+
+int ks_context_at_level(const ks_context *top, int level, ks_context **out) {
+  if (!top || !out) return KS_EINVAL;
+  *out = nullptr;
+  if (top->top_L >= 0) return KS_EINVAL;  // a view of a view: take the top context
+  if (level < 0 || level > top->L) return KS_EINVAL;
+  std::vector<u64> q(top->mods.begin(), top->mods.begin() + level + 1);
+  std::vector<u64> p(top->mods.begin() + top->nq, top->mods.end());
+  return create_context(top->dnum, top->logn, level, q.data(), p.data(), top->alpha, top, out);
 }
 
 void ks_context_destroy(ks_context *c) {
@@ -597,7 +690,9 @@ int ks_context_info(const ks_context *c, ks_info *info) {
   info->QP = c->qp;
   info->nq = c->nq;
   info->np = c->np;
-  info->evk_words = (size_t)c->beta * 2 * c->qp * c->N;
+  info->evk_words = (size_t)c->beta * 2 * c->eqp * c->N;
+  info->L = c->L;
+  info->top_L = c->top_L < 0 ? c->L : c->top_L;
   info->in_words = (size_t)c->nq * c->N;
   info->out_words = (size_t)2 * c->nq * c->N;
   info->table_bytes = c->table_bytes;
@@ -625,35 +720,16 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
   Plan pl;
   int rc = make_plan(c, variant, chunks, &pl);
   if (rc) return rc;
-  const size_t need = pl.total * 8;
   cudaStream_t s = (cudaStream_t)stream;
-  JobSet js;
-  js.n = 1;
-  js.j[0].d = (const u64 *)d;
-  js.j[0].evk = (const u64 *)evk;
-  js.j[0].out = (u64 *)out;
-  if (ws) {
-    if (ws_bytes < need) return KS_EINVAL;
-    js.j[0].ws = (u64 *)ws;
+  return with_workspace(c, ws, ws_bytes, pl.total * 8, [&](u64 *base) {
+    JobSet js = {};
+    js.n = 1;
+    js.j[0].d = (const u64 *)d;
+    js.j[0].evk = (const u64 *)evk;
+    js.j[0].out = (u64 *)out;
+    js.j[0].ws = base;
     return run_plan(c, pl, js, s);
-  }
-  std::lock_guard<std::mutex> lk(c->ws_mu);
-  if (c->ws_bytes < need) {
-    if (c->ws) {
-      // a smaller arena may still be in use by earlier work on any stream
-      cudaDeviceSynchronize();
-      cudaFree(c->ws);
-      c->ws = nullptr;
-      c->ws_bytes = 0;
-    }
-    if (cudaMalloc(&c->ws, need) != cudaSuccess) {
-      cudaGetLastError();
-      return KS_ENOMEM;
-    }
-    c->ws_bytes = need;
-  }
-  js.j[0].ws = (u64 *)c->ws;
-  return run_plan(c, pl, js, s);
+  });
 }
 
 int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
@@ -689,38 +765,82 @@ int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, u
 
 int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uint64_t *a,
               const int32_t *e, uint64_t *evk, void *stream) {
-  if (!c || !s_from || !s_to || !a || !e || !evk) return KS_EINVAL;
-  if (!aligned16(a) || !aligned16(evk)) return KS_EALIGN;
+  return keygen_impl(c, s_from, s_to, 0, false, a, e, evk, stream);
+}
+
+int ks_keygen_relin(ks_context *c, const int8_t *s, const uint64_t *a, const int32_t *e,
+                    uint64_t *evk, void *stream) {
+  return keygen_impl(c, s, s, 0, true, a, e, evk, stream);
+}
+
+int ks_keygen_galois(ks_context *c, const int8_t *s, uint32_t galois_elt, const uint64_t *a,
+                     const int32_t *e, uint64_t *evk, void *stream) {
+  if (!c || !galois_ok(c, galois_elt)) return KS_EINVAL;
+  const u64 two_n = (u64)2 * c->N;
+  // k^-1 mod 2N by Newton iteration (k odd): x <- x (2 - k x) doubles the correct bits
+  u64 inv = galois_elt;
+  for (int it = 0; it < 5; ++it) inv = (inv * (2 - (u64)galois_elt * inv)) & (two_n - 1);
+  return keygen_impl(c, s, s, (unsigned)inv, false, a, e, evk, stream);
+}
+
+int ks_eval_workspace_size(const ks_context *c, int op, int variant, int chunks, size_t *bytes) {
+  if (!c || !bytes || op < KS_OP_SWITCH || op > KS_OP_HROT) return KS_EINVAL;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
+  if (rc) return rc;
+  *bytes = (pl.total + (size_t)op * c->nq * c->N) * 8;
+  return KS_OK;
+}
+
+int ks_hmul(ks_context *c, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *rlk,
+            uint64_t *out, int variant, int chunks, void *ws, size_t ws_bytes, void *stream) {
+  if (!c || !ct1 || !ct2 || !rlk || !out) return KS_EINVAL;
+  if (!aligned16(ct1) || !aligned16(ct2) || !aligned16(rlk) || !aligned16(out) ||
+      (ws && !aligned16(ws)))
+    return KS_EALIGN;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
+  if (rc) return rc;
+  const size_t extra = (size_t)c->nq * c->N;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t N = c->N;
-  const int npoly = 2 + c->beta;
-  u64 *polys = nullptr;
-  if (cudaMalloc(&polys, (size_t)npoly * c->qp * N * 8) != cudaSuccess) {
-    cudaGetLastError();
-    return KS_ENOMEM;
-  }
-  int rc = KS_OK;
-  do {
-    cudaError_t err = launch_keygen_lift(c, s_from, s_to, e, polys, s);
-    if (err) { rc = cuda_rc(err); break; }
-    // transform every lifted limb in place
+  return with_workspace(c, ws, ws_bytes, (pl.total + extra) * 8, [&](u64 *base) {
+    u64 *d2 = base + pl.total;
+    KS_TRY(launch_tensor(c, (const u64 *)ct1, (const u64 *)ct2, (u64 *)out, d2, s));
     JobSet js = {};
     js.n = 1;
-    js.j[0].ws = polys;
-    WsOff wo = {};
-    Tasks lin = {};
-    lin.mode = TASK_LINEAR;
-    lin.n = npoly * c->qp;
-    err = c->lt->ntt_col(c, js, wo, lin, BUF_TMP, s);
-    if (!err) err = c->lt->ntt_row(c, js, wo, lin, BUF_TMP, s);
-    if (err) { rc = cuda_rc(err); break; }
-    err = launch_keygen_combine(c, polys, (const u64 *)a, (u64 *)evk, s);
-    if (err) { rc = cuda_rc(err); break; }
-    err = cudaStreamSynchronize(s);
-    if (err) rc = cuda_rc(err);
-  } while (0);
-  cudaFree(polys);
-  return rc;
+    js.j[0].d = d2;
+    js.j[0].evk = (const u64 *)rlk;
+    js.j[0].out = (u64 *)out;
+    js.j[0].ws = base;
+    js.j[0].add = (const u64 *)out;
+    js.j[0].addmask = 3;
+    return run_plan(c, pl, js, s);
+  });
+}
+
+int ks_hrot(ks_context *c, const uint64_t *ct, uint32_t galois_elt, const uint64_t *rtk,
+            uint64_t *out, int variant, int chunks, void *ws, size_t ws_bytes, void *stream) {
+  if (!c || !ct || !rtk || !out || !galois_ok(c, galois_elt)) return KS_EINVAL;
+  if (!aligned16(ct) || !aligned16(rtk) || !aligned16(out) || (ws && !aligned16(ws)))
+    return KS_EALIGN;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
+  if (rc) return rc;
+  const size_t extra = (size_t)2 * c->nq * c->N;
+  cudaStream_t s = (cudaStream_t)stream;
+  return with_workspace(c, ws, ws_bytes, (pl.total + extra) * 8, [&](u64 *base) {
+    u64 *y0 = base + pl.total, *y1 = y0 + (size_t)c->nq * c->N;
+    KS_TRY(launch_automorph(c, (const u64 *)ct, galois_elt, y0, y1, s));
+    JobSet js = {};
+    js.n = 1;
+    js.j[0].d = y1;
+    js.j[0].evk = (const u64 *)rtk;
+    js.j[0].out = (u64 *)out;
+    js.j[0].ws = base;
+    js.j[0].add = y0;  // out_0 += sigma(ct_0); out_1 is the KeySwitch's alone
+    js.j[0].addmask = 1;
+    return run_plan(c, pl, js, s);
+  });
 }
 
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
@@ -837,7 +957,7 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       const Plan &pl = plans[g];
       const std::vector<int> &mem = members[g];
       for (size_t k0 = 0; k0 < mem.size() && rc == KS_OK; k0 += kMaxBatch) {
-        JobSet js;
+        JobSet js = {};
         js.n = (int)std::min<size_t>(kMaxBatch, mem.size() - k0);
         for (int q = 0; q < js.n; ++q) {
           const ks_job &jb = jobs[mem[k0 + q]];
@@ -907,7 +1027,7 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
       const int v = b[0] | radix[ri];
       Plan pl;
       if (make_plan(c, v, b[1], &pl) != KS_OK) continue;
-      JobSet js;
+      JobSet js = {};
       js.n = batch;
       for (int q = 0; q < batch; ++q) {
         char *base = (char *)mem + q * (ws_max + out_b);
@@ -940,7 +1060,7 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
     // leave the caller's out with the switched result (every candidate computes it)
     Plan pl;
     make_plan(c, best_v, best_c, &pl);
-    JobSet js;
+    JobSet js = {};
     js.n = 1;
     js.j[0].d = (const u64 *)d;
     js.j[0].evk = (const u64 *)evk;

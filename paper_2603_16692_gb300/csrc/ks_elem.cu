@@ -85,8 +85,8 @@ __global__ void k_keymult(EArgs a, JobSet js, WsOff wo, Tasks tk) {
         y = csub(shoup(__ldg(jp.d + (size_t)t * N + n), mi.r1, mi.r1s, mi.m), mi.m);
       else
         y = __ldg(tmp + (size_t)(j * tk.sm.sj + t * tk.sm.st + tk.sm.base) * N + n);
-      mac128(s0, y, __ldg(jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + n));
-      mac128(s1, y, __ldg(jp.evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + n));
+      mac128(s0, y, __ldg(jp.evk + kern::evk_off(a, j, 0, t) + n));
+      mac128(s1, y, __ldg(jp.evk + kern::evk_off(a, j, 1, t) + n));
     }
     u64 r0v = csub(redc(s0, mi.m, mi.minv), mi.m);
     u64 r1v = csub(redc(s1, mi.m, mi.minv), mi.m);
@@ -111,16 +111,20 @@ __global__ void k_moddown_scale(EArgs a, JobSet js, WsOff wo, Tasks tk) {
   const size_t N = a.N;
   const u64 *z = jp.ws + wo.tmp2 + (size_t)task_slot(w) * N;
   const u64 *ac = jp.ws + wo.acc + ((size_t)c * a.qp + i) * N;
-  u64 *o = jp.out + ((size_t)c * a.nq + i) * N;
+  const size_t ob = ((size_t)c * a.nq + i) * N;
+  u64 *o = jp.out + ob;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
        n += (size_t)gridDim.x * blockDim.x)
-    o[n] = csub(shoup(__ldg(ac + n) + m - __ldg(z + n), pv.x, pv.y, m), m);
+    o[n] = kern::out_word(jp, c, ob + n,
+                          csub(shoup(__ldg(ac + n) + m - __ldg(z + n), pv.x, pv.y, m), m), m);
 }
 
 // polys [2 + beta][QP][N]: 0 = s_from, 1 = s_to, 2 + j = e_j, as residues mod each prime.
+// With kinv != 0, s_from is replaced by sigma_k(s_from)(x) = s_from(x^k): output
+// coefficient n takes source n1 = n k^-1 mod 2N, negated when n1 >= N (x^N = -1).
 __global__ void k_keygen_lift(EArgs a, const int8_t *__restrict__ sf,
                               const int8_t *__restrict__ st, const int32_t *__restrict__ e,
-                              u64 *polys) {
+                              unsigned kinv, u64 *polys) {
   const int poly = blockIdx.z, t = blockIdx.y;
   const u64 m = a.tab.mod[t].m;
   const size_t N = a.N;
@@ -128,7 +132,10 @@ __global__ void k_keygen_lift(EArgs a, const int8_t *__restrict__ sf,
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
        n += (size_t)gridDim.x * blockDim.x) {
     long long x;
-    if (poly == 0)
+    if (poly == 0 && kinv) {
+      const size_t n1 = (n * kinv) & (2 * N - 1);
+      x = n1 < N ? sf[n1] : -(long long)sf[n1 - N];
+    } else if (poly == 0)
       x = sf[n];
     else if (poly == 1)
       x = st[n];
@@ -176,6 +183,64 @@ __global__ void k_keygen_combine(EArgs a, const u64 *__restrict__ polys,
   }
 }
 
+__global__ void k_keygen_square(EArgs a, u64 *polys) {
+  const int t = blockIdx.y;
+  const ModInfo mi = a.tab.mod[t];
+  const size_t N = a.N;
+  u64 *o = polys + (size_t)t * N;  // poly 0 = s_from
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x)
+    o[n] = mulmod_full(o[n], o[n], mi);
+}
+
+// x*y + z*w mod m for canonical inputs: the exact 128-bit sum (< 2 m^2 < m 2^64) is
+// reduced once, then the 2^-64 of REDC is undone by a second REDC against 2^128 mod m.
+__device__ __forceinline__ u64 mulmod2_full(u64 x, u64 y, u64 z, u64 w, const ModInfo &mi) {
+  U128 p = {0, 0};
+  mac128(p, x, y);
+  mac128(p, z, w);
+  const u64 t = csub(redc(p, mi.m, mi.minv), mi.m);
+  U128 p2 = {0, 0};
+  mac128(p2, t, mi.r2);
+  return csub(redc(p2, mi.m, mi.minv), mi.m);
+}
+
+// HMUL tensor product, limb i = blockIdx.y. Each thread reads its four words before
+// it writes, so out may alias x or y.
+__global__ void k_tensor(EArgs a, const u64 *x, const u64 *y, u64 *out, u64 *d2) {
+  const int i = blockIdx.y;
+  const ModInfo mi = a.tab.mod[i];
+  const size_t N = a.N, P = (size_t)a.nq * N, off = (size_t)i * N;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const u64 x0 = x[off + n], x1 = x[P + off + n], y0 = y[off + n], y1 = y[P + off + n];
+    const u64 r0 = mulmod_full(x0, y0, mi);
+    const u64 r1 = mulmod2_full(x0, y1, x1, y0, mi);
+    const u64 r2 = mulmod_full(x1, y1, mi);
+    out[off + n] = r0;
+    out[P + off + n] = r1;
+    d2[off + n] = r2;
+  }
+}
+
+// Galois automorphism in the NTT domain. Slot j holds a(w_j), w_j = psi^(2 brv(j) + 1);
+// sigma_k(a)(w_j) = a(w_j^k) = a(w_j') with 2 brv(j') + 1 = (2 brv(j) + 1) k mod 2N,
+// so the automorphism is the gather y[j] = x[j']. Limb i = blockIdx.y, c = blockIdx.z.
+__global__ void k_automorph(EArgs a, int logn, const u64 *__restrict__ ct, unsigned k,
+                            u64 *y0, u64 *y1) {
+  const int i = blockIdx.y, c = blockIdx.z;
+  const size_t N = a.N;
+  const u64 *x = ct + ((size_t)c * a.nq + i) * N;
+  u64 *y = (c == 0 ? y0 : y1) + (size_t)i * N;
+  const unsigned mask2n = (unsigned)(2 * N - 1), sh = 32 - logn;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const unsigned e = (2u * (__brev((unsigned)n) >> sh) + 1u) * k & mask2n;
+    const unsigned src = __brev((e - 1u) >> 1) >> sh;
+    y[n] = __ldg(x + src);
+  }
+}
+
 int ew_blocks(size_t N) {
   const size_t b = (N + 1023) / 1024;
   return (int)(b < 1 ? 1 : b);
@@ -213,9 +278,26 @@ cudaError_t launch_moddown_scale(const ks_context *c, const JobSet &js, const Ws
 }
 
 cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
-                               const int32_t *e, u64 *polys, cudaStream_t s) {
+                               const int32_t *e, unsigned kinv, u64 *polys, cudaStream_t s) {
   k_keygen_lift<<<dim3(ew_blocks(c->N), c->qp, 2 + c->beta), 256, 0, s>>>(eargs(c), sf, st, e,
-                                                                          polys);
+                                                                          kinv, polys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keygen_square(const ks_context *c, u64 *polys, cudaStream_t s) {
+  k_keygen_square<<<dim3(ew_blocks(c->N), c->qp), 256, 0, s>>>(eargs(c), polys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor(const ks_context *c, const u64 *x, const u64 *y, u64 *out, u64 *d2,
+                          cudaStream_t s) {
+  k_tensor<<<dim3(ew_blocks(c->N), c->nq), 256, 0, s>>>(eargs(c), x, y, out, d2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_automorph(const ks_context *c, const u64 *ct, unsigned k, u64 *y0, u64 *y1,
+                             cudaStream_t s) {
+  k_automorph<<<dim3(ew_blocks(c->N), c->nq, 2), 256, 0, s>>>(eargs(c), c->logn, ct, k, y0, y1);
   return cudaGetLastError();
 }
 

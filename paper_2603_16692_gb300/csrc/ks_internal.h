@@ -61,9 +61,11 @@ struct Tasks {
 constexpr int kMaxBatch = 16;
 struct JobPtr {
   const u64 *d;    // [L+1][N] input
-  const u64 *evk;  // [beta][2][QP][N]
+  const u64 *evk;  // [beta][2][EQP][N] (EQP = QP, or the top level's QP for a level view)
   u64 *out;        // [2][L+1][N]
   u64 *ws;         // this job's workspace
+  const u64 *add;  // optional addend [2][L+1][N] (may alias out): out_c += add_c when
+  int addmask;     // bit c of addmask is set (HMUL / HROT epilogues); 0 = plain store
 };
 struct JobSet {
   int n;
@@ -97,6 +99,11 @@ struct LaunchTable;
 
 struct ks_context {
   int dnum, logn, L, alpha, beta, nq, np, qp;
+  // Key layout: evk[j][c][t'] with t' = t for Q-limbs, eqp_base + (t - nq) for P-limbs,
+  // limb stride eqp. A top-level context has eqp = qp, epb = nq; a level view (KeySwitch
+  // at level l < L with the top level's keys) keeps the top level's layout.
+  int eqp = 0, epb = 0;
+  int top_L = -1;  // level of the context whose keys this one uses (-1: itself)
   int N;
   int loga, logb, loggr;  // two-pass split N = 2^loga * 2^logb; rows per row tile 2^loggr
   const ks::LaunchTable *lt = nullptr;   // radix-8 kernels
@@ -189,9 +196,20 @@ int persist_launch(void *dev, int njobs, int nwork, size_t state_offset,
                    unsigned long long limit_ns, bool stall, cudaStream_t s);
 int persist_status(const void *dev, size_t state_offset, cudaStream_t s);
 
+// Key generation: lift s_from (optionally through the automorphism x -> x^k, given
+// by kinv = k^-1 mod 2N; kinv 0 = identity), s_to and the errors to residues.
 cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
-                               const int32_t *e, u64 *polys, cudaStream_t s);
+                               const int32_t *e, unsigned kinv, u64 *polys, cudaStream_t s);
+// Square the NTT-form s_from residues in place (relinearisation key: s_from = s^2).
+cudaError_t launch_keygen_square(const ks_context *c, u64 *polys, cudaStream_t s);
 cudaError_t launch_keygen_combine(const ks_context *c, const u64 *polys, const u64 *a,
                                   u64 *evk, cudaStream_t s);
+// HMUL tensor product over Q (NTT form): out_0 = x0 y0, out_1 = x0 y1 + x1 y0, d2 = x1 y1.
+cudaError_t launch_tensor(const ks_context *c, const u64 *x, const u64 *y, u64 *out, u64 *d2,
+                          cudaStream_t s);
+// Galois automorphism x -> x^k of both polynomials of ct (NTT form, bit-reversed slots):
+// y0 = sigma(ct_0), y1 = sigma(ct_1).
+cudaError_t launch_automorph(const ks_context *c, const u64 *ct, unsigned k, u64 *y0, u64 *y1,
+                             cudaStream_t s);
 
 }  // namespace ks

@@ -24,7 +24,20 @@ struct KArgs {
   Tables tab;
   int N, nq, np, qp, alpha, beta;
   int run_up, run_down;
+  int eqp, epb;  // key layout (see ks_context)
 };
+
+// Word offset of evk[j][c][limb t] (t in the context's Q u P numbering).
+__host__ __device__ __forceinline__ size_t evk_off(const KArgs &a, int j, int c, int t) {
+  const int tt = t < a.nq ? t : a.epb + (t - a.nq);
+  return ((size_t)(j * 2 + c) * a.eqp + tt) * (size_t)a.N;
+}
+
+// The epilogue store of an output word: out = r, or r + addend (mod m).
+__device__ __forceinline__ u64 out_word(const JobPtr &jp, int c, size_t idx, u64 r, u64 m) {
+  if ((jp.addmask >> c) & 1) r = addmod(r, jp.add[idx], m);
+  return r;
+}
 
 inline KArgs make_args(const ks_context *c) {
   KArgs a;
@@ -37,6 +50,8 @@ inline KArgs make_args(const ks_context *c) {
   a.beta = c->beta;
   a.run_up = c->run_up;
   a.run_down = c->run_down;
+  a.eqp = c->eqp;
+  a.epb = c->epb;
   return a;
 }
 
@@ -506,8 +521,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
   constexpr unsigned TB = GT::TILE * 8;
   auto prefetch_digit = [&](int j) {
     if (threadIdx.x != 0 || j >= tk.j1) return;
-    prefetch_l2(jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + off0, TB);
-    prefetch_l2(jp.evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + off0, TB);
+    prefetch_l2(jp.evk + evk_off(a, j, 0, t) + off0, TB);
+    prefetch_l2(jp.evk + evk_off(a, j, 1, t) + off0, TB);
     const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
     if (t >= lo && t < hi)
       prefetch_l2(jp.d + (size_t)t * N + off0, TB);
@@ -525,8 +540,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
     prefetch_digit(j + 1);
     const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
     const bool own = t >= lo && t < hi;
-    const u64 *e0 = jp.evk + ((size_t)(j * 2 + 0) * a.qp + t) * N + off0;
-    const u64 *e1 = jp.evk + ((size_t)(j * 2 + 1) * a.qp + t) * N + off0;
+    const u64 *e0 = jp.evk + evk_off(a, j, 0, t) + off0;
+    const u64 *e1 = jp.evk + evk_off(a, j, 1, t) + off0;
     if (own) {
       const u64 *dt = jp.d + (size_t)t * N + off0;
 #pragma unroll
@@ -621,14 +636,27 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
     __syncthreads();
     tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
     const u64 *ac = acc + ((size_t)c * a.qp + i) * N + off0;
-    u64 *o = jp.out + ((size_t)c * a.nq + i) * N + off0;
+    const size_t ob = ((size_t)c * a.nq + i) * N + off0;
+    u64 *o = jp.out + ob;
+    if ((jp.addmask >> c) & 1) {
+      const u64 *ad = jp.add + ob;
 #pragma unroll
-    for (int k = 0; k < GT::EPT; ++k) {
-      const int e = threadIdx.x + k * GT::NT;
-      if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
-      const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
-      const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
-      o[e] = csub(shoup(ac[e] + m - z, pv.x, pv.y, m), m);
+      for (int k = 0; k < GT::EPT; ++k) {
+        const int e = threadIdx.x + k * GT::NT;
+        if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
+        const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
+        const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
+        o[e] = addmod(csub(shoup(ac[e] + m - z, pv.x, pv.y, m), m), ad[e], m);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < GT::EPT; ++k) {
+        const int e = threadIdx.x + k * GT::NT;
+        if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
+        const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
+        const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
+        o[e] = csub(shoup(ac[e] + m - z, pv.x, pv.y, m), m);
+      }
     }
     __syncthreads();
   }

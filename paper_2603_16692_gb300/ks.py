@@ -44,7 +44,8 @@ class ks_info(ctypes.Structure):
                 ("evk_words", ctypes.c_size_t), ("in_words", ctypes.c_size_t),
                 ("out_words", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t),
                 ("tuned_variant", ctypes.c_int), ("tuned_chunks", ctypes.c_int),
-                ("tuned_batch", ctypes.c_int), ("tuned_ms", ctypes.c_float)]
+                ("tuned_batch", ctypes.c_int), ("tuned_ms", ctypes.c_float),
+                ("L", ctypes.c_int), ("top_L", ctypes.c_int)]
 
 
 class ks_kernel_stat(ctypes.Structure):
@@ -66,7 +67,9 @@ SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_key
            "ks_workspace_size", "ks_switch", "ks_switch_host", "ks_switch_batch",
            "ks_sync_status", "ks_strerror", "ks_cuda_error_string", "ks_profile_begin",
            "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune",
-           "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status")
+           "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status",
+           "ks_context_at_level", "ks_keygen_relin", "ks_keygen_galois",
+           "ks_eval_workspace_size", "ks_hmul", "ks_hrot")
 
 
 def lib_path() -> str:
@@ -99,6 +102,12 @@ def load(build: bool = True):
         l.ks_mlp_train.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, ctypes.c_float, i, vp, vp]
         l.ks_sync_status.argtypes = [vp, vp]
         l.ks_batch_status.argtypes = [vp]
+        l.ks_context_at_level.argtypes = [vp, i, ctypes.POINTER(vp)]
+        l.ks_keygen_relin.argtypes = [vp, vp, vp, vp, vp, vp]
+        l.ks_keygen_galois.argtypes = [vp, vp, ctypes.c_uint32, vp, vp, vp, vp]
+        l.ks_eval_workspace_size.argtypes = [vp, i, i, i, ctypes.POINTER(sz)]
+        l.ks_hmul.argtypes = [vp, vp, vp, vp, vp, i, i, vp, sz, vp]
+        l.ks_hrot.argtypes = [vp, vp, ctypes.c_uint32, vp, vp, i, i, vp, sz, vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
         l.ks_noalloc_scratch_bytes.argtypes = []
@@ -154,6 +163,13 @@ def ks_context_create(dnum: int, log2n: int, L: int, q, p) -> int:
     return h.value
 
 
+def ks_context_at_level(ctx: int, level: int) -> int:
+    """Handle of a level view of ctx (KeySwitch at `level` with ctx's keys)."""
+    h = ctypes.c_void_p()
+    _check(load().ks_context_at_level(ctx, level, ctypes.byref(h)), "ks_context_at_level")
+    return h.value
+
+
 def ks_context_destroy(ctx: int):
     load().ks_context_destroy(ctx)
 
@@ -167,6 +183,47 @@ def ks_context_info(ctx: int) -> dict:
 def ks_keygen(ctx: int, s_from, s_to, a, e, evk, stream=None):
     _check(load().ks_keygen(ctx, _ptr(s_from), _ptr(s_to), _ptr(a), _ptr(e), _ptr(evk),
                             _stream(stream)), "ks_keygen")
+
+
+def ks_keygen_relin(ctx: int, s, a, e, evk, stream=None):
+    _check(load().ks_keygen_relin(ctx, _ptr(s), _ptr(a), _ptr(e), _ptr(evk), _stream(stream)),
+           "ks_keygen_relin")
+
+
+def ks_keygen_galois(ctx: int, s, galois_elt: int, a, e, evk, stream=None):
+    _check(load().ks_keygen_galois(ctx, _ptr(s), galois_elt, _ptr(a), _ptr(e), _ptr(evk),
+                                   _stream(stream)), "ks_keygen_galois")
+
+
+KS_OP_SWITCH, KS_OP_HMUL, KS_OP_HROT = 0, 1, 2
+
+
+def ks_eval_workspace_size(ctx: int, op: int, variant: int = 0, chunks: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(load().ks_eval_workspace_size(ctx, op, variant, chunks, ctypes.byref(n)),
+           "ks_eval_workspace_size")
+    return n.value
+
+
+def _ws(workspace):
+    return workspace.numel() * workspace.element_size() if workspace is not None else 0
+
+
+def ks_hmul(ctx: int, ct1, ct2, rlk, out, variant: int = 0, chunks: int = 0, workspace=None,
+            stream=None):
+    _check(load().ks_hmul(ctx, _ptr(ct1), _ptr(ct2), _ptr(rlk), _ptr(out), variant, chunks,
+                          _ptr(workspace), _ws(workspace), _stream(stream)), "ks_hmul")
+
+
+def ks_hrot(ctx: int, ct, galois_elt: int, rtk, out, variant: int = 0, chunks: int = 0,
+            workspace=None, stream=None):
+    _check(load().ks_hrot(ctx, _ptr(ct), galois_elt, _ptr(rtk), _ptr(out), variant, chunks,
+                          _ptr(workspace), _ws(workspace), _stream(stream)), "ks_hrot")
+
+
+def galois_elt(r: int, N: int) -> int:
+    """Galois element of a rotation by r slots (5^r mod 2N); r = None: conjugation."""
+    return 2 * N - 1 if r is None else pow(5, r % (N // 2), 2 * N)
 
 
 def ks_workspace_size(ctx: int, variant: int, chunks: int = 0) -> int:
@@ -287,12 +344,19 @@ def ks_batch_status(stream=None) -> int:
 
 
 class Context:
-    """Owns a ks_context for one parameter set (workload.Params)."""
+    """Owns a ks_context for one parameter set (workload.Params), or a level view of
+    another Context (``Context.at_level``)."""
 
-    def __init__(self, prm):
+    def __init__(self, prm, _handle=None):
         self.prm = prm
-        self.h = ks_context_create(prm.dnum, prm.logn, prm.L, prm.q, prm.p)
+        self.h = _handle or ks_context_create(prm.dnum, prm.logn, prm.L, prm.q, prm.p)
         self.info = ks_context_info(self.h)
+        self.level = self.info["L"]
+        self.nq = self.info["nq"]
+
+    def at_level(self, level: int) -> "Context":
+        """KeySwitch / HMUL / HROT at `level` with this context's keys."""
+        return Context(self.prm, ks_context_at_level(self.h, level))
 
     def close(self):
         if self.h:
@@ -312,9 +376,40 @@ class Context:
         ks_keygen(self.h, s_from, s_to, a, e, evk, stream)
         return evk
 
-    def switch(self, d, evk, out=None, variant=KS_AUTO, chunks=0, workspace=None, stream=None):
+    def keygen_relin(self, s, a, e, stream=None):
         import torch
+        prm = self.prm
+        evk = torch.empty((prm.beta, 2, prm.QP, prm.N), dtype=torch.uint64, device=a.device)
+        ks_keygen_relin(self.h, s, a, e, evk, stream)
+        return evk
+
+    def keygen_galois(self, s, k, a, e, stream=None):
+        import torch
+        prm = self.prm
+        evk = torch.empty((prm.beta, 2, prm.QP, prm.N), dtype=torch.uint64, device=a.device)
+        ks_keygen_galois(self.h, s, k, a, e, evk, stream)
+        return evk
+
+    def _out(self, like):
+        import torch
+        return torch.empty((2, self.nq, self.prm.N), dtype=torch.uint64, device=like.device)
+
+    def switch(self, d, evk, out=None, variant=KS_AUTO, chunks=0, workspace=None, stream=None):
         if out is None:
-            out = torch.empty((2, self.prm.L + 1, self.prm.N), dtype=torch.uint64, device=d.device)
+            out = self._out(d)
         ks_switch(self.h, d, evk, out, variant, chunks, workspace, stream)
+        return out
+
+    def hmul(self, ct1, ct2, rlk, out=None, variant=KS_AUTO, chunks=0, workspace=None,
+             stream=None):
+        if out is None:
+            out = self._out(ct1)
+        ks_hmul(self.h, ct1, ct2, rlk, out, variant, chunks, workspace, stream)
+        return out
+
+    def hrot(self, ct, k, rtk, out=None, variant=KS_AUTO, chunks=0, workspace=None,
+             stream=None):
+        if out is None:
+            out = self._out(ct)
+        ks_hrot(self.h, ct, k, rtk, out, variant, chunks, workspace, stream)
         return out
