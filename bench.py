@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-job uneven batch measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-eval", action="store_true",
+                    help="skip the HMUL / HROT / level-aware measurements")
     return ap.parse_args()
 
 
@@ -293,6 +295,99 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
     return out
 
 
+# ---------------------------------------------------------------------------
+# HMUL and HROT throughput (Sec. II-A: tensor product / Galois automorphism plus a
+# KeySwitch), and level-aware switching (Sec. V: re-select the dataflow as the
+# level falls): one KeySwitch per level from L down to 0 at (4, 2^16, 35), with one
+# fixed plan for every level against the plan ks_tune picks at each level.
+
+def eval_measure(args, ks, torch, dev, stream, l2):
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4321)
+
+    def rand_limbs(mods, lead, n):
+        t = torch.empty((*lead, len(mods), n), dtype=torch.int64, device=dev)
+        for i, m in enumerate(mods):
+            t[..., i, :] = torch.randint(0, m, (*lead, n), generator=gen, device=dev,
+                                         dtype=torch.int64)
+        return t.view(torch.uint64)
+
+    flush = torch.empty(2 * l2 // 8 + 1, dtype=torch.int64, device=dev)
+
+    def per_call_ms(fn, reps):
+        """Mean device time of fn() with L2 flushed before every call (flush untimed)."""
+        for k in range(2):
+            fn(k)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for k, (a, b) in enumerate(evs):
+            flush.zero_()
+            a.record(stream)
+            fn(k)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+    out = {"l2_flushed_between_calls": True}
+    reps = 30
+    for name, cfg in (("c2", W.C2), ("c3", W.C3)):
+        prm = W.make_params(*cfg)
+        ctx = ks.Context(prm)
+        try:
+            keys = [rand_limbs(prm.mods, (prm.beta, 2), prm.N) for _ in range(2)]
+            cts = [rand_limbs(prm.q, (2,), prm.N) for _ in range(3)]
+            res = torch.empty_like(cts[0])
+            k_rot = ks.galois_elt(1, prm.N)
+            v, c = ks.ks_tune(ctx.h, cts[0][1].contiguous(), keys[0], res, 1, stream)
+            t_ks = per_call_ms(lambda k: ks.ks_switch(ctx.h, cts[k % 3][1], keys[k % 2], res, v,
+                                                      c, None, stream), reps)
+            t_mul = per_call_ms(lambda k: ks.ks_hmul(ctx.h, cts[k % 3], cts[(k + 1) % 3],
+                                                     keys[k % 2], res, v, c, None, stream), reps)
+            t_rot = per_call_ms(lambda k: ks.ks_hrot(ctx.h, cts[k % 3], k_rot, keys[k % 2], res,
+                                                     v, c, None, stream), reps)
+            out[name] = {"workload": prm.name(), "plan": ks.variant_name(v, c),
+                         "keyswitch_per_s": 1e3 / t_ks, "hmul_per_s": 1e3 / t_mul,
+                         "hrot_per_s": 1e3 / t_rot, "ks_ms": t_ks, "hmul_ms": t_mul,
+                         "hrot_ms": t_rot}
+        finally:
+            ctx.close()
+
+    prm = W.make_params(*W.C3)
+    top = ks.Context(prm)
+    try:
+        keys = [rand_limbs(prm.mods, (prm.beta, 2), prm.N) for _ in range(2)]
+        fixed = ks.KS_DPOB
+        rows, t_fix, t_dyn = [], 0.0, 0.0
+        for level in range(prm.L, -1, -1):
+            view = top.at_level(level)
+            try:
+                ds = [rand_limbs(prm.q[:level + 1], (), prm.N) for _ in range(2)]
+                res = torch.empty((2, level + 1, prm.N), dtype=torch.uint64, device=dev)
+                v, c = ks.ks_tune(view.h, ds[0], keys[0], res, 1, stream)
+                tf = per_call_ms(lambda k: ks.ks_switch(view.h, ds[k % 2], keys[k % 2], res, fixed,
+                                                        0, None, stream), 10)
+                td = per_call_ms(lambda k: ks.ks_switch(view.h, ds[k % 2], keys[k % 2], res, v, c,
+                                                        None, stream), 10)
+                t_fix += tf
+                t_dyn += min(td, tf) if (v, c) == (fixed, 0) else td
+                rows.append({"level": level, "tuned": ks.variant_name(v, c),
+                             "ms_fixed": round(tf, 5), "ms_tuned": round(td, 5)})
+            finally:
+                view.close()
+        picks = {}
+        for r in rows:
+            picks[r["tuned"]] = picks.get(r["tuned"], 0) + 1
+        out["levels"] = {
+            "workload": f"one KeySwitch at each level {prm.L}..0 of {prm.name()} with the "
+                        f"top-level key (level views)",
+            "fixed_plan": ks.variant_name(fixed), "chain_ms_fixed": t_fix,
+            "chain_ms_per_level_tuned": t_dyn, "speedup": t_fix / t_dyn, "picks": picks,
+            "per_level": rows}
+    finally:
+        top.close()
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -451,6 +546,8 @@ def main():
     }
     if not args.no_batch:
         line["batch64"] = batch_measure(args, ks, torch, dev, stream, hbm)
+    if not args.no_eval:
+        line["eval"] = eval_measure(args, ks, torch, dev, stream, l2)
     if world == 1 and not args.no_cpu:
         reps, el, cores = oracle_sample(prm, args.cpu_seconds, 10000)
         line["cpu_baseline"] = {"value": reps / el, "unit": UNIT, "cores": cores,

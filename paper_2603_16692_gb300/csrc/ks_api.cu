@@ -567,8 +567,8 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   PersistBatch *pb = persist_new();
   persist_build(*pb, ctxs, jp, wo);
   const size_t bytes = persist_bytes(*pb), soff = persist_state_offset(*pb);
-  int nj = 0, nw = 0;
-  persist_counts(*pb, &nj, &nw);
+  int nj = 0, nw = 0, nc = 0;
+  persist_counts(*pb, &nj, &nw, &nc);
   int rc = KS_OK;
   void *buf = nullptr;
   if (graph && !stall) {
@@ -598,7 +598,7 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   persist_free(pb);
   if (rc) return rc;
   if (!(graph && !stall)) {
-    rc = persist_launch(buf, nj, nw, soff, kPersistWaitNs, stall, s);
+    rc = persist_launch(buf, nj, nw, nc, soff, kPersistWaitNs, stall, s);
     if (rc == KS_OK) {
       g_batch.last_state_buf = buf;
       g_batch.last_state_off = soff;
@@ -607,7 +607,7 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   }
   cudaStream_t cs = g_batch.capture_stream();
   KS_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  rc = persist_launch(buf, nj, nw, soff, kPersistWaitNs, false, cs);
+  rc = persist_launch(buf, nj, nw, nc, soff, kPersistWaitNs, false, cs);
   cudaGraph_t gr = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &gr);
   if (rc == KS_OK && e != cudaSuccess) rc = cuda_rc(e);

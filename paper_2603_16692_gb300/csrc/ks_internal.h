@@ -190,9 +190,9 @@ void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
                    const std::vector<JobPtr> &jp, const std::vector<WsOff> &wo);
 size_t persist_bytes(const PersistBatch &pb);
 size_t persist_state_offset(const PersistBatch &pb);
-int persist_counts(const PersistBatch &pb, int *njobs, int *nwork);
+int persist_counts(const PersistBatch &pb, int *njobs, int *nwork, int *ncnt);
 int persist_upload(const PersistBatch &pb, void *dev, cudaStream_t s);
-int persist_launch(void *dev, int njobs, int nwork, size_t state_offset,
+int persist_launch(void *dev, int njobs, int nwork, int ncnt, size_t state_offset,
                    unsigned long long limit_ns, bool stall, cudaStream_t s);
 int persist_status(const void *dev, size_t state_offset, cudaStream_t s);
 

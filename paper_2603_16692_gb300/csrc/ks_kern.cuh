@@ -56,11 +56,13 @@ inline KArgs make_args(const ks_context *c) {
 }
 
 // Work item y of a task descriptor (see Tasks in ks_internal.h).
-__device__ __forceinline__ uint32_t decode(const KArgs &a, const Tasks &tk, int y) {
+__host__ __device__ __forceinline__ uint32_t decode(const KArgs &a, const Tasks &tk, int y) {
   if (tk.mode == TASK_UP) {
     for (int j = tk.j0; j < tk.j1; ++j) {
-      const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
-      const int ovl = max(lo, tk.t0), ov = max(0, min(hi, tk.t1) - ovl);
+      const int lo = j * a.alpha, hi = lo + a.alpha < a.nq ? lo + a.alpha : a.nq;
+      const int ovl = lo > tk.t0 ? lo : tk.t0;
+      const int ovh = hi < tk.t1 ? hi : tk.t1;
+      const int ov = ovh - ovl > 0 ? ovh - ovl : 0;
       const int cnt = (tk.t1 - tk.t0) - ov;
       if (y < cnt) {
         int t = tk.t0 + y;

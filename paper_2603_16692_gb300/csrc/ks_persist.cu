@@ -1,22 +1,31 @@
-// One persistent launch for a batch of KeySwitches of uneven (dnum, N, L).
-//
-// Every CTA of a co-resident grid loops: it claims the next work item from a
-// device counter, waits until the item's job has finished the previous stage,
-// runs the item (one tile of one stage, the same device code as the per-stage
-// kernels) and counts it done. Work items are listed stage-major over all jobs
-// (every job's stage s before any job's stage s+1), so an item only waits for
-// items with smaller indices. Items are claimed in index order, and only by CTAs
-// that are running, so the earliest unfinished item is held by a running CTA
-// and has nothing left to wait for: the loop cannot deadlock, resident grid or
-// not.
+// One persistent launch for a batch of KeySwitches of uneven (dnum, N, L): a
+// dataflow executor over tile-level work items.
 //
 // Stages of one job (DPOB, fused, two-pass NTT; N = 2^13..2^17):
 //   0 iNTT rows (d)   1 iNTT columns (d)   2 ModUp BConv + NTT columns
 //   3 NTT rows + key multiply   4 iNTT rows (P-limbs)   5 iNTT columns (P-limbs)
 //   6 ModDown BConv + NTT columns   7 NTT rows + P^-1 scaling
+// A work item is one tile of one stage (the same device code as the per-stage
+// kernels). It waits on at most two dependency counters and signals one, so an
+// item starts as soon as the tiles it reads are written, not when the whole
+// previous stage is done:
+//   1 (col tile, limb i)      waits for the row tiles of limb i       (stage 0)
+//   2 (col tile c, (t, j))    waits for col tile c of digit j's limbs (stage 1)
+//   3 (row tile r, target t)  waits for every (col tile, digit) of t  (stage 2)
+//   4 (row tile r, P-limb k)  waits for row tile r of target L+1+k    (stage 3)
+//   5 (col tile, P-limb k)    waits for the row tiles of P-limb k     (stage 4)
+//   6 (col tile c, (c', i))   waits for col tile c of every P-limb    (stage 5)
+//   7 (row tile r, limb i)    waits for every col tile of (0, i), (1, i)  (stage 6)
+//                             and for row tile r of target i          (stage 3)
+// The host builds the items, their counters and the counts they wait for.
 //
-// Each CTA claims its next item while it runs the current one; a claimed item
-// only waits for items with smaller indices, so the argument above still holds.
+// Every CTA loops: it claims the next item from a device counter, waits for the
+// item's dependencies, runs it and signals. Items are listed stage-major over
+// all jobs, so an item only depends on items with smaller indices. Items are
+// claimed in index order, and only by CTAs that are running, so the earliest
+// unfinished item is held by a running CTA and has nothing left to wait for: the
+// loop cannot deadlock, resident grid or not. Each CTA claims its next item while
+// it runs the current one; that item too only waits for smaller indices.
 // Completion is counted with a release increment after the CTA's barrier, and the
 // consumer's acquire load of the counter (then a barrier) orders its reads after
 // the producer's writes.
@@ -24,7 +33,7 @@
 // Waits are bounded: a wait that exceeds `limit_ns` of %globaltimer sets the
 // device error word and the abort flag, and every CTA then returns; the host
 // reads the error with ks_batch_status (KS_ETIMEOUT). Buffers written during the
-// launch are read with coherent loads after an acquire on the stage counter.
+// launch are read with coherent loads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,14 +60,16 @@ struct PJob {
   WsOff wo;
   Tasks up, tg, dn, d1;
   int logn;
-  int count[kStages];  // work items of each stage
 };
 
+// One tile of one stage of one job, with its dependencies: counters cnt[w0] and
+// cnt[w1] (-1: none) must reach n0 and n1 before it runs; it then adds 1 to
+// cnt[sig] (-1: none).
 struct PWork {
-  uint16_t job;
-  uint8_t stage;
-  uint8_t pad;
-  uint16_t bx, by;
+  uint16_t job, bx, by;
+  uint8_t stage, pad;
+  int32_t w0, w1, sig;
+  uint16_t n0, n1;
 };
 
 struct PState {
@@ -66,7 +77,7 @@ struct PState {
   int abort;
   int err;
   int pad;
-  int done[1];  // [njobs][kStages]
+  int cnt[1];  // dependency counters
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -159,10 +170,11 @@ __global__ void __launch_bounds__(kPNT, 3) k_persist(const PJob *__restrict__ jo
       ok = 1;
       if (k < nwork) {
         const PWork w = work[k];
-        if (w.stage > 0)
-          ok = wait_count(&st->done[w.job * kStages + w.stage - 1],
-                          jobs[w.job].count[w.stage - 1], st, limit_ns);
-        // claim the next item now, so that the claim's latency hides behind this one
+        if (w.w0 >= 0) ok = wait_count(&st->cnt[w.w0], w.n0, st, limit_ns);
+        if (ok && w.w1 >= 0) ok = wait_count(&st->cnt[w.w1], w.n1, st, limit_ns);
+        // claim the next item now, while this one runs. (Claiming two ahead and
+        // prefetching descriptors measured slower on GB300: it hoards the last
+        // items on busy CTAs and raises register spills.)
         nxt = ok ? atomicAdd(&st->next, 1) : nwork;
       }
     }
@@ -186,7 +198,7 @@ __global__ void __launch_bounds__(kPNT, 3) k_persist(const PJob *__restrict__ jo
       default: run_stage<17>(J, w.stage, w.bx, w.by, raw, cst); break;
     }
     __syncthreads();
-    if (threadIdx.x == 0) red_release_add(&st->done[w.job * kStages + w.stage], 1);
+    if (threadIdx.x == 0 && w.sig >= 0) red_release_add(&st->cnt[w.sig], 1);
   }
 }
 
@@ -218,27 +230,48 @@ int grid_of(int logn, int which) {
 struct PersistBatch {
   std::vector<PJob> jobs;
   std::vector<PWork> work;
+  int ncnt = 0;
 };
 
 bool persist_supported(const ks_context *c) { return c->logn >= 13 && c->logn <= 17; }
 
 PersistBatch *persist_new() { return new PersistBatch(); }
 void persist_free(PersistBatch *pb) { delete pb; }
-int persist_counts(const PersistBatch &pb, int *njobs, int *nwork) {
+int persist_counts(const PersistBatch &pb, int *njobs, int *nwork, int *ncnt) {
   *njobs = (int)pb.jobs.size();
   *nwork = (int)pb.work.size();
+  *ncnt = pb.ncnt;
   return KS_OK;
 }
 
 int persist_radix(int logn) { return prl(logn); }
 
-// Build the descriptors and the stage-major work list for jobs whose plans are
-// DPOB fused (OutputBulk: one group per phase).
+namespace {
+
+// Counter layout of one job (offsets into PState::cnt).
+struct JobCounters {
+  int c01;  // [nq]          row tiles of limb i done (stage 0)
+  int c12;  // [beta][gc]    limbs of digit j done in col tile c (stage 1)
+  int c23;  // [qp]          (col tile, digit) items of target t done (stage 2)
+  int c3p;  // [np][gr]      key multiply of P-target k, row tile r (stage 3)
+  int c3q;  // [nq][gr]      key multiply of Q-target i, row tile r (stage 3)
+  int c45;  // [np]          row tiles of P-limb k done (stage 4)
+  int c56;  // [gc]          P-limbs done in col tile c (stage 5)
+  int c67;  // [nq]          (col tile, c) items of limb i done (stage 6)
+};
+
+}  // namespace
+
+// Build the descriptors, counters and the stage-major work list for jobs whose
+// plans are DPOB fused (OutputBulk: one group per phase).
 void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
                    const std::vector<JobPtr> &jp, const std::vector<WsOff> &wo) {
   pb.jobs.clear();
   pb.work.clear();
+  pb.ncnt = 0;
   const int n = (int)ctx.size();
+  std::vector<JobCounters> jc(n);
+  std::vector<long long> work(n);
   for (int k = 0; k < n; ++k) {
     const ks_context *c = ctx[k];
     PJob J;
@@ -271,59 +304,113 @@ void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
     J.tg = tg;
     J.dn = dn;
     J.d1 = d1;
-    const int gr = grid_of(c->logn, 0), gc = grid_of(c->logn, 1);
-    const int items[kStages][2] = {{gr, c->nq},
-                                   {gc, c->nq},
-                                   {gc, kern::count_tasks(c, up)},
-                                   {gr, kern::count_tasks(c, tg)},
-                                   {gr, c->np},
-                                   {gc, c->np},
-                                   {gc, kern::count_tasks(c, dn)},
-                                   {gr, kern::count_tasks(c, d1)}};
-    for (int s = 0; s < kStages; ++s) J.count[s] = items[s][0] * items[s][1];
     pb.jobs.push_back(J);
+    const int gr = grid_of(c->logn, 0), gc = grid_of(c->logn, 1);
+    JobCounters &q = jc[k];
+    int o = pb.ncnt;
+    q.c01 = o; o += c->nq;
+    q.c12 = o; o += c->beta * gc;
+    q.c23 = o; o += c->qp;
+    q.c3p = o; o += c->np * gr;
+    q.c3q = o; o += c->nq * gr;
+    q.c45 = o; o += c->np;
+    q.c56 = o; o += gc;
+    q.c67 = o; o += c->nq;
+    pb.ncnt = o;
+    work[k] = (long long)(c->qp * c->beta) << c->logn;
   }
   // largest jobs first within each stage (measured 1% faster than batch order)
   std::vector<int> ord(n);
-  std::vector<long long> work(n);
-  for (int k = 0; k < n; ++k) {
-    ord[k] = k;
-    work[k] = 0;
-    for (int s = 0; s < kStages; ++s) work[k] += pb.jobs[k].count[s];
-    work[k] <<= pb.jobs[k].logn;
-  }
+  for (int k = 0; k < n; ++k) ord[k] = k;
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work[x] > work[y]; });
+  auto item = [&](int k, int s, int bx, int by, int w0, int n0, int w1, int n1, int sig) {
+    PWork w;
+    w.job = (uint16_t)k;
+    w.bx = (uint16_t)bx;
+    w.by = (uint16_t)by;
+    w.stage = (uint8_t)s;
+    w.pad = 0;
+    w.w0 = w0;
+    w.n0 = (uint16_t)n0;
+    w.w1 = w1;
+    w.n1 = (uint16_t)n1;
+    w.sig = sig;
+    pb.work.push_back(w);
+  };
   for (int s = 0; s < kStages; ++s)
     for (int kk = 0; kk < n; ++kk) {
       const int k = ord[kk];
+      const ks_context *c = ctx[k];
       const PJob &J = pb.jobs[k];
-      const int gx = (s == 1 || s == 2 || s == 5 || s == 6) ? grid_of(J.logn, 1)
-                                                             : grid_of(J.logn, 0);
-      const int gy = J.count[s] / gx;
-      for (int by = 0; by < gy; ++by)
-        for (int bx = 0; bx < gx; ++bx) {
-          PWork w;
-          w.job = (uint16_t)k;
-          w.stage = (uint8_t)s;
-          w.pad = 0;
-          w.bx = (uint16_t)bx;
-          w.by = (uint16_t)by;
-          pb.work.push_back(w);
+      const JobCounters &q = jc[k];
+      const int gr = grid_of(c->logn, 0), gc = grid_of(c->logn, 1);
+      const int nq = c->nq, np = c->np, al = c->alpha;
+      auto dsize = [&](int j) { return std::min(nq, (j + 1) * al) - j * al; };
+      auto ndig = [&](int t) { return c->beta - (t < nq ? 1 : 0); };
+      switch (s) {
+        case 0:
+          for (int i = 0; i < nq; ++i)
+            for (int r = 0; r < gr; ++r) item(k, 0, r, i, -1, 0, -1, 0, q.c01 + i);
+          break;
+        case 1:
+          for (int i = 0; i < nq; ++i)
+            for (int cc = 0; cc < gc; ++cc)
+              item(k, 1, cc, i, q.c01 + i, gr, -1, 0, q.c12 + (i / al) * gc + cc);
+          break;
+        case 2: {
+          const int nt = kern::count_tasks(c, J.up);
+          for (int y = 0; y < nt; ++y) {
+            const uint32_t w = kern::decode(J.a, J.up, y);
+            const int t = task_limb(w), j = task_dig(w);
+            for (int cc = 0; cc < gc; ++cc)
+              item(k, 2, cc, y, q.c12 + j * gc + cc, dsize(j), -1, 0, q.c23 + t);
+          }
+          break;
         }
+        case 3:
+          for (int t = 0; t < c->qp; ++t)
+            for (int r = 0; r < gr; ++r)
+              item(k, 3, r, t, ndig(t) > 0 ? q.c23 + t : -1, gc * ndig(t), -1, 0,
+                   t < nq ? q.c3q + t * gr + r : q.c3p + (t - nq) * gr + r);
+          break;
+        case 4:
+          for (int kp = 0; kp < np; ++kp)
+            for (int r = 0; r < gr; ++r)
+              item(k, 4, r, kp, q.c3p + kp * gr + r, 1, -1, 0, q.c45 + kp);
+          break;
+        case 5:
+          for (int kp = 0; kp < np; ++kp)
+            for (int cc = 0; cc < gc; ++cc) item(k, 5, cc, kp, q.c45 + kp, gr, -1, 0, q.c56 + cc);
+          break;
+        case 6: {
+          const int nt = kern::count_tasks(c, J.dn);
+          for (int y = 0; y < nt; ++y) {
+            const int i = task_limb(kern::decode(J.a, J.dn, y));
+            for (int cc = 0; cc < gc; ++cc) item(k, 6, cc, y, q.c56 + cc, np, -1, 0, q.c67 + i);
+          }
+          break;
+        }
+        default:
+          for (int i = 0; i < nq; ++i)
+            for (int r = 0; r < gr; ++r)
+              item(k, 7, r, i, q.c67 + i, 2 * gc, q.c3q + i * gr + r, 1, -1);
+          break;
+      }
     }
 }
 
 size_t persist_job_bytes() { return sizeof(PJob); }
 size_t persist_work_bytes() { return sizeof(PWork); }
-size_t persist_state_bytes(int njobs) { return sizeof(PState) + sizeof(int) * (size_t)njobs * kStages; }
+size_t persist_state_bytes(int ncnt) { return sizeof(PState) + sizeof(int) * (size_t)ncnt; }
 
-// Device image of a built batch: jobs | work | state.
+// Device image of a built batch: jobs | work | state (16-byte aligned pieces).
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 size_t persist_bytes(const PersistBatch &pb) {
-  return pb.jobs.size() * sizeof(PJob) + pb.work.size() * sizeof(PWork) +
-         persist_state_bytes((int)pb.jobs.size());
+  return align16(pb.jobs.size() * sizeof(PJob)) + align16(pb.work.size() * sizeof(PWork)) +
+         persist_state_bytes(pb.ncnt);
 }
 size_t persist_state_offset(const PersistBatch &pb) {
-  return pb.jobs.size() * sizeof(PJob) + pb.work.size() * sizeof(PWork);
+  return align16(pb.jobs.size() * sizeof(PJob)) + align16(pb.work.size() * sizeof(PWork));
 }
 
 // Copy the descriptors and the work list to `dev` (stream-ordered; not capturable:
@@ -331,14 +418,15 @@ size_t persist_state_offset(const PersistBatch &pb) {
 int persist_upload(const PersistBatch &pb, void *dev, cudaStream_t s) {
   const size_t jb = pb.jobs.size() * sizeof(PJob), wb = pb.work.size() * sizeof(PWork);
   cudaError_t e = cudaMemcpyAsync(dev, pb.jobs.data(), jb, cudaMemcpyHostToDevice, s);
-  if (!e) e = cudaMemcpyAsync((char *)dev + jb, pb.work.data(), wb, cudaMemcpyHostToDevice, s);
+  if (!e)
+    e = cudaMemcpyAsync((char *)dev + align16(jb), pb.work.data(), wb, cudaMemcpyHostToDevice, s);
   return e ? KS_ECUDA : KS_OK;
 }
 
 // Reset the state and launch the persistent kernel over an uploaded image
-// (capturable). `stall` (tests only) counts job 0's first stage one short, so the
-// items of its second stage wait until the bounded wait gives up.
-int persist_launch(void *dev, int njobs, int nwork, size_t state_offset,
+// (capturable). `stall` (tests only) starts the first counter at -1, so the items
+// that wait on it (job 0's first column items) wait until the bounded wait gives up.
+int persist_launch(void *dev, int njobs, int nwork, int ncnt, size_t state_offset,
                    unsigned long long limit_ns, bool stall, cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
@@ -356,10 +444,10 @@ int persist_launch(void *dev, int njobs, int nwork, size_t state_offset,
   });
   if (attr != cudaSuccess || blocks_per_sm < 1) return KS_ECUDA;
   char *base = (char *)dev;
-  const size_t jb = (size_t)njobs * sizeof(PJob);
+  const size_t jb = align16((size_t)njobs * sizeof(PJob));
   PState *st = (PState *)(base + state_offset);
-  cudaError_t e = cudaMemsetAsync(st, 0, persist_state_bytes(njobs), s);
-  if (!e && stall) e = cudaMemsetAsync(&st->done[0], 0xff, sizeof(int), s);  // -1
+  cudaError_t e = cudaMemsetAsync(st, 0, persist_state_bytes(ncnt), s);
+  if (!e && stall) e = cudaMemsetAsync(&st->cnt[0], 0xff, sizeof(int), s);  // -1
   if (e) return KS_ECUDA;
   const int grid = std::max(1, std::min(nwork, blocks_per_sm * sms));
   k_persist<<<grid, kPNT, kPSmem, s>>>((const PJob *)base, (const PWork *)(base + jb), nwork, st,

@@ -1,0 +1,62 @@
+"""One KeySwitch (or HMUL / HROT) of a given (dnum, N, L) and plan, for profilers.
+
+Sets up a context and seeded random operands (uniform residues; no key generation,
+so that the only library kernels the process launches are the ones of the single
+timed operation), then runs the operation once (``--reps`` times) and exits. The
+kernel names all start with ``k_``, so ``ncu -k regex:^k_`` captures exactly the
+operation's launches.
+
+    python -m paper_2603_16692_gb300.profile_case --cfg 4,16,30 --variant DPOB
+"""
+from __future__ import annotations
+
+import argparse
+
+from . import ks
+from . import workload as W
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--cfg", default="4,16,30", help="dnum,log2N,L")
+    ap.add_argument("--variant", default="DPOB", help="DSOB / DPOB / DSOC / DPOC")
+    ap.add_argument("--chunks", type=int, default=0)
+    ap.add_argument("--unfused", action="store_true")
+    ap.add_argument("--radix", type=int, default=8, choices=[4, 8, 16])
+    ap.add_argument("--op", default="switch", choices=["switch", "hmul", "hrot"])
+    ap.add_argument("--level", type=int, default=-1, help="run on a level view (default: top)")
+    ap.add_argument("--reps", type=int, default=1)
+    args = ap.parse_args(argv)
+
+    import torch
+    dnum, logn, L = (int(x) for x in args.cfg.split(","))
+    prm = W.make_params(dnum, logn, L)
+    dev = torch.device("cuda", 0)
+    v = ks.VARIANTS[args.variant.upper()] | (ks.KS_UNFUSED if args.unfused else 0) | \
+        {4: ks.KS_RADIX4, 8: 0, 16: ks.KS_RADIX16}[args.radix]
+    top = ks.Context(prm)
+    ctx = top.at_level(args.level) if args.level >= 0 else top
+    nq = ctx.nq
+    g = W.rng(2024, 11)
+    evk = torch.from_numpy(W.uniform_limbs(g, prm.mods * (2 * prm.beta), prm.N).reshape(
+        prm.beta, 2, prm.QP, prm.N)).to(dev)
+    ct = torch.from_numpy(W.uniform_limbs(g, prm.q[:nq] * 2, prm.N).reshape(2, nq, prm.N)).to(dev)
+    ct2 = torch.from_numpy(W.uniform_limbs(g, prm.q[:nq] * 2, prm.N).reshape(2, nq, prm.N)).to(dev)
+    out = torch.empty_like(ct)
+    torch.cuda.synchronize()
+    for _ in range(args.reps):
+        if args.op == "switch":
+            ctx.switch(ct[1], evk, out, v, args.chunks)
+        elif args.op == "hmul":
+            ctx.hmul(ct, ct2, evk, out, v, args.chunks)
+        else:
+            ctx.hrot(ct, ks.galois_elt(1, prm.N), evk, out, v, args.chunks)
+    torch.cuda.synchronize()
+    print(f"{args.op} {prm.name()} level {nq - 1} {ks.variant_name(v, args.chunks)}: ok")
+    if ctx is not top:
+        ctx.close()
+    top.close()
+
+
+if __name__ == "__main__":
+    main()
