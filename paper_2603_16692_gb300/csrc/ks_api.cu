@@ -470,6 +470,69 @@ int keygen_impl(ks_context *c, const int8_t *s_from, const int8_t *s_to, unsigne
   return rc;
 }
 
+// At most this many graphs are kept per context (least recently used dropped).
+constexpr size_t kGraphCache = 32;
+
+void drop_graph_cache(ks_context *c) {
+  std::lock_guard<std::mutex> lk(c->gmu);
+  if (!c->gcache.empty()) cudaDeviceSynchronize();  // no replay of these graphs in flight
+  for (auto &kv : c->gcache)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  c->gcache.clear();
+}
+
+// Enqueue one operation on s through the context's graph cache: the first call
+// with a key runs enqueue(s) directly; the second captures enqueue on a private
+// stream into a CUDA graph (the kernel chain then launches without per-kernel
+// launch gaps); later calls replay it. While the library profiler is on, every
+// call runs directly (per-launch events need the individual launches).
+template <class F>
+int cached_launch(ks_context *c, const std::array<uintptr_t, 10> &key, cudaStream_t s,
+                  F enqueue) {
+  if (g_prof.on) return enqueue(s);
+  std::unique_lock<std::mutex> lk(c->gmu);
+  auto it = c->gcache.find(key);
+  if (it == c->gcache.end()) {
+    if (c->gcache.size() >= kGraphCache) {
+      auto old = c->gcache.begin();
+      for (auto q = c->gcache.begin(); q != c->gcache.end(); ++q)
+        if (q->second.last < old->second.last) old = q;
+      if (old->second.exec) cudaGraphExecDestroy(old->second.exec);
+      c->gcache.erase(old);
+    }
+    c->gcache[key].last = ++c->gclock;
+    lk.unlock();
+    return enqueue(s);
+  }
+  it->second.last = ++c->gclock;
+  if (!it->second.exec) {
+    if (!c->gstream && cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) {
+      cudaGetLastError();
+      lk.unlock();
+      return enqueue(s);
+    }
+    KS_TRY(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue(c->gstream);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &gr);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == KS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (rc != KS_OK || e != cudaSuccess || !exec) {
+      cudaGetLastError();
+      c->gcache.erase(it);
+      lk.unlock();
+      return rc != KS_OK ? rc : enqueue(s);
+    }
+    it->second.exec = exec;
+  }
+  cudaGraphExec_t exec = it->second.exec;
+  lk.unlock();
+  return cuda_rc(cudaGraphLaunch(exec, s));
+}
+
+int plan_code(const Plan &pl) { return pl.base | (pl.rl << 8) | (pl.unfused ? 1 << 12 : 0); }
+
 // Galois elements are odd residues k in [1, 2N).
 bool galois_ok(const ks_context *c, uint32_t k) {
   return (k & 1) && (u64)k < (u64)2 * c->N;
@@ -676,6 +739,8 @@ int ks_context_at_level(const ks_context *top, int level, ks_context **out) {
 void ks_context_destroy(ks_context *c) {
   if (!c) return;
   forget_graphs(c);
+  drop_graph_cache(c);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->table_mem) cudaFree(c->table_mem);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
@@ -728,7 +793,10 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
     js.j[0].evk = (const u64 *)evk;
     js.j[0].out = (u64 *)out;
     js.j[0].ws = base;
-    return run_plan(c, pl, js, s);
+    const std::array<uintptr_t, 10> key = {
+        0, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)d, (uintptr_t)evk, 0,
+        (uintptr_t)out, (uintptr_t)base, (uintptr_t)s, 0};
+    return cached_launch(c, key, s, [&](cudaStream_t q) { return run_plan(c, pl, js, q); });
   });
 }
 
@@ -805,7 +873,6 @@ int ks_hmul(ks_context *c, const uint64_t *ct1, const uint64_t *ct2, const uint6
   cudaStream_t s = (cudaStream_t)stream;
   return with_workspace(c, ws, ws_bytes, (pl.total + extra) * 8, [&](u64 *base) {
     u64 *d2 = base + pl.total;
-    KS_TRY(launch_tensor(c, (const u64 *)ct1, (const u64 *)ct2, (u64 *)out, d2, s));
     JobSet js = {};
     js.n = 1;
     js.j[0].d = d2;
@@ -814,7 +881,13 @@ int ks_hmul(ks_context *c, const uint64_t *ct1, const uint64_t *ct2, const uint6
     js.j[0].ws = base;
     js.j[0].add = (const u64 *)out;
     js.j[0].addmask = 3;
-    return run_plan(c, pl, js, s);
+    const std::array<uintptr_t, 10> key = {
+        1, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)ct1, (uintptr_t)ct2,
+        (uintptr_t)rlk, (uintptr_t)out, (uintptr_t)base, (uintptr_t)s, 0};
+    return cached_launch(c, key, s, [&](cudaStream_t q) {
+      KS_TRY(launch_tensor(c, (const u64 *)ct1, (const u64 *)ct2, (u64 *)out, d2, q));
+      return run_plan(c, pl, js, q);
+    });
   });
 }
 
@@ -830,7 +903,6 @@ int ks_hrot(ks_context *c, const uint64_t *ct, uint32_t galois_elt, const uint64
   cudaStream_t s = (cudaStream_t)stream;
   return with_workspace(c, ws, ws_bytes, (pl.total + extra) * 8, [&](u64 *base) {
     u64 *y0 = base + pl.total, *y1 = y0 + (size_t)c->nq * c->N;
-    KS_TRY(launch_automorph(c, (const u64 *)ct, galois_elt, y0, y1, s));
     JobSet js = {};
     js.n = 1;
     js.j[0].d = y1;
@@ -839,7 +911,13 @@ int ks_hrot(ks_context *c, const uint64_t *ct, uint32_t galois_elt, const uint64
     js.j[0].ws = base;
     js.j[0].add = y0;  // out_0 += sigma(ct_0); out_1 is the KeySwitch's alone
     js.j[0].addmask = 1;
-    return run_plan(c, pl, js, s);
+    const std::array<uintptr_t, 10> key = {
+        2, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)ct, (uintptr_t)galois_elt,
+        (uintptr_t)rtk, (uintptr_t)out, (uintptr_t)base, (uintptr_t)s, 0};
+    return cached_launch(c, key, s, [&](cudaStream_t q) {
+      KS_TRY(launch_automorph(c, (const u64 *)ct, galois_elt, y0, y1, q));
+      return run_plan(c, pl, js, q);
+    });
   });
 }
 

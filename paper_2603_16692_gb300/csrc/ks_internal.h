@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -125,6 +127,16 @@ struct ks_context {
   // staging buffers for ks_switch_host
   void *stage = nullptr;
   size_t stage_bytes = 0;
+  // CUDA graphs of repeated single-operation calls (ks_switch / ks_hmul / ks_hrot
+  // with the same plan, buffers and stream), captured on the second such call
+  std::mutex gmu;
+  struct CachedGraph {
+    cudaGraphExec_t exec = nullptr;  // null: seen once, not captured yet
+    unsigned long long last = 0;
+  };
+  std::map<std::array<uintptr_t, 10>, CachedGraph> gcache;
+  unsigned long long gclock = 0;
+  cudaStream_t gstream = nullptr;  // capture stream
 };
 
 namespace ks {

@@ -1,0 +1,70 @@
+"""Repeated single operations replay a cached CUDA graph (captured on the second
+call with the same plan, buffers and stream): every replay must read the buffers'
+current contents and give the oracle's result."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2603_16692_gb300 import ks
+from paper_2603_16692_gb300 import workload as W
+from tests.gpu_util import dev, first_mismatch, host, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("variant,chunks", [(ks.KS_DPOB, 0), (ks.KS_DSOC | ks.KS_RADIX4, 3),
+                                            (ks.KS_DSOB | ks.KS_UNFUSED, 0)])
+def test_switch_replays_see_new_inputs(variant, chunks):
+    import torch
+    cfg = (3, 14, 8)
+    cases = [oracle_case(cfg, s) for s in (0, 1, 2)]
+    prm = cases[0][0]
+    ctx = ks.Context(prm)
+    try:
+        d = dev(cases[0][5])
+        evk = dev(cases[0][6])
+        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
+        # calls 1 (direct), 2 (capture), 3..6 (replays), inputs changed in place
+        for rep in range(6):
+            c = cases[rep % 3]
+            d.copy_(torch.from_numpy(c[5]).cuda())
+            evk.copy_(torch.from_numpy(c[6]).cuda())
+            out.fill_(7)
+            ctx.switch(d, evk, out, variant=variant, chunks=chunks)
+            torch.cuda.synchronize()
+            got = host(out)
+            assert np.array_equal(got, c[7]), f"call {rep}: " + first_mismatch(got, c[7])
+    finally:
+        ctx.close()
+
+
+def test_hmul_and_hrot_replays():
+    import torch
+    cfg = (2, 13, 5)
+    prm = W.make_params(*cfg)
+    _, s, a, e = W.gen_keys(prm, 1)
+    rlk_o = O.keygen_poly(prm, O.negacyclic_mul_i64(s, s, prm.logn), s, a, e)
+    k = ks.galois_elt(3, prm.N)
+    rtk_o = O.keygen_poly(prm, O.automorphism_i64(s, prm.logn, k), s, a, e)
+    ctx = ks.Context(prm)
+    try:
+        rlk, rtk = dev(rlk_o), dev(rtk_o)
+        ct1 = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
+        ct2 = torch.empty_like(ct1)
+        out = torch.empty_like(ct1)
+        for rep in range(5):
+            g = W.rng(rep, 12)
+            x = W.uniform_limbs(g, prm.q * 2, prm.N).reshape(2, prm.L + 1, prm.N)
+            y = W.uniform_limbs(g, prm.q * 2, prm.N).reshape(2, prm.L + 1, prm.N)
+            ct1.copy_(torch.from_numpy(x).cuda())
+            ct2.copy_(torch.from_numpy(y).cuda())
+            ctx.hmul(ct1, ct2, rlk, out)
+            torch.cuda.synchronize()
+            want = O.hmul(prm, prm.L, x, y, rlk_o)
+            assert np.array_equal(host(out), want), f"hmul call {rep}"
+            ctx.hrot(ct1, k, rtk, out)
+            torch.cuda.synchronize()
+            want = O.hrot(prm, prm.L, x, k, rtk_o)
+            assert np.array_equal(host(out), want), f"hrot call {rep}"
+    finally:
+        ctx.close()
