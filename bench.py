@@ -39,10 +39,11 @@ WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 # per clock x the maximum SM clock, divided by 10 IMADs per 64-bit Shoup modular
 # multiplication (one 64x64 high product ~4 IMAD + two 64-bit low products ~3 each).
 SMS, IMAD_PER_SM_CLK, IMAD_PER_MODOP = 152, 64, 10
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
-# of this bench's command (profiles/); keyed by workload and kernel. None = not
-# captured for the current kernel code.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one cold-cache ncu
+# capture of the same kernel on the same workload (35.685120 MB read + 512 B written);
+# keyed by (workload, plan, kernel). Missing = not captured for the current kernel
+# code and plan (reported as null).
+NCU_TRAFFIC = {("c2", "DPOB", "modup_row_keymult"): 35685632}
 
 
 def parse():
@@ -515,7 +516,7 @@ def main():
     ops_l, bytes_l = dom["ops"] / dom["launches"], dom["bytes"] / dom["launches"]
     alu_ach = ops_l / (per_launch_ms / 1e3) / 1e9
     hbm_ach = bytes_l / (per_launch_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get(args.workload, {}).get(dom["name"])
+    traffic = NCU_TRAFFIC.get((args.workload, ks.variant_name(variant, args.chunks), dom["name"]))
     roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu_ach, "peak": alu_peak,
                 "unit": "Gmodop/s", "frac": alu_ach / alu_peak, "traffic": traffic,
                 "peak_source": f"derived: {SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_mhz:.0f}"
