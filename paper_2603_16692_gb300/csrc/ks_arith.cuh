@@ -69,6 +69,32 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// L2 eviction priorities (createpolicy): twiddle tables are read by every launch and
+// should stay in L2 (evict_last); key words are read once per KeySwitch (evict_first).
+__device__ __forceinline__ u64 l2_keep() {
+  u64 p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ u64 l2_stream() {
+  u64 p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Read-only loads with an L2 cache policy.
+__device__ __forceinline__ ulonglong2 ldg_pol(const ulonglong2 *p, u64 pol) {
+  ulonglong2 r;
+  asm("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+      : "=l"(r.x), "=l"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ u64 ldg_pol(const u64 *p, u64 pol) {
+  u64 r;
+  asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
 // [0, 4m) -> [0, m)
 __device__ __forceinline__ u64 canon4(u64 x, u64 m) { return csub(csub(x, 2 * m), m); }
 

@@ -174,7 +174,8 @@ __device__ __forceinline__ void store_cols(u64 *dst, const u64 *s, int c0) {
 template <class GT>
 __device__ __forceinline__ void stage_tw(ulonglong2 *tws, const ulonglong2 *__restrict__ src,
                                          int n) {
-  for (int k = threadIdx.x; k < n; k += GT::NT) tws[k] = __ldg(src + k);
+  const u64 pol = l2_keep();
+  for (int k = threadIdx.x; k < n; k += GT::NT) tws[k] = ldg_pol(src + k, pol);
 }
 
 // Column-pass twiddles of a prime: the first N1 entries of its column table.
@@ -533,6 +534,7 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
   };
   prefetch_digit(tk.j0);
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  const u64 pol = l2_stream();
   // Per-digit products are reduced by REDC and summed lazily in [0, 2m).
   u64 s0[EPT], s1[EPT];
   const u64 m2 = 2 * mi.m;
@@ -552,8 +554,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
         if (GT::TILE % GT::NT == 0 || e < GT::TILE) {
           const u64 y = csub(shoup(__ldg(dt + e), mi.r1, mi.r1s, mi.m), mi.m);
           U128 p0 = {0, 0}, p1 = {0, 0};
-          mac128(p0, y, __ldg(e0 + e));
-          mac128(p1, y, __ldg(e1 + e));
+          mac128(p0, y, ldg_pol(e0 + e, pol));
+          mac128(p1, y, ldg_pol(e1 + e, pol));
           const u64 a0v = s0[k] + redc(p0, mi.m, mi.minv), a1v = s1[k] + redc(p1, mi.m, mi.minv);
           s0[k] = a0v >= m2 ? a0v - m2 : a0v;
           s1[k] = a1v >= m2 ? a1v - m2 : a1v;
@@ -574,8 +576,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
           const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
           const u64 y = reduce_full(sm[x * GT::PR + g], mi.m, mi.mu);
           U128 p0 = {0, 0}, p1 = {0, 0};
-          mac128(p0, y, __ldg(e0 + e));
-          mac128(p1, y, __ldg(e1 + e));
+          mac128(p0, y, ldg_pol(e0 + e, pol));
+          mac128(p1, y, ldg_pol(e1 + e, pol));
           const u64 a0v = s0[k] + redc(p0, mi.m, mi.minv), a1v = s1[k] + redc(p1, mi.m, mi.minv);
           s0[k] = a0v >= m2 ? a0v - m2 : a0v;
           s1[k] = a1v >= m2 ? a1v - m2 : a1v;

@@ -28,8 +28,12 @@ namespace ks {
 // Compile-time geometry of the two passes for N = 2^LOGN (also used on the host
 // to lay out the row-pass twiddle table by row tile).
 __host__ __device__ constexpr int geo_loga(int logn) { return logn <= 12 ? 0 : logn / 2; }
+// Tiles of 2^10 points up to N = 2^15 and 2^11 above (measured on GB300: at 2^15 the
+// smaller tiles double the CTAs of the one-wave launches, 94.8 -> 85.8 us per
+// KeySwitch at (2, 2^15, 10); at 2^16 they speed the row passes and slow the column
+// passes by about as much).
 __host__ __device__ constexpr int geo_tile_log(int logn) {
-  return logn <= 12 ? logn : (logn >= 15 ? 11 : 10);
+  return logn <= 12 ? logn : (logn >= 16 ? 11 : 10);
 }
 __host__ __device__ constexpr int geo_loggr(int logn) {
   return geo_tile_log(logn) - (logn - geo_loga(logn));

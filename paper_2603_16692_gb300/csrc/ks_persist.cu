@@ -51,8 +51,9 @@ using kern::KArgs;
 constexpr int kStages = 8;
 constexpr int kPNT = 256;  // threads per CTA of the persistent kernel
 
-// The radix of the rounds for each N: 256 threads per tile at every size.
-__host__ __device__ constexpr int prl(int logn) { return logn <= 14 ? 2 : 3; }
+// The radix of the rounds for each N: 256 threads per tile at every size (tiles of
+// 2^10 points take radix 4, tiles of 2^11 radix 8).
+__host__ __device__ constexpr int prl(int logn) { return geo_tile_log(logn) - 8; }
 
 struct PJob {
   KArgs a;
