@@ -30,6 +30,7 @@ __device__ __forceinline__ u64 bconv_point(const u64 *__restrict__ src, size_t N
 
 // ModUp BConv of digit j onto limb t (Montgomery-scaled), TASK_UP item (t, j, slot).
 __global__ void k_bconv_up(EArgs a, JobSet js, WsOff wo, Tasks tk) {
+  pdl_wait();
   __shared__ u64 cst[kMaxLimbs];
   const JobPtr jp = js.j[blockIdx.z];
   const u64 *v = jp.ws + wo.v;
@@ -46,10 +47,12 @@ __global__ void k_bconv_up(EArgs a, JobSet js, WsOff wo, Tasks tk) {
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
        n += (size_t)gridDim.x * blockDim.x)
     o[n] = bconv_point(v + (size_t)i0 * N, N, n, ns, cst, a.run_up, mi);
+  pdl_trigger();
 }
 
 // ModDown BConv of the P-limbs of polynomial c onto q_i, TASK_DOWN item (i, c, slot).
 __global__ void k_bconv_down(EArgs a, JobSet js, WsOff wo, Tasks tk) {
+  pdl_wait();
   __shared__ u64 cst[kMaxLimbs];
   const JobPtr jp = js.j[blockIdx.z];
   const u64 *vp = jp.ws + wo.vp;
@@ -65,10 +68,12 @@ __global__ void k_bconv_down(EArgs a, JobSet js, WsOff wo, Tasks tk) {
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
        n += (size_t)gridDim.x * blockDim.x)
     o[n] = bconv_point(vp + (size_t)c * a.np * N, N, n, a.np, cst, a.run_down, mi);
+  pdl_trigger();
 }
 
 // acc_c[t] (+)= sum_{j0 <= j < j1} ext_j[t] * evk[j][c][t], TASK_TARGET item t.
 __global__ void k_keymult(EArgs a, JobSet js, WsOff wo, Tasks tk) {
+  pdl_wait();
   const JobPtr jp = js.j[blockIdx.z];
   const u64 *tmp = jp.ws + wo.tmp;
   u64 *acc = jp.ws + wo.acc;
@@ -99,10 +104,12 @@ __global__ void k_keymult(EArgs a, JobSet js, WsOff wo, Tasks tk) {
     *a0 = r0v;
     *a1 = r1v;
   }
+  pdl_trigger();
 }
 
 // out_c[i] = (acc_c[i] - zhat) * P^-1, TASK_DOWN item (i, c, slot of zhat).
 __global__ void k_moddown_scale(EArgs a, JobSet js, WsOff wo, Tasks tk) {
+  pdl_wait();
   const JobPtr jp = js.j[blockIdx.z];
   const uint32_t w = decode(a, tk, blockIdx.y);
   const int i = task_limb(w), c = task_dig(w);
@@ -117,6 +124,7 @@ __global__ void k_moddown_scale(EArgs a, JobSet js, WsOff wo, Tasks tk) {
        n += (size_t)gridDim.x * blockDim.x)
     o[n] = kern::out_word(jp, c, ob + n,
                           csub(shoup(__ldg(ac + n) + m - __ldg(z + n), pv.x, pv.y, m), m), m);
+  pdl_trigger();
 }
 
 // polys [2 + beta][QP][N]: 0 = s_from, 1 = s_to, 2 + j = e_j, as residues mod each prime.
@@ -208,6 +216,7 @@ __device__ __forceinline__ u64 mulmod2_full(u64 x, u64 y, u64 z, u64 w, const Mo
 // HMUL tensor product, limb i = blockIdx.y. Each thread reads its four words before
 // it writes, so out may alias x or y.
 __global__ void k_tensor(EArgs a, const u64 *x, const u64 *y, u64 *out, u64 *d2) {
+  pdl_wait();
   const int i = blockIdx.y;
   const ModInfo mi = a.tab.mod[i];
   const size_t N = a.N, P = (size_t)a.nq * N, off = (size_t)i * N;
@@ -221,6 +230,7 @@ __global__ void k_tensor(EArgs a, const u64 *x, const u64 *y, u64 *out, u64 *d2)
     out[P + off + n] = r1;
     d2[off + n] = r2;
   }
+  pdl_trigger();
 }
 
 // Galois automorphism in the NTT domain. Slot j holds a(w_j), w_j = psi^(2 brv(j) + 1);
@@ -228,6 +238,7 @@ __global__ void k_tensor(EArgs a, const u64 *x, const u64 *y, u64 *out, u64 *d2)
 // so the automorphism is the gather y[j] = x[j']. Limb i = blockIdx.y, c = blockIdx.z.
 __global__ void k_automorph(EArgs a, int logn, const u64 *__restrict__ ct, unsigned k,
                             u64 *y0, u64 *y1) {
+  pdl_wait();
   const int i = blockIdx.y, c = blockIdx.z;
   const size_t N = a.N;
   const u64 *x = ct + ((size_t)c * a.nq + i) * N;
@@ -239,6 +250,7 @@ __global__ void k_automorph(EArgs a, int logn, const u64 *__restrict__ ct, unsig
     const unsigned src = __brev((e - 1u) >> 1) >> sh;
     y[n] = __ldg(x + src);
   }
+  pdl_trigger();
 }
 
 int ew_blocks(size_t N) {
@@ -251,30 +263,30 @@ int ew_blocks(size_t N) {
 cudaError_t launch_bconv_up(const ks_context *c, const JobSet &js, const WsOff &o,
                             const Tasks &tk, int count, cudaStream_t s) {
   if (count == 0 || js.n == 0) return cudaSuccess;
-  k_bconv_up<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
-  return cudaGetLastError();
+  return launch_pdl(k_bconv_up, dim3(ew_blocks(c->N), count, js.n), dim3(256), 0, s, eargs(c),
+                    js, o, tk);
 }
 
 cudaError_t launch_bconv_down(const ks_context *c, const JobSet &js, const WsOff &o,
                               const Tasks &tk, int count, cudaStream_t s) {
   if (count == 0 || js.n == 0) return cudaSuccess;
-  k_bconv_down<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
-  return cudaGetLastError();
+  return launch_pdl(k_bconv_down, dim3(ew_blocks(c->N), count, js.n), dim3(256), 0, s, eargs(c),
+                    js, o, tk);
 }
 
 cudaError_t launch_keymult(const ks_context *c, const JobSet &js, const WsOff &o,
                            const Tasks &tk, cudaStream_t s) {
   const int count = tk.t1 - tk.t0;
   if (count <= 0 || js.n == 0) return cudaSuccess;
-  k_keymult<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
-  return cudaGetLastError();
+  return launch_pdl(k_keymult, dim3(ew_blocks(c->N), count, js.n), dim3(256), 0, s, eargs(c), js,
+                    o, tk);
 }
 
 cudaError_t launch_moddown_scale(const ks_context *c, const JobSet &js, const WsOff &o,
                                  const Tasks &tk, int count, cudaStream_t s) {
   if (count == 0 || js.n == 0) return cudaSuccess;
-  k_moddown_scale<<<dim3(ew_blocks(c->N), count, js.n), 256, 0, s>>>(eargs(c), js, o, tk);
-  return cudaGetLastError();
+  return launch_pdl(k_moddown_scale, dim3(ew_blocks(c->N), count, js.n), dim3(256), 0, s,
+                    eargs(c), js, o, tk);
 }
 
 cudaError_t launch_keygen_lift(const ks_context *c, const int8_t *sf, const int8_t *st,
@@ -291,14 +303,14 @@ cudaError_t launch_keygen_square(const ks_context *c, u64 *polys, cudaStream_t s
 
 cudaError_t launch_tensor(const ks_context *c, const u64 *x, const u64 *y, u64 *out, u64 *d2,
                           cudaStream_t s) {
-  k_tensor<<<dim3(ew_blocks(c->N), c->nq), 256, 0, s>>>(eargs(c), x, y, out, d2);
-  return cudaGetLastError();
+  return launch_pdl(k_tensor, dim3(ew_blocks(c->N), c->nq), dim3(256), 0, s, eargs(c), x, y, out,
+                    d2);
 }
 
 cudaError_t launch_automorph(const ks_context *c, const u64 *ct, unsigned k, u64 *y0, u64 *y1,
                              cudaStream_t s) {
-  k_automorph<<<dim3(ew_blocks(c->N), c->nq, 2), 256, 0, s>>>(eargs(c), c->logn, ct, k, y0, y1);
-  return cudaGetLastError();
+  return launch_pdl(k_automorph, dim3(ew_blocks(c->N), c->nq, 2), dim3(256), 0, s, eargs(c),
+                    c->logn, ct, k, y0, y1);
 }
 
 cudaError_t launch_keygen_combine(const ks_context *c, const u64 *polys, const u64 *arand,

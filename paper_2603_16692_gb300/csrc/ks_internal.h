@@ -141,6 +141,25 @@ struct ks_context {
 
 namespace ks {
 
+// Launch `kernel` on s with programmatic stream serialization allowed: it may start
+// while the previous kernel of the stream finishes (the kernels synchronise with
+// griddepcontrol.wait before touching shared buffers).
+template <class... KT, class... AT>
+inline cudaError_t launch_pdl(void (*kernel)(KT...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, AT &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<AT &&>(args)...);
+}
+
 // Host-side helpers (ks_host.cu)
 int build_tables(ks_context *ctx);
 bool is_prime_u64(u64 n);

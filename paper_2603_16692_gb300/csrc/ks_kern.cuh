@@ -362,6 +362,7 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   const u64 m = a.tab.mod[prime].m, mu = a.tab.mod[prime].mu;
   const size_t N = a.N;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_i, prime, blk), GT::TWR);
+  pdl_wait();
   const ulonglong2 sc = is.scale[ii];
   for (int o = 0; o < is.outer; ++o) {
     load_rows<GT>(sm, is.src + ((size_t)o * is.src_outer + ii) * N, r0);
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
     k_inv_row(KArgs a, JobSet js, WsOff wo, int which) {
   extern __shared__ __align__(16) unsigned char raw[];
   inv_row_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
+  pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
@@ -402,6 +404,7 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
   const int c0 = bx * GT::GC;
   const u64 m = a.tab.mod[prime].m;
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_i, prime), GT::TWC);
+  pdl_wait();
   const ulonglong2 sc = is.scale[ii];
   for (int o = 0; o < is.outer; ++o) {
     u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * (size_t)a.N;
@@ -427,6 +430,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>:
     k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
   extern __shared__ __align__(16) unsigned char raw[];
   inv_col_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
+  pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // Buffers of a forward pass for job jp: the BConv sources and the output buffer.
@@ -461,6 +465,7 @@ __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, c
   const int t = task_limb(w);
   const int c0 = bx * GT::GC;
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_f, t), GT::TWC);
+  pdl_wait();
   produce<GT, PRO, true>(a, sm, cst, w, src, dst, c0);
   __syncthreads();
   tile_fwd<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false, RL>(sm, tws, a.tab.mod[t].m);
@@ -473,6 +478,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   fwd_col_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, buf, blockIdx.x, blockIdx.y, raw, cst);
+  pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // Plain forward row pass: canonical result back in place.
@@ -490,11 +496,13 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   const int t = task_limb(w), blk = blockIdx.x, r0 = blk * GT::GR;
   const u64 m = a.tab.mod[t].m;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  pdl_wait();
   u64 *b = dst + (size_t)task_slot(w) * a.N;
   load_rows<GT>(sm, b, r0);
   __syncthreads();
   tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
   store_rows<GT>(b, sm, r0, m, a.tab.mod[t].mu);
+  pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // ModUp row pass fused with the key multiply. One CTA = one row tile of one
@@ -534,6 +542,7 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
   };
   prefetch_digit(tk.j0);
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  pdl_wait();
   const u64 pol = l2_stream();
   // Per-digit products are reduced by REDC and summed lazily in [0, 2m).
   u64 s0[EPT], s1[EPT];
@@ -609,6 +618,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>:
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   keymult_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
+  pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // ModDown row pass fused with the final scaling, both polynomials c = 0, 1 of
@@ -631,6 +641,7 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
   if (threadIdx.x == 0)
     for (int c = 0; c < 2; ++c) prefetch_l2(acc + ((size_t)c * a.qp + i) * N + off0, GT::TILE * 8);
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
+  pdl_wait();
   for (int c = 0; c < 2; ++c) {
     const uint32_t wc = pack_task(i, c, task_slot(w) + c * tk.span);
     if (GT::LOGA == 0)
@@ -672,6 +683,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   moddown_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
+  pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // ---------------------------------------------------------------------------
@@ -715,18 +727,16 @@ struct Launch {
                               cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
     if (inner == 0 || js.n == 0) return cudaSuccess;
-    k_inv_row<LOGN, RL><<<dim3(GRID_ROW, inner, js.n), GT::NT, GT::SMEM_ROW, s>>>(
-          args_of(c), js, wo, which);
-    return cudaGetLastError();
+    return launch_pdl(k_inv_row<LOGN, RL>, dim3(GRID_ROW, inner, js.n), dim3(GT::NT),
+                      GT::SMEM_ROW, s, args_of(c), js, wo, which);
   }
 
   static cudaError_t intt_col(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
                               cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
     if (GT::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
-    k_inv_col<LOGN, RL><<<dim3(GRID_COL, inner, js.n), GT::NT, GT::SMEM_COL, s>>>(
-        args_of(c), js, wo, which);
-    return cudaGetLastError();
+    return launch_pdl(k_inv_col<LOGN, RL>, dim3(GRID_COL, inner, js.n), dim3(GT::NT),
+                      GT::SMEM_COL, s, args_of(c), js, wo, which);
   }
 
   template <int PRO>
@@ -734,9 +744,8 @@ struct Launch {
                          const Tasks &tk, int buf, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (GT::LOGA == 0 || n == 0 || js.n == 0) return cudaSuccess;
-    k_fwd_col<LOGN, RL, PRO><<<dim3(GRID_COL, n, js.n), GT::NT, GT::SMEM_COL, s>>>(
-        args_of(c), js, wo, tk, buf);
-    return cudaGetLastError();
+    return launch_pdl(k_fwd_col<LOGN, RL, PRO>, dim3(GRID_COL, n, js.n), dim3(GT::NT),
+                      GT::SMEM_COL, s, args_of(c), js, wo, tk, buf);
   }
 
   static cudaError_t modup_col(const ks_context *c, const JobSet &js, const WsOff &wo,
@@ -753,18 +762,16 @@ struct Launch {
                                const Tasks &tk, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
-    k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW,
-                                                s>>>(args_of(c), js, wo, tk);
-    return cudaGetLastError();
+    return launch_pdl(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, dim3(GRID_ROW, n, js.n),
+                      dim3(GT::NT), GT::SMEM_ROW, s, args_of(c), js, wo, tk);
   }
 
   static cudaError_t moddown_row(const ks_context *c, const JobSet &js, const WsOff &wo,
                                  const Tasks &tk, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
-    k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW,
-                                                  s>>>(args_of(c), js, wo, tk);
-    return cudaGetLastError();
+    return launch_pdl(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, dim3(GRID_ROW, n, js.n),
+                      dim3(GT::NT), GT::SMEM_ROW, s, args_of(c), js, wo, tk);
   }
 
   static cudaError_t ntt_col(const ks_context *c, const JobSet &js, const WsOff &wo,
@@ -776,9 +783,8 @@ struct Launch {
                              const Tasks &tk, int buf, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
-    k_fwd_row_store<LOGN, RL><<<dim3(GRID_ROW, n, js.n), GT::NT, GT::SMEM_ROW, s>>>(
-          args_of(c), js, wo, tk, buf);
-    return cudaGetLastError();
+    return launch_pdl(k_fwd_row_store<LOGN, RL>, dim3(GRID_ROW, n, js.n), dim3(GT::NT),
+                      GT::SMEM_ROW, s, args_of(c), js, wo, tk, buf);
   }
 
   static const LaunchTable &table() {
