@@ -188,9 +188,13 @@ int ks_hrot(ks_context *ctx, const uint64_t *ct_dev, uint32_t galois_elt,
             const uint64_t *rtk_dev, uint64_t *out_dev, int variant, int chunks, void *ws,
             size_t ws_bytes, void *stream);
 
-/* ks_switch with host buffers: copies d_host to the device, switches, copies the
- * result to out_host, and synchronizes `stream` before returning. Pinned host
- * memory gives the full copy bandwidth. evk stays device-resident. */
+/* ks_switch with host buffers d_host [L+1][N] and out_host [2][L+1][N]; evk stays
+ * device-resident; synchronizes `stream` before returning.
+ *   Pinned (page-locked, device-mapped) buffers: the first kernel reads the input
+ *   straight from host memory over the CPU-GPU link and the last kernel writes the
+ *   result straight into host memory (no staging copies).
+ *   Pageable buffers: copied through device staging buffers owned by the context.
+ * Both host buffers must stay valid and unmodified by other threads until return. */
 int ks_switch_host(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
                    uint64_t *out_host, int variant, int chunks, void *stream);
 

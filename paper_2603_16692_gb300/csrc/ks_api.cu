@@ -470,6 +470,18 @@ int keygen_impl(ks_context *c, const int8_t *s_from, const int8_t *s_to, unsigne
   return rc;
 }
 
+// Device address of a pinned (page-locked, device-mapped) host buffer, or null for
+// pageable memory and device memory.
+const u64 *host_mapped(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  return (const u64 *)at.devicePointer;
+}
+
 // At most this many graphs are kept per context (least recently used dropped).
 constexpr size_t kGraphCache = 32;
 
@@ -505,6 +517,10 @@ int cached_launch(ks_context *c, const std::array<uintptr_t, 10> &key, cudaStrea
     return enqueue(s);
   }
   it->second.last = ++c->gclock;
+  if (it->second.direct) {
+    lk.unlock();
+    return enqueue(s);
+  }
   if (!it->second.exec) {
     if (!c->gstream && cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) {
       cudaGetLastError();
@@ -519,10 +535,11 @@ int cached_launch(ks_context *c, const std::array<uintptr_t, 10> &key, cudaStrea
     if (rc == KS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, gr, 0);
     if (gr) cudaGraphDestroy(gr);
     if (rc != KS_OK || e != cudaSuccess || !exec) {
+      // not capturable: run this key directly from now on (a real error shows again)
       cudaGetLastError();
-      c->gcache.erase(it);
+      it->second.direct = true;
       lk.unlock();
-      return rc != KS_OK ? rc : enqueue(s);
+      return enqueue(s);
     }
     it->second.exec = exec;
   }
@@ -823,10 +840,38 @@ int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, u
   }
   uint64_t *din = (uint64_t *)c->stage;
   uint64_t *dout = din + (size_t)c->nq * c->N;
-  KS_TRY(cudaMemcpyAsync(din, d_host, in_b, cudaMemcpyHostToDevice, s));
-  int rc = ks_switch(c, din, evk, dout, variant, chunks, nullptr, 0, stream);
+  if (!aligned16(evk)) return KS_EALIGN;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
   if (rc) return rc;
-  KS_TRY(cudaMemcpyAsync(out_host, dout, out_b, cudaMemcpyDeviceToHost, s));
+  // Pinned (device-mapped) host buffers: the first kernel reads the input from host
+  // memory over the CPU-GPU link (leaving a device copy for the key multiply) and the
+  // last kernel writes the result straight into host memory - no staging copies.
+  // Otherwise: copy in, KeySwitch, copy out. Either way one cached graph per
+  // (plan, buffers, stream) where it can be captured.
+  const u64 *d_map = host_mapped(d_host);
+  u64 *out_map = const_cast<u64 *>(host_mapped(out_host));
+  const bool mapped = d_map && out_map;
+  rc = with_workspace(c, nullptr, 0, pl.total * 8, [&](u64 *base) {
+    JobSet js = {};
+    js.n = 1;
+    js.j[0].d = (const u64 *)din;
+    js.j[0].evk = (const u64 *)evk;
+    js.j[0].out = mapped ? out_map : (u64 *)dout;
+    js.j[0].ws = base;
+    js.j[0].dsrc = mapped ? d_map : nullptr;
+    const std::array<uintptr_t, 10> key = {
+        3, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)d_host, (uintptr_t)evk,
+        (uintptr_t)din, (uintptr_t)out_host, (uintptr_t)base, (uintptr_t)s, 0};
+    return cached_launch(c, key, s, [&](cudaStream_t q) {
+      if (!mapped) KS_TRY(cudaMemcpyAsync(din, d_host, in_b, cudaMemcpyHostToDevice, q));
+      const int r = run_plan(c, pl, js, q);
+      if (r) return r;
+      if (!mapped) KS_TRY(cudaMemcpyAsync(out_host, dout, out_b, cudaMemcpyDeviceToHost, q));
+      return (int)KS_OK;
+    });
+  });
+  if (rc) return rc;
   KS_TRY(cudaStreamSynchronize(s));
   return KS_OK;
 }

@@ -68,6 +68,8 @@ struct JobPtr {
   u64 *ws;         // this job's workspace
   const u64 *add;  // optional addend [2][L+1][N] (may alias out): out_c += add_c when
   int addmask;     // bit c of addmask is set (HMUL / HROT epilogues); 0 = plain store
+  const u64 *dsrc; // optional: the input in (pinned, device-mapped) host memory; the
+                   // input iNTT reads it and leaves a device copy in d
 };
 struct JobSet {
   int n;
@@ -133,6 +135,7 @@ struct ks_context {
   struct CachedGraph {
     cudaGraphExec_t exec = nullptr;  // null: seen once, not captured yet
     unsigned long long last = 0;
+    bool direct = false;  // capture failed (e.g. pageable host memory): launch directly
   };
   std::map<std::array<uintptr_t, 10>, CachedGraph> gcache;
   unsigned long long gclock = 0;

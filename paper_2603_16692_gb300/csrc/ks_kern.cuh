@@ -123,6 +123,25 @@ __device__ __forceinline__ void load_rows(u64 *s, const u64 *src, int r0) {
   }
 }
 
+// load_rows that also writes the loaded words to `copy` (same layout): the input
+// read from host memory leaves its device copy on the way.
+template <class GT>
+__device__ __forceinline__ void load_rows_copy(u64 *s, const u64 *src, u64 *copy, int r0) {
+  constexpr int TILE = GT::TILE, LOGB = GT::LOGB, P = GT::PR;
+  const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src + ((size_t)r0 << LOGB));
+  ulonglong2 *c2 = reinterpret_cast<ulonglong2 *>(copy + ((size_t)r0 << LOGB));
+#pragma unroll
+  for (int it = 0; it < (TILE / 2 + GT::NT - 1) / GT::NT; ++it) {
+    const int e2 = threadIdx.x + it * GT::NT;
+    if ((TILE / 2) % GT::NT != 0 && e2 >= TILE / 2) break;
+    const ulonglong2 val = s2[e2];
+    c2[e2] = val;
+    const int e = 2 * e2, g = e >> LOGB, x = e & ((1 << LOGB) - 1);
+    s[x * P + g] = val.x;
+    s[(x + 1) * P + g] = val.y;
+  }
+}
+
 template <class GT>
 __device__ __forceinline__ void store_rows(u64 *dst, const u64 *s, int r0, u64 m, u64 mu) {
   // lazy values -> canonical
@@ -365,7 +384,11 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   pdl_wait();
   const ulonglong2 sc = is.scale[ii];
   for (int o = 0; o < is.outer; ++o) {
-    load_rows<GT>(sm, is.src + ((size_t)o * is.src_outer + ii) * N, r0);
+    if (which == 0 && jp.dsrc)
+      load_rows_copy<GT>(sm, jp.dsrc + (size_t)ii * N, const_cast<u64 *>(jp.d) + (size_t)ii * N,
+                         r0);
+    else
+      load_rows<GT>(sm, is.src + ((size_t)o * is.src_outer + ii) * N, r0);
     __syncthreads();
     tile_inv<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
     u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * N;

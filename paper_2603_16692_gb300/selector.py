@@ -1,13 +1,17 @@
 """Learned dataflow selector (the parameter-aware choice the paper proposes in Sec. V).
 
-A 6 -> 64 -> 64 -> 4 FP32 MLP predicts the log-latency of four candidate plans
-from workload features; the selected plan is the argmin. The candidates are the
-plans that compete on GB300 in the library's own sweep of ten plans (four
-dataflows x radix 8 / radix 4, OutputChunked with 2 and 4 chunks): DSOB, DPOB,
-DPOB with radix-4 rounds, and DPOC with 2 chunks. Training and inference run in
-the library's CUDA kernels (ks_mlp_train, ks_mlp_forward). Exhaustive timing of
-all ten plans stays the fallback and judges the regret. The selector never
-touches the KeySwitch arithmetic.
+A 6 -> 64 -> 64 -> 4 FP32 MLP predicts the latency of four candidate plans from
+workload features; the selected plan is the argmin. The candidates are the plans
+that compete on GB300 in the library's own sweep of ten plans (four dataflows x
+radix 8 / radix 4, OutputChunked with 2 and 4 chunks): DPOB, DSOB, DPOB with
+radix-4 rounds, and DPOC with 2 chunks. Output 0 is the log-latency of DPOB,
+outputs 1-3 the log-ratios of the other candidates to it (each output standardised
+over the training rows): the latencies span three orders of magnitude across
+workloads while the choice depends on differences of a few percent, which an
+absolute-log target leaves almost unweighted. Training and inference run in the
+library's CUDA kernels (ks_mlp_train, ks_mlp_forward). Exhaustive timing of all
+ten plans stays the fallback and judges the regret. The selector never touches
+the KeySwitch arithmetic.
 
 Features of (dnum, N, L) on a GPU with L2 bytes: log2 N, L+1, dnum, and log2 of
 (DPOB footprint / L2), (DSOB footprint / L2), (evk bytes / L2), where the
@@ -24,8 +28,18 @@ import numpy as np
 from . import ks
 from . import workload as W
 
-CANDS = [("DSOB", ks.KS_DSOB, 0), ("DPOB", ks.KS_DPOB, 0),
+CANDS = [("DPOB", ks.KS_DPOB, 0), ("DSOB", ks.KS_DSOB, 0),
          ("DPOB-r4", ks.KS_DPOB | ks.KS_RADIX4, 0), ("DPOC-c2", ks.KS_DPOC, 2)]
+
+
+def encode(log_ms: np.ndarray) -> np.ndarray:
+    """Targets from candidate log-latencies: [log t_0, log t_k - log t_0 (k >= 1)]."""
+    return np.concatenate([log_ms[:, :1], log_ms[:, 1:] - log_ms[:, :1]], axis=1)
+
+
+def decode(enc: np.ndarray) -> np.ndarray:
+    """Candidate log-latencies from network outputs (inverse of encode)."""
+    return np.concatenate([enc[:, :1], enc[:, 1:] + enc[:, :1]], axis=1)
 DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 
 
@@ -133,7 +147,9 @@ class Selector:
         self.params = np.asarray(params, dtype=np.float32)
         self.x_mean = np.asarray(x_mean, dtype=np.float64)
         self.x_std = np.asarray(x_std, dtype=np.float64)
-        self.t_mean, self.t_std, self.l2 = float(t_mean), float(t_std), int(l2)
+        self.t_mean = np.asarray(t_mean, dtype=np.float64)  # per output
+        self.t_std = np.asarray(t_std, dtype=np.float64)
+        self.l2 = int(l2)
 
     def norm_x(self, feats) -> np.ndarray:
         return ((np.asarray(feats, dtype=np.float64) - self.x_mean) / self.x_std).astype(np.float32)
@@ -151,15 +167,15 @@ class Selector:
             ks.ks_mlp_forward(p, xs, ys)
             y[s:s + xs.shape[0]] = ys
         torch.cuda.synchronize()
-        return np.exp(y.cpu().numpy().astype(np.float64) * self.t_std + self.t_mean)
+        return np.exp(decode(y.cpu().numpy().astype(np.float64) * self.t_std + self.t_mean))
 
     def choose(self, prms) -> list:
         return [int(k) for k in np.argmin(self.predict_ms(prms), axis=1)]
 
     def to_json(self) -> dict:
         return {"params": self.params.tolist(), "x_mean": self.x_mean.tolist(),
-                "x_std": self.x_std.tolist(), "t_mean": self.t_mean, "t_std": self.t_std,
-                "l2": self.l2, "cands": [n for n, _, _ in CANDS]}
+                "x_std": self.x_std.tolist(), "t_mean": self.t_mean.tolist(),
+                "t_std": self.t_std.tolist(), "l2": self.l2, "cands": [n for n, _, _ in CANDS]}
 
     @staticmethod
     def from_json(d) -> "Selector":
@@ -183,9 +199,9 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
     l2 = data["l2"]
     X = np.array([features(prms[i], l2) for i in idx], dtype=np.float64)
     cols = columns(data)
-    T = np.log(np.array([data["ms"][i] for i in idx], dtype=np.float64)[:, cols])
+    T = encode(np.log(np.array([data["ms"][i] for i in idx], dtype=np.float64)[:, cols]))
     x_mean, x_std = X.mean(0), X.std(0) + 1e-9
-    t_mean, t_std = T.mean(), T.std() + 1e-9
+    t_mean, t_std = T.mean(0), T.std(0) + 1e-9
     sel = Selector(init_params(seed), x_mean, x_std, t_mean, t_std, l2)
     dev = torch.device("cuda")
     x = torch.from_numpy(np.ascontiguousarray(sel.norm_x(X))).to(dev)

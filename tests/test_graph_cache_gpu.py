@@ -68,3 +68,35 @@ def test_hmul_and_hrot_replays():
             assert np.array_equal(host(out), want), f"hrot call {rep}"
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_entry_replays(pinned):
+    """ks_switch_host: pinned buffers are captured with their copies into one graph;
+    pageable buffers cannot be captured and keep running directly. Every call must
+    return the oracle's result for the current contents."""
+    import torch
+    cfg = (2, 13, 6)
+    cases = [oracle_case(cfg, s) for s in (0, 1, 2)]
+    prm = cases[0][0]
+    ctx = ks.Context(prm)
+    try:
+        evk = dev(cases[0][6])
+        if pinned:
+            d_h = torch.empty((prm.L + 1, prm.N), dtype=torch.uint64).pin_memory()
+            out_h = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64).pin_memory()
+        else:
+            d_h = np.empty((prm.L + 1, prm.N), dtype=np.uint64)
+            out_h = np.empty((2, prm.L + 1, prm.N), dtype=np.uint64)
+        for rep in range(5):
+            c = cases[rep % 3]
+            evk.copy_(torch.from_numpy(c[6]).cuda())
+            if pinned:
+                d_h.copy_(torch.from_numpy(c[5]))
+            else:
+                d_h[...] = c[5]
+            ks.ks_switch_host(ctx.h, d_h, evk, out_h)
+            got = out_h.numpy() if pinned else out_h
+            assert np.array_equal(got, c[7]), f"call {rep}: " + first_mismatch(got, c[7])
+    finally:
+        ctx.close()

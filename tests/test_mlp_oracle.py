@@ -38,3 +38,14 @@ def test_masked_entries_do_not_contribute():
     t2 = t.copy()
     t2[:, 1] += 100.0
     assert np.allclose(M.loss_and_grad(p, x, t, mask)[1], M.loss_and_grad(p, x, t2, mask)[1])
+
+
+def test_selector_target_encoding_round_trips():
+    """Output 0 is the first candidate's log-latency, the others are log-ratios to it."""
+    from paper_2603_16692_gb300 import selector as S
+    g = np.random.default_rng(3)
+    L = np.log(g.uniform(0.01, 10.0, size=(7, 4)))
+    E = S.encode(L)
+    assert np.allclose(E[:, 0], L[:, 0])
+    assert np.allclose(E[:, 1:], L[:, 1:] - L[:, :1])
+    assert np.allclose(S.decode(E), L)
