@@ -372,7 +372,7 @@ __device__ __forceinline__ InttSet intt_set(const KArgs &a, const JobPtr &jp, co
 template <int LOGN, int RL>
 __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              int which, int bx, int by, unsigned char *raw) {
-  using GT = GeoT<LOGN, RL>;
+  using GT = GeoT<LOGN, RL, 1>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
   const InttSet is = intt_set(a, jp, wo, which);
@@ -407,7 +407,7 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
 }
 
 template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
     k_inv_row(KArgs a, JobSet js, WsOff wo, int which) {
   extern __shared__ __align__(16) unsigned char raw[];
   inv_row_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
 template <int LOGN, int RL>
 __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              int which, int bx, int by, unsigned char *raw) {
-  using GT = GeoT<LOGN, RL>;
+  using GT = GeoT<LOGN, RL, 0>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
   const InttSet is = intt_set(a, jp, wo, which);
@@ -449,7 +449,8 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
 }
 
 template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 512 : 768))
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT,
+                                  min_blocks(GeoT<LOGN, RL, 0>::NT, RL == 4 ? 512 : 768))
     k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
   extern __shared__ __align__(16) unsigned char raw[];
   inv_col_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
@@ -478,7 +479,7 @@ template <int LOGN, int RL, int PRO>
 __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int buf, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
-  using GT = GeoT<LOGN, RL>;
+  using GT = GeoT<LOGN, RL, 0>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
   const u64 *src;
@@ -496,7 +497,7 @@ __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, c
 }
 
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT)
     k_fwd_col(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
@@ -506,9 +507,9 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
 
 // Plain forward row pass: canonical result back in place.
 template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
     k_fwd_row_store(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
-  using GT = GeoT<LOGN, RL>;
+  using GT = GeoT<LOGN, RL, 1>;
   extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
@@ -539,7 +540,7 @@ template <int LOGN, int RL, int PRO>
 __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
-  using GT = GeoT<LOGN, RL>;
+  using GT = GeoT<LOGN, RL, 1>;
   constexpr int EPT = GT::EPT;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
@@ -636,7 +637,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
 }
 
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT, min_blocks(GeoT<LOGN, RL>::NT, RL == 4 ? 384 : 768))
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
+                                  min_blocks(GeoT<LOGN, RL, 1>::NT, RL == 4 ? 384 : 768))
     k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
@@ -651,7 +653,7 @@ template <int LOGN, int RL, int PRO>
 __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
-  using GT = GeoT<LOGN, RL>;
+  using GT = GeoT<LOGN, RL, 1>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
   const u64 *vp = jp.ws + wo.vp, *tmp2 = jp.ws + wo.tmp2, *acc = jp.ws + wo.acc;
@@ -701,7 +703,7 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
 }
 
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL>::NT)
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
     k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
@@ -723,23 +725,24 @@ inline KArgs args_of(const ks_context *c) { return make_args(c); }
 
 template <int LOGN, int RL>
 struct Launch {
-  using GT = GeoT<LOGN, RL>;
-  static constexpr int GRID_COL = GT::LOGA == 0 ? 1 : GT::N2 / GT::GC;
-  static constexpr int GRID_ROW = GT::N1 / GT::GR;
-  static constexpr int PRO_ROW_UP = GT::LOGA == 0 ? PRO_UP : PRO_LOAD;
-  static constexpr int PRO_ROW_DOWN = GT::LOGA == 0 ? PRO_DOWN : PRO_LOAD;
+  using GTC = GeoT<LOGN, RL, 0>;  // column-pass geometry
+  using GTR = GeoT<LOGN, RL, 1>;  // row-pass geometry
+  static constexpr int GRID_COL = GTC::LOGA == 0 ? 1 : GTC::N2 / GTC::GC;
+  static constexpr int GRID_ROW = GTR::N1 / GTR::GR;
+  static constexpr int PRO_ROW_UP = GTR::LOGA == 0 ? PRO_UP : PRO_LOAD;
+  static constexpr int PRO_ROW_DOWN = GTR::LOGA == 0 ? PRO_DOWN : PRO_LOAD;
 
   static cudaError_t prepare() {
     cudaError_t e;
-    if ((e = smem_attr(k_inv_row<LOGN, RL>, GT::SMEM_ROW))) return e;
-    if ((e = smem_attr(k_fwd_row_store<LOGN, RL>, GT::SMEM_ROW))) return e;
-    if ((e = smem_attr(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, GT::SMEM_ROW))) return e;
-    if ((e = smem_attr(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, GT::SMEM_ROW))) return e;
-    if (GT::LOGA > 0) {
-      if ((e = smem_attr(k_inv_col<LOGN, RL>, GT::SMEM_COL))) return e;
-      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_LOAD>, GT::SMEM_COL))) return e;
-      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_UP>, GT::SMEM_COL))) return e;
-      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_DOWN>, GT::SMEM_COL))) return e;
+    if ((e = smem_attr(k_inv_row<LOGN, RL>, GTR::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_store<LOGN, RL>, GTR::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, GTR::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, GTR::SMEM_ROW))) return e;
+    if (GTC::LOGA > 0) {
+      if ((e = smem_attr(k_inv_col<LOGN, RL>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_LOAD>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_UP>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_DOWN>, GTC::SMEM_COL))) return e;
     }
     return cudaSuccess;
   }
@@ -750,25 +753,25 @@ struct Launch {
                               cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
     if (inner == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_inv_row<LOGN, RL>, dim3(GRID_ROW, inner, js.n), dim3(GT::NT),
-                      GT::SMEM_ROW, s, args_of(c), js, wo, which);
+    return launch_pdl(k_inv_row<LOGN, RL>, dim3(GRID_ROW, inner, js.n), dim3(GTR::NT),
+                      GTR::SMEM_ROW, s, args_of(c), js, wo, which);
   }
 
   static cudaError_t intt_col(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
                               cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
-    if (GT::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_inv_col<LOGN, RL>, dim3(GRID_COL, inner, js.n), dim3(GT::NT),
-                      GT::SMEM_COL, s, args_of(c), js, wo, which);
+    if (GTC::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
+    return launch_pdl(k_inv_col<LOGN, RL>, dim3(GRID_COL, inner, js.n), dim3(GTC::NT),
+                      GTC::SMEM_COL, s, args_of(c), js, wo, which);
   }
 
   template <int PRO>
   static cudaError_t col(const ks_context *c, const JobSet &js, const WsOff &wo,
                          const Tasks &tk, int buf, cudaStream_t s) {
     const int n = count_tasks(c, tk);
-    if (GT::LOGA == 0 || n == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_fwd_col<LOGN, RL, PRO>, dim3(GRID_COL, n, js.n), dim3(GT::NT),
-                      GT::SMEM_COL, s, args_of(c), js, wo, tk, buf);
+    if (GTC::LOGA == 0 || n == 0 || js.n == 0) return cudaSuccess;
+    return launch_pdl(k_fwd_col<LOGN, RL, PRO>, dim3(GRID_COL, n, js.n), dim3(GTC::NT),
+                      GTC::SMEM_COL, s, args_of(c), js, wo, tk, buf);
   }
 
   static cudaError_t modup_col(const ks_context *c, const JobSet &js, const WsOff &wo,
@@ -786,7 +789,7 @@ struct Launch {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
     return launch_pdl(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, dim3(GRID_ROW, n, js.n),
-                      dim3(GT::NT), GT::SMEM_ROW, s, args_of(c), js, wo, tk);
+                      dim3(GTR::NT), GTR::SMEM_ROW, s, args_of(c), js, wo, tk);
   }
 
   static cudaError_t moddown_row(const ks_context *c, const JobSet &js, const WsOff &wo,
@@ -794,7 +797,7 @@ struct Launch {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
     return launch_pdl(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, dim3(GRID_ROW, n, js.n),
-                      dim3(GT::NT), GT::SMEM_ROW, s, args_of(c), js, wo, tk);
+                      dim3(GTR::NT), GTR::SMEM_ROW, s, args_of(c), js, wo, tk);
   }
 
   static cudaError_t ntt_col(const ks_context *c, const JobSet &js, const WsOff &wo,
@@ -806,8 +809,8 @@ struct Launch {
                              const Tasks &tk, int buf, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_fwd_row_store<LOGN, RL>, dim3(GRID_ROW, n, js.n), dim3(GT::NT),
-                      GT::SMEM_ROW, s, args_of(c), js, wo, tk, buf);
+    return launch_pdl(k_fwd_row_store<LOGN, RL>, dim3(GRID_ROW, n, js.n), dim3(GTR::NT),
+                      GTR::SMEM_ROW, s, args_of(c), js, wo, tk, buf);
   }
 
   static const LaunchTable &table() {

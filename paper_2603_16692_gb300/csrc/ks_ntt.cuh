@@ -28,24 +28,27 @@ namespace ks {
 // Compile-time geometry of the two passes for N = 2^LOGN (also used on the host
 // to lay out the row-pass twiddle table by row tile).
 __host__ __device__ constexpr int geo_loga(int logn) { return logn <= 12 ? 0 : logn / 2; }
-// Tiles of 2^10 points up to N = 2^15 and 2^11 above (measured on GB300: at 2^15 the
-// smaller tiles double the CTAs of the one-wave launches, 94.8 -> 85.8 us per
-// KeySwitch at (2, 2^15, 10); at 2^16 they speed the row passes and slow the column
-// passes by about as much).
-__host__ __device__ constexpr int geo_tile_log(int logn) {
+// Tiles: 2^10 points up to N = 2^15; above, 2^11 for the column pass and 2^10 for
+// the row pass (measured on GB300: at 2^15 the smaller tiles double the CTAs of the
+// one-wave launches, 94.8 -> 85.8 us per KeySwitch at (2, 2^15, 10); at 2^16 the row
+// passes are faster and the column passes slower with 2^10-point tiles).
+__host__ __device__ constexpr int geo_tile_log_col(int logn) {
   return logn <= 12 ? logn : (logn >= 16 ? 11 : 10);
 }
+__host__ __device__ constexpr int geo_tile_log_row(int logn) { return logn <= 12 ? logn : 10; }
 __host__ __device__ constexpr int geo_loggr(int logn) {
-  return geo_tile_log(logn) - (logn - geo_loga(logn));
+  return geo_tile_log_row(logn) - (logn - geo_loga(logn));
 }
 
 // RL: log2 of the radix of the register rounds; a thread holds 2^RL points.
-template <int LOGN, int RL_ = 3>
+// ROW: geometry of the row pass (1) or of the column pass (0); a kernel runs one pass
+// and uses only that pass's fields.
+template <int LOGN, int RL_, int ROW>
 struct GeoT {
   static constexpr int RL = RL_;
   static constexpr int LOGA = geo_loga(LOGN);  // log N1
   static constexpr int LOGB = LOGN - LOGA;     // log N2
-  static constexpr int TILE_LOG = geo_tile_log(LOGN);
+  static constexpr int TILE_LOG = ROW ? geo_tile_log_row(LOGN) : geo_tile_log_col(LOGN);
   static constexpr int LOGGC = LOGA == 0 ? 0 : TILE_LOG - LOGA;  // columns per column tile
   static constexpr int LOGGR = TILE_LOG - LOGB;                  // rows per row tile
   static constexpr int TILE = 1 << TILE_LOG;

@@ -51,9 +51,10 @@ using kern::KArgs;
 constexpr int kStages = 8;
 constexpr int kPNT = 256;  // threads per CTA of the persistent kernel
 
-// The radix of the rounds for each N: 256 threads per tile at every size (tiles of
-// 2^10 points take radix 4, tiles of 2^11 radix 8).
-__host__ __device__ constexpr int prl(int logn) { return geo_tile_log(logn) - 8; }
+// The radix of the rounds for each N and pass: 256 threads per tile at every size
+// (tiles of 2^10 points take radix 4, tiles of 2^11 radix 8).
+__host__ __device__ constexpr int prl_col(int logn) { return geo_tile_log_col(logn) - 8; }
+__host__ __device__ constexpr int prl_row(int logn) { return geo_tile_log_row(logn) - 8; }
 
 struct PJob {
   KArgs a;
@@ -122,18 +123,18 @@ __device__ int wait_count(const int *flag, int target, PState *st, unsigned long
 template <int LOGN, int STAGE>
 __device__ __forceinline__ void stage_fn(const PJob &J, int which, int bx, int by,
                                       unsigned char *raw, u64 *cst) {
-  constexpr int RL = prl(LOGN);
-  if constexpr (STAGE == 0) kern::inv_row_body<LOGN, RL>(J.a, J.jp, J.wo, which, bx, by, raw);
-  if constexpr (STAGE == 1) kern::inv_col_body<LOGN, RL>(J.a, J.jp, J.wo, which, bx, by, raw);
+  constexpr int RC = prl_col(LOGN), RR = prl_row(LOGN);
+  if constexpr (STAGE == 0) kern::inv_row_body<LOGN, RR>(J.a, J.jp, J.wo, which, bx, by, raw);
+  if constexpr (STAGE == 1) kern::inv_col_body<LOGN, RC>(J.a, J.jp, J.wo, which, bx, by, raw);
   if constexpr (STAGE == 2)
-    kern::fwd_col_body<LOGN, RL, kern::PRO_UP>(J.a, J.jp, J.wo, J.up, BUF_TMP, bx, by, raw, cst);
+    kern::fwd_col_body<LOGN, RC, kern::PRO_UP>(J.a, J.jp, J.wo, J.up, BUF_TMP, bx, by, raw, cst);
   if constexpr (STAGE == 3)
-    kern::keymult_body<LOGN, RL, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.tg, bx, by, raw, cst);
+    kern::keymult_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.tg, bx, by, raw, cst);
   if constexpr (STAGE == 6)
-    kern::fwd_col_body<LOGN, RL, kern::PRO_DOWN>(J.a, J.jp, J.wo, J.dn, BUF_TMP2, bx, by, raw,
+    kern::fwd_col_body<LOGN, RC, kern::PRO_DOWN>(J.a, J.jp, J.wo, J.dn, BUF_TMP2, bx, by, raw,
                                                 cst);
   if constexpr (STAGE == 7)
-    kern::moddown_body<LOGN, RL, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.d1, bx, by, raw, cst);
+    kern::moddown_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.d1, bx, by, raw, cst);
 }
 
 template <int LOGN>
@@ -205,23 +206,26 @@ __global__ void __launch_bounds__(kPNT, 3) k_persist(const PJob *__restrict__ jo
 
 template <int LOGN>
 constexpr int smem_of() {
-  using GT = GeoT<LOGN, prl(LOGN)>;
-  return GT::SMEM_COL > GT::SMEM_ROW ? GT::SMEM_COL : GT::SMEM_ROW;
+  using GC = GeoT<LOGN, prl_col(LOGN), 0>;
+  using GR = GeoT<LOGN, prl_row(LOGN), 1>;
+  return GC::SMEM_COL > GR::SMEM_ROW ? GC::SMEM_COL : GR::SMEM_ROW;
 }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kPSmem =
     cmax(cmax(cmax(smem_of<13>(), smem_of<14>()), cmax(smem_of<15>(), smem_of<16>())),
          smem_of<17>());
 
-static_assert(GeoT<13, prl(13)>::NT == kPNT && GeoT<14, prl(14)>::NT == kPNT &&
-                  GeoT<15, prl(15)>::NT == kPNT && GeoT<16, prl(16)>::NT == kPNT &&
-                  GeoT<17, prl(17)>::NT == kPNT,
-              "one block size for every size");
+template <int LOGN>
+constexpr bool nt_ok() {
+  return GeoT<LOGN, prl_col(LOGN), 0>::NT == kPNT && GeoT<LOGN, prl_row(LOGN), 1>::NT == kPNT;
+}
+static_assert(nt_ok<13>() && nt_ok<14>() && nt_ok<15>() && nt_ok<16>() && nt_ok<17>(),
+              "one block size for every size and pass");
 
 int grid_of(int logn, int which) {
   // column-pass grid (which 1) or row-pass grid (which 0) for N = 2^logn
-  const int loga = geo_loga(logn), logb = logn - loga, tl = geo_tile_log(logn);
-  const int gc = 1 << (tl - loga), gr = 1 << (tl - logb);
+  const int loga = geo_loga(logn), logb = logn - loga;
+  const int gc = 1 << (geo_tile_log_col(logn) - loga), gr = 1 << (geo_tile_log_row(logn) - logb);
   return which ? (1 << logb) / gc : (1 << loga) / gr;
 }
 
@@ -245,7 +249,7 @@ int persist_counts(const PersistBatch &pb, int *njobs, int *nwork, int *ncnt) {
   return KS_OK;
 }
 
-int persist_radix(int logn) { return prl(logn); }
+int persist_radix(int logn) { return prl_col(logn); }
 
 namespace {
 
