@@ -496,8 +496,13 @@ __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, c
   store_cols<GT>(dst + (size_t)task_slot(w) * a.N, sm, c0);
 }
 
+// Tiles of 256+ threads: 4 CTAs per SM (64 registers, a few spilled words) measured
+// 1-3% faster on GB300 at N >= 2^16 than the compiler's 78-register choice; smaller
+// tiles keep that choice.
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT)
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT,
+                                  min_blocks(GeoT<LOGN, RL, 0>::NT,
+                                             GeoT<LOGN, RL, 0>::NT >= 256 ? 1024 : 0))
     k_fwd_col(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
