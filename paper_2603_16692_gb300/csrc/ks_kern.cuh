@@ -708,7 +708,8 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
 }
 
 template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
+                                  min_blocks(GeoT<LOGN, RL, 1>::NT, RL == 4 ? 0 : 1024))
     k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
