@@ -643,7 +643,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
 
 template <int LOGN, int RL, int PRO>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
-                                  min_blocks(GeoT<LOGN, RL, 1>::NT, RL == 4 ? 384 : 768))
+                                  min_blocks(GeoT<LOGN, RL, 1>::NT,
+                                             RL == 4 ? 384 : RL == 2 ? 1024 : 768))
     k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
