@@ -80,6 +80,22 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The maximum of x over all ranks of the process group (x with one process)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time
+    (ranks are independent replicas, so each processed units_per_rank)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def workload_config(prm, variant_name, chunks, unfused, ring, ring_mb, l2_mb):
     return {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
             "N": prm.N, "L": prm.L, "alpha": prm.alpha, "beta": prm.beta, "QP": prm.QP,
@@ -117,7 +133,8 @@ def run_reference(args, prm, rank: int, world: int):
     t_one = one[1]
     budget = 90.0
     steps = max(1, min(args.steps, int(budget / max(t_one, 1e-6))))
-    warm = min(args.warmup, 2)
+    # all requested warm-up steps, unless they alone would exceed ~30 s (then >= 3)
+    warm = min(args.warmup, max(3, int(30.0 / max(t_one, 1e-6))))
     for _ in range(warm):
         oracle_sample(prm, 0.0, 1)
     reps, el, cores = oracle_sample(prm, 1e9, steps)
@@ -129,7 +146,9 @@ def run_reference(args, prm, rank: int, world: int):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
-                       "N": prm.N, "L": prm.L},
+                       "N": prm.N, "L": prm.L, "alpha": prm.alpha, "beta": prm.beta,
+                       "QP": prm.QP, "qbits": 50, "pbits": 60,
+                       "variant": "oracle (schoolbook, host cores)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -465,12 +484,8 @@ def main():
     barrier()
     t_wall1 = time.time()
     sampler.mark(t_wall0, t_wall1)
-    el_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([el_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
-    value = world * args.steps / (el_ms / 1e3)
+    el_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    value = job_rate(world, args.steps, el_ms)
 
     # per-kernel event timing over a second pass of the same steps (kept out of `value`)
     kprof = min(args.steps, 500)
@@ -480,7 +495,8 @@ def main():
     stats = ks.ks_profile_end()
     launches_per_step = sum(s["launches"] for s in stats) / kprof
 
-    # end to end through the host-buffer entry point (pinned memory, copies in the region)
+    # end to end through the host-buffer entry point: pinned host buffers, the input read
+    # from and the result written to host memory inside the timed region
     d_h = torch.from_numpy(W.gen_input(prm, 0)).pin_memory()
     out_h = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64).pin_memory()
     ke = max(10, min(args.steps, 1000))
@@ -495,12 +511,8 @@ def main():
     e1.record(stream)
     barrier()
     sampler.mark(t_wall2, time.time())
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * ke / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e2e_value = job_rate(world, ke, e2e_ms)
     clocks = sampler.stop()
 
     if rank != 0:

@@ -1,0 +1,66 @@
+"""The bench's multi-rank path on CPU: world_size-2 gloo process group on 127.0.0.1.
+
+Ranks are independent replicas (no data-path collective); the only cross-rank steps
+are the barrier and the maximum of the timed region over ranks, from which rank 0
+reports the whole-job throughput. The reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, results):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dist.barrier()
+        local_ms = 10.0 + 5.0 * rank  # rank 1 is the slow one
+        ms = bench.max_over_ranks(local_ms, dist, "cpu")
+        results[rank] = (ms, bench.job_rate(world, 100, ms))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_report_the_slowest_rank_and_the_whole_job_rate():
+    world = 2
+    with mp.Manager() as mgr:
+        results = mgr.dict()
+        mp.start_processes(_rank, args=(world, _free_port(), results), nprocs=world,
+                           start_method="spawn", join=True)
+        got = dict(results)
+    assert set(got) == {0, 1}
+    for rank in range(world):
+        ms, rate = got[rank]
+        assert ms == 15.0  # the maximum over ranks, seen by every rank
+        assert rate == pytest.approx(world * 100 / 0.015)
+
+
+def test_one_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+    assert bench.job_rate(1, 10, 5.0) == pytest.approx(2000.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2603_16692_gb300 import workload as W
+    # rank 1 of 2 returns at once, before looking at its arguments, timing or printing
+    bench.run_reference(None, W.make_params(*W.C1), rank=1, world=2)
+    assert capsys.readouterr().out == ""
