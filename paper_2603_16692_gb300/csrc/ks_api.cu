@@ -498,6 +498,15 @@ void drop_graph_cache(ks_context *c) {
 // stream into a CUDA graph (the kernel chain then launches without per-kernel
 // launch gaps); later calls replay it. While the library profiler is on, every
 // call runs directly (per-launch events need the individual launches).
+//
+// Which operations use it (measured on GB300): the kernels of an operation are
+// chained by programmatic dependent launch, which also overlaps consecutive
+// operations on a stream when they are launched directly but not across graph
+// launches. Directly launched, (2, 2^15, 10) runs at 76.7 us per KeySwitch against
+// 83.0 us replayed from graphs. Graphs are used where launches cost more than they
+// overlap: single-pass sizes (N <= 2^12, a few microseconds of GPU work per kernel)
+// and the synchronous host-buffer entry point (one launch per call).
+bool use_graphs(const ks_context *c) { return c->loga == 0; }
 template <class F>
 int cached_launch(ks_context *c, const std::array<uintptr_t, 10> &key, cudaStream_t s,
                   F enqueue) {
@@ -813,6 +822,7 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
     const std::array<uintptr_t, 10> key = {
         0, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)d, (uintptr_t)evk, 0,
         (uintptr_t)out, (uintptr_t)base, (uintptr_t)s, 0};
+    if (!use_graphs(c)) return run_plan(c, pl, js, s);
     return cached_launch(c, key, s, [&](cudaStream_t q) { return run_plan(c, pl, js, q); });
   });
 }
@@ -929,10 +939,11 @@ int ks_hmul(ks_context *c, const uint64_t *ct1, const uint64_t *ct2, const uint6
     const std::array<uintptr_t, 10> key = {
         1, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)ct1, (uintptr_t)ct2,
         (uintptr_t)rlk, (uintptr_t)out, (uintptr_t)base, (uintptr_t)s, 0};
-    return cached_launch(c, key, s, [&](cudaStream_t q) {
+    auto enqueue = [&](cudaStream_t q) {
       KS_TRY(launch_tensor(c, (const u64 *)ct1, (const u64 *)ct2, (u64 *)out, d2, q));
       return run_plan(c, pl, js, q);
-    });
+    };
+    return use_graphs(c) ? cached_launch(c, key, s, enqueue) : enqueue(s);
   });
 }
 
@@ -959,10 +970,11 @@ int ks_hrot(ks_context *c, const uint64_t *ct, uint32_t galois_elt, const uint64
     const std::array<uintptr_t, 10> key = {
         2, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)ct, (uintptr_t)galois_elt,
         (uintptr_t)rtk, (uintptr_t)out, (uintptr_t)base, (uintptr_t)s, 0};
-    return cached_launch(c, key, s, [&](cudaStream_t q) {
+    auto enqueue = [&](cudaStream_t q) {
       KS_TRY(launch_automorph(c, (const u64 *)ct, galois_elt, y0, y1, q));
       return run_plan(c, pl, js, q);
-    });
+    };
+    return use_graphs(c) ? cached_launch(c, key, s, enqueue) : enqueue(s);
   });
 }
 

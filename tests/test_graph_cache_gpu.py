@@ -1,6 +1,7 @@
-"""Repeated single operations replay a cached CUDA graph (captured on the second
-call with the same plan, buffers and stream): every replay must read the buffers'
-current contents and give the oracle's result."""
+"""Repeated single operations: at single-pass sizes (N <= 2^12) and through the
+host-buffer entry point they replay a cached CUDA graph (captured on the second call
+with the same plan, buffers and stream); larger sizes launch directly. Every call must
+read the buffers' current contents and give the oracle's result."""
 import numpy as np
 import pytest
 
@@ -12,11 +13,11 @@ from tests.gpu_util import dev, first_mismatch, host, oracle_case
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("cfg", [(3, 12, 8), (3, 14, 8)])
 @pytest.mark.parametrize("variant,chunks", [(ks.KS_DPOB, 0), (ks.KS_DSOC | ks.KS_RADIX4, 3),
                                             (ks.KS_DSOB | ks.KS_UNFUSED, 0)])
-def test_switch_replays_see_new_inputs(variant, chunks):
+def test_switch_replays_see_new_inputs(cfg, variant, chunks):
     import torch
-    cfg = (3, 14, 8)
     cases = [oracle_case(cfg, s) for s in (0, 1, 2)]
     prm = cases[0][0]
     ctx = ks.Context(prm)
@@ -38,9 +39,9 @@ def test_switch_replays_see_new_inputs(variant, chunks):
         ctx.close()
 
 
-def test_hmul_and_hrot_replays():
+@pytest.mark.parametrize("cfg", [(2, 12, 5), (2, 13, 5)])
+def test_hmul_and_hrot_replays(cfg):
     import torch
-    cfg = (2, 13, 5)
     prm = W.make_params(*cfg)
     _, s, a, e = W.gen_keys(prm, 1)
     rlk_o = O.keygen_poly(prm, O.negacyclic_mul_i64(s, s, prm.logn), s, a, e)
