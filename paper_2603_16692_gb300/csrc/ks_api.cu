@@ -280,6 +280,9 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
   return KS_OK;
 }
 
+// Internal streams of ks_switch_batch.
+constexpr int kBatchStreams = 16;
+
 // Shared state of ks_switch_batch: the batch workspace arena, fork streams,
 // dependency events and the captured graphs (keyed by the jobs' pointers).
 struct BatchState {
@@ -300,7 +303,7 @@ struct BatchState {
   const void *last_state_buf = nullptr;
   size_t last_state_off = 0;
   cudaStream_t stream(int g) {
-    const size_t k = (size_t)g % 16;
+    const size_t k = (size_t)g % kBatchStreams;
     while (streams.size() <= k) {
       cudaStream_t st = nullptr;
       cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -1082,11 +1085,34 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       fork = g_batch.event();
       cudaEventRecord(fork, s);
     }
+    // Largest groups first, each on the internal stream with the least work so far
+    // (longest-processing-time order): the big jobs of an uneven batch start at once,
+    // on different streams, and the small ones fill in behind them. Work ~ the
+    // NTT volume beta * QP * N log N of a job.
+    std::vector<int> order(G), sid(G, 0);
+    std::vector<double> cost(G);
+    for (int g = 0; g < G; ++g) {
+      order[g] = g;
+      const ks_context *c = ctxs[g];
+      cost[g] = (double)members[g].size() * c->beta * c->qp * c->N * c->logn;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    {
+      double load[kBatchStreams] = {};
+      for (int g : order) {
+        int k = 0;
+        for (int q = 1; q < kBatchStreams; ++q)
+          if (load[q] < load[k]) k = q;
+        sid[g] = k;
+        load[k] += cost[g];
+      }
+    }
     char *base = (char *)g_batch.arena;
-    for (int g = 0; g < G && rc == KS_OK; ++g) {
+    for (int oi = 0; oi < G && rc == KS_OK; ++oi) {
+      const int g = order[oi];
       cudaStream_t sg = s;
       if (G > 1) {
-        sg = g_batch.stream(g);
+        sg = g_batch.stream(sid[g]);
         cudaStreamWaitEvent(sg, fork, 0);
       }
       const Plan &pl = plans[g];
