@@ -45,6 +45,10 @@ SMS, IMAD_PER_SM_CLK, IMAD_PER_MODOP = 152, 64, 10
 # kernel). Missing = not captured for the current kernel code and plan (null).
 NCU_TRAFFIC = {("c2", "DPOB", "modup_row_keymult"): 35692032,
                ("c2", "DPOB-r4", "modup_row_keymult"): 35660544}
+# From the same captures: the busiest integer pipe (sm__pipe_fmaheavy_cycles_active, %
+# of peak) and the issue activity (smsp__issue_active, % of peak) of that launch.
+NCU_PIPES = {("c2", "DPOB", "modup_row_keymult"): {"fmaheavy_pct": 30.7, "issue_pct": 31.9},
+             ("c2", "DPOB-r4", "modup_row_keymult"): {"fmaheavy_pct": 34.9, "issue_pct": 40.5}}
 
 
 def parse():
@@ -529,14 +533,16 @@ def main():
     ops_l, bytes_l = dom["ops"] / dom["launches"], dom["bytes"] / dom["launches"]
     alu_ach = ops_l / (per_launch_ms / 1e3) / 1e9
     hbm_ach = bytes_l / (per_launch_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get((args.workload, ks.variant_name(variant, args.chunks), dom["name"]))
+    nkey = (args.workload, ks.variant_name(variant, args.chunks), dom["name"])
+    traffic = NCU_TRAFFIC.get(nkey)
     roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu_ach, "peak": alu_peak,
                 "unit": "Gmodop/s", "frac": alu_ach / alu_peak, "traffic": traffic,
                 "peak_source": f"derived: {SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_mhz:.0f}"
                                f" MHz / {IMAD_PER_MODOP} IMAD per modop",
                 "algo_bytes_per_launch": bytes_l, "hbm_achieved_gbs": hbm_ach,
                 "hbm_frac": hbm_ach / hbm,
-                "share": dom["ms"] / sum(s["ms"] for s in stats)}
+                "share": dom["ms"] / sum(s["ms"] for s in stats),
+                "ncu_pipes": NCU_PIPES.get(nkey)}
     algo = prm.algo_bytes()
     ks_gbs = algo * value / world / 1e9
     line = {
