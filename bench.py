@@ -274,8 +274,9 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
         sel, losses = S.train(data, tr)
         sel_info = S.evaluate(data, sel, te, tr)
         sel_info["train_final_loss"] = float(losses[-1])
-        sel_info["sweep"] = f"{len(data['points'])} points x {len(data['cands'])} plans, " \
-                            f"{len(tr)} train / {len(te)} held out"
+        sel_info["sweep"] = f"{len(data['points'])} points (+ {len(data.get('levels', []))} " \
+                            f"lower-level rows) x {len(data['cands'])} plans, {len(tr)} train / " \
+                            f"{len(te)} held-out points"
         picks = sel.choose([W.make_params(*cfg) for cfg in jobs])
         arg_sel = [(h, d, evk, out, S.CANDS[k][1], S.CANDS[k][2])
                    for (h, d, evk, out), k in zip(arg, picks)]
@@ -377,12 +378,19 @@ def eval_measure(args, ks, torch, dev, stream, l2):
         finally:
             ctx.close()
 
+    # the learned selector, trained on the committed sweep, picks a plan per level too
+    from paper_2603_16692_gb300 import selector as S
+    try:
+        data = S.load_json(os.path.join(S.DATA, "sweep_gb300.json"))
+        sel, _ = S.train(data, S.split(len(data["points"]))[0])
+    except (OSError, ValueError, KeyError):
+        sel = None
     prm = W.make_params(*W.C3)
     top = ks.Context(prm)
     try:
         keys = [rand_limbs(prm.mods, (prm.beta, 2), prm.N) for _ in range(2)]
         fixed = ks.KS_DPOB
-        rows, t_fix, t_dyn = [], 0.0, 0.0
+        rows, t_fix, t_dyn, t_mlp = [], 0.0, 0.0, 0.0
         for level in range(prm.L, -1, -1):
             view = top.at_level(level)
             try:
@@ -395,19 +403,35 @@ def eval_measure(args, ks, torch, dev, stream, l2):
                                                         None, stream), 10)
                 t_fix += tf
                 t_dyn += min(td, tf) if (v, c) == (fixed, 0) else td
-                rows.append({"level": level, "tuned": ks.variant_name(v, c),
-                             "ms_fixed": round(tf, 5), "ms_tuned": round(td, 5)})
+                row = {"level": level, "tuned": ks.variant_name(v, c),
+                       "ms_fixed": round(tf, 5), "ms_tuned": round(td, 5)}
+                if sel is not None:
+                    _, vm, cm = S.CANDS[sel.choose([S.level_shape(prm, level)])[0]]
+                    if (vm, cm) == (fixed, 0):
+                        tm = tf
+                    elif (vm, cm) == (v, c):
+                        tm = td
+                    else:
+                        tm = per_call_ms(lambda k: ks.ks_switch(view.h, ds[k % 2], keys[k % 2], res,
+                                                                vm, cm, None, stream), 10)
+                    t_mlp += tm
+                    row.update(mlp=ks.variant_name(vm, cm), ms_mlp=round(tm, 5))
+                rows.append(row)
             finally:
                 view.close()
-        picks = {}
+        picks, mpicks = {}, {}
         for r in rows:
             picks[r["tuned"]] = picks.get(r["tuned"], 0) + 1
+            if "mlp" in r:
+                mpicks[r["mlp"]] = mpicks.get(r["mlp"], 0) + 1
         out["levels"] = {
             "workload": f"one KeySwitch at each level {prm.L}..0 of {prm.name()} with the "
                         f"top-level key (level views)",
             "fixed_plan": ks.variant_name(fixed), "chain_ms_fixed": t_fix,
             "chain_ms_per_level_tuned": t_dyn, "speedup": t_fix / t_dyn, "picks": picks,
-            "per_level": rows}
+            "chain_ms_per_level_selector": t_mlp if sel is not None else None,
+            "selector_speedup": t_fix / t_mlp if sel is not None and t_mlp > 0 else None,
+            "selector_picks": mpicks, "per_level": rows}
     finally:
         top.close()
     return out

@@ -279,7 +279,7 @@ int ks_sync_status(ks_context *ctx, void *stream);
  * (W[i][j]: input i to output j). x [batch][6], y / t / mask [batch][4], all device
  * float arrays, batch <= KS_MLP_MAX_BATCH. Asynchronous on `stream`. */
 #define KS_MLP_PARAMS 4868
-#define KS_MLP_MAX_BATCH 256
+#define KS_MLP_MAX_BATCH 4096
 int ks_mlp_forward(const float *params_dev, const float *x_dev, int batch, float *y_dev,
                    void *stream);
 /* Gradient of the masked mean-squared loss sum(mask (y - t)^2) / sum(mask) with

@@ -7,10 +7,11 @@
 //   W1 [6][64] | b1 [64] | W2 [64][64] | b2 [64] | W3 [64][4] | b3 [4]
 // with W[i][j] the weight from input i to output j.
 //
-// Training runs in one CTA over the whole batch (B <= KS_MLP_MAX_BATCH): forward,
+// Training runs in one CTA over the whole batch (B <= KS_MLP_MAX_BATCH rows): forward,
 // masked mean-squared loss, backward and the Adam update, `steps` times in one
-// launch. Every gradient entry is summed by one thread in sample order, so results
-// are deterministic.
+// launch. The rows pass through shared memory in chunks of CH; every gradient entry
+// is summed by one thread, chunk after chunk in row order, so results are
+// deterministic and equal to the full-batch gradient.
 #include <cuda_runtime.h>
 
 #include "ks_internal.h"
@@ -21,6 +22,7 @@ constexpr int IN = 6, H = 64, OUT = 4;
 constexpr int OW1 = 0, OB1 = OW1 + IN * H, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H,
               OB3 = OW3 + H * OUT, NP = OB3 + OUT;
 constexpr int NT = 256;
+constexpr int CH = 256;  // rows per chunk held in shared memory
 
 static_assert(NP == KS_MLP_PARAMS, "parameter layout");
 
@@ -68,28 +70,22 @@ __device__ void forward(const Smem &m, int B) {
   __syncthreads();
 }
 
-// Loss 1/cnt sum mask (y - t)^2; leaves dL/dy in m.y and the gradients in g.
-__device__ float backward(const Smem &m, int B, const float *t, const float *mask, float *g,
-                          float *red) {
-  // count of targets and loss
-  float cnt = 0.f, loss = 0.f;
+// Masked squared error of a chunk, sum mask (y - t)^2 / total, and its gradient
+// added into g (written when first): leaves dL/dy in m.y. Returns the chunk's loss part.
+__device__ float backward(const Smem &m, int B, const float *t, const float *mask, float total,
+                          bool first, float *g, float *red) {
+  float loss = 0.f;
   for (int k = threadIdx.x; k < B * OUT; k += NT) {
-    const float w = mask[k], d = m.y[k] - t[k];
-    cnt += w;
-    loss += w * d * d;
+    const float d = m.y[k] - t[k];
+    loss += mask[k] * d * d;
   }
-  red[threadIdx.x] = cnt;
-  red[NT + threadIdx.x] = loss;
+  red[threadIdx.x] = loss;
   __syncthreads();
   for (int s = NT / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      red[threadIdx.x] += red[threadIdx.x + s];
-      red[NT + threadIdx.x] += red[NT + threadIdx.x + s];
-    }
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  const float total = red[0] > 0.f ? red[0] : 1.f;
-  const float L = red[NT] / total;
+  const float L = red[0] / total;
   __syncthreads();
   for (int k = threadIdx.x; k < B * OUT; k += NT) m.y[k] = mask[k] * 2.f * (m.y[k] - t[k]) / total;
   __syncthreads();
@@ -99,11 +95,11 @@ __device__ float backward(const Smem &m, int B, const float *t, const float *mas
     if (k < H * OUT) {
       const int i = k / OUT, o = k % OUT;
       for (int b = 0; b < B; ++b) a += m.h2[b * H + i] * m.y[b * OUT + o];
-      g[OW3 + k] = a;
+      g[OW3 + k] = first ? a : g[OW3 + k] + a;
     } else {
       const int o = k - H * OUT;
       for (int b = 0; b < B; ++b) a += m.y[b * OUT + o];
-      g[OB3 + o] = a;
+      g[OB3 + o] = first ? a : g[OB3 + o] + a;
     }
   }
   // dh2 = (dy W3^T) * [h2 > 0]
@@ -121,11 +117,11 @@ __device__ float backward(const Smem &m, int B, const float *t, const float *mas
     if (k < H * H) {
       const int i = k / H, j = k % H;
       for (int b = 0; b < B; ++b) a += m.h1[b * H + i] * m.dh[b * H + j];
-      g[OW2 + k] = a;
+      g[OW2 + k] = first ? a : g[OW2 + k] + a;
     } else {
       const int j = k - H * H;
       for (int b = 0; b < B; ++b) a += m.dh[b * H + j];
-      g[OB2 + j] = a;
+      g[OB2 + j] = first ? a : g[OB2 + j] + a;
     }
   }
   // dh1 = (dh2 W2^T) * [h1 > 0], written over h2 (no longer needed)
@@ -142,41 +138,75 @@ __device__ float backward(const Smem &m, int B, const float *t, const float *mas
     if (k < IN * H) {
       const int i = k / H, j = k % H;
       for (int b = 0; b < B; ++b) a += m.x[b * IN + i] * m.h2[b * H + j];
-      g[OW1 + k] = a;
+      g[OW1 + k] = first ? a : g[OW1 + k] + a;
     } else {
       const int j = k - IN * H;
       for (int b = 0; b < B; ++b) a += m.h2[b * H + j];
-      g[OB1 + j] = a;
+      g[OB1 + j] = first ? a : g[OB1 + j] + a;
     }
   }
   __syncthreads();
   return L;
 }
 
-__device__ void load(const Smem &m, const float *params, const float *x, int B) {
+// Sum of the mask over all rows (the loss denominator; 1 if the mask is empty).
+__device__ float mask_total(const float *mask, int B, float *red) {
+  float cnt = 0.f;
+  for (int k = threadIdx.x; k < B * OUT; k += NT) cnt += mask[k];
+  red[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const float total = red[0] > 0.f ? red[0] : 1.f;
+  __syncthreads();
+  return total;
+}
+
+// Loss and full-batch gradient (into g) over all B rows, chunk by chunk.
+__device__ float loss_grad(const Smem &m, const float *x, const float *t, const float *mask,
+                           int B, float total, float *g, float *red) {
+  float L = 0.f;
+  for (int r0 = 0; r0 < B; r0 += CH) {
+    const int nb = min(CH, B - r0);
+    for (int k = threadIdx.x; k < nb * IN; k += NT) m.x[k] = x[(size_t)r0 * IN + k];
+    __syncthreads();
+    forward(m, nb);
+    L += backward(m, nb, t + (size_t)r0 * OUT, mask + (size_t)r0 * OUT, total, r0 == 0, g, red);
+  }
+  return L;
+}
+
+__device__ void load_params(const Smem &m, const float *params) {
   for (int k = threadIdx.x; k < NP; k += NT) m.p[k] = params[k];
-  for (int k = threadIdx.x; k < B * IN; k += NT) m.x[k] = x[k];
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(NT) k_mlp_forward(const float *params, const float *x, int B,
                                                     float *y) {
   extern __shared__ float s[];
-  const Smem m = carve(s, B);
-  load(m, params, x, B);
-  forward(m, B);
-  for (int k = threadIdx.x; k < B * OUT; k += NT) y[k] = m.y[k];
+  const Smem m = carve(s, CH);
+  load_params(m, params);
+  for (int r0 = 0; r0 < B; r0 += CH) {
+    const int nb = min(CH, B - r0);
+    for (int k = threadIdx.x; k < nb * IN; k += NT) m.x[k] = x[(size_t)r0 * IN + k];
+    __syncthreads();
+    forward(m, nb);
+    for (int k = threadIdx.x; k < nb * OUT; k += NT) y[(size_t)r0 * OUT + k] = m.y[k];
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_mlp_grad(const float *params, const float *x,
                                                  const float *t, const float *mask, int B,
                                                  float *grad, float *loss) {
   extern __shared__ float s[];
-  __shared__ float red[2 * NT];
-  const Smem m = carve(s, B);
-  load(m, params, x, B);
-  forward(m, B);
-  const float L = backward(m, B, t, mask, grad, red);
+  __shared__ float red[NT];
+  const Smem m = carve(s, CH);
+  load_params(m, params);
+  const float total = mask_total(mask, B, red);
+  const float L = loss_grad(m, x, t, mask, B, total, grad, red);
   if (threadIdx.x == 0) *loss = L;
 }
 
@@ -187,14 +217,15 @@ __global__ void __launch_bounds__(NT) k_mlp_train(float *params, float *adam_m, 
                                                   const float *mask, int B, int steps, float lr,
                                                   int step0, float *loss) {
   extern __shared__ float s[];
-  __shared__ float red[2 * NT];
-  const Smem m = carve(s, B);
-  load(m, params, x, B);
+  __shared__ float red[NT];
+  const Smem m = carve(s, CH);
+  load_params(m, params);
+  const float total = mask_total(mask, B, red);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   for (int it = 0; it < steps; ++it) {
-    forward(m, B);
-    const float L = backward(m, B, t, mask, grad, red);
+    const float L = loss_grad(m, x, t, mask, B, total, grad, red);
     if (threadIdx.x == 0) loss[it] = L;
+    __syncthreads();  // the gradient is complete before the update reads it
     const int st = step0 + it + 1;
     const float c1 = 1.f - powf(b1, (float)st), c2 = 1.f - powf(b2, (float)st);
     for (int k = threadIdx.x; k < NP; k += NT) {
@@ -232,7 +263,7 @@ extern "C" {
 
 int ks_mlp_forward(const float *params, const float *x, int batch, float *y, void *stream) {
   if (!params || !x || !y || batch < 1 || batch > KS_MLP_MAX_BATCH) return KS_EINVAL;
-  const size_t smem = smem_floats(batch) * sizeof(float);
+  const size_t smem = smem_floats(CH) * sizeof(float);
   if (launch_check(smem)) return KS_EINVAL;
   cudaError_t e = opt_in(k_mlp_forward, smem);
   if (e) return rc_of(e);
@@ -245,7 +276,7 @@ int ks_mlp_grad(const float *params, const float *x, const float *t, const float
   if (!params || !x || !t || !mask || !grad || !loss || batch < 1 ||
       batch > KS_MLP_MAX_BATCH)
     return KS_EINVAL;
-  const size_t smem = smem_floats(batch) * sizeof(float);
+  const size_t smem = smem_floats(CH) * sizeof(float);
   if (launch_check(smem)) return KS_EINVAL;
   cudaError_t e = opt_in(k_mlp_grad, smem);
   if (e) return rc_of(e);
@@ -260,7 +291,7 @@ int ks_mlp_train(float *params, float *adam_m, float *adam_v, float *grad_scratc
       batch < 1 || batch > KS_MLP_MAX_BATCH || steps < 0 || step0 < 0)
     return KS_EINVAL;
   if (steps == 0) return KS_OK;
-  const size_t smem = smem_floats(batch) * sizeof(float);
+  const size_t smem = smem_floats(CH) * sizeof(float);
   if (launch_check(smem)) return KS_EINVAL;
   cudaError_t e = opt_in(k_mlp_train, smem);
   if (e) return rc_of(e);

@@ -314,7 +314,7 @@ def variant_name(v: int, chunks: int = 0) -> str:
     return s
 
 
-KS_MLP_PARAMS, KS_MLP_MAX_BATCH = 4868, 256
+KS_MLP_PARAMS, KS_MLP_MAX_BATCH = 4868, 4096
 
 
 def ks_mlp_forward(params, x, y, stream=None):

@@ -19,6 +19,7 @@ footprints are the ModUp working sets of Table III (beta*QP*N*8 and QP*N*8 bytes
 """
 from __future__ import annotations
 
+import dataclasses
 import json
 import math
 import os
@@ -40,7 +41,40 @@ def encode(log_ms: np.ndarray) -> np.ndarray:
 def decode(enc: np.ndarray) -> np.ndarray:
     """Candidate log-latencies from network outputs (inverse of encode)."""
     return np.concatenate([enc[:, :1], enc[:, 1:] + enc[:, :1]], axis=1)
+
+
 DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+@dataclasses.dataclass(frozen=True)
+class LevelShape:
+    """The shape of a KeySwitch at level l of a context (a level view): l+1 Q-limbs,
+    the context's alpha special primes, beta_l = ceil((l+1)/alpha) digits. It has the
+    attributes `features` reads, with the number of digits in the role of dnum, so the
+    selector can pick a plan per level (Sec. V: switch the dataflow as L falls)."""
+    logn: int
+    L: int
+    alpha: int
+
+    @property
+    def N(self):
+        return 1 << self.logn
+
+    @property
+    def beta(self):
+        return -(-(self.L + 1) // self.alpha)
+
+    @property
+    def dnum(self):
+        return self.beta
+
+    @property
+    def QP(self):
+        return self.L + 1 + self.alpha
+
+
+def level_shape(prm, level: int) -> LevelShape:
+    return LevelShape(prm.logn, level, prm.alpha)
 
 
 def footprints(prm) -> dict:
@@ -85,12 +119,21 @@ ALL_PLANS = [(f"{n}{'-r4' if r4 else ''}", v | (ks.KS_RADIX4 if r4 else 0), c)
                              ("DPOC-c4", ks.KS_DPOC, 4)] for r4 in (0, 1)]
 
 
+def sweep_levels(L: int) -> list:
+    """The lower levels measured beside a top-level point: L/2 and L/5 (rounded down,
+    distinct, below L)."""
+    return sorted({lv for lv in (L // 2, L // 5) if 0 <= lv < L})
+
+
 def sweep(points, reps: int = 5, seed: int = 0, log=print, cands=None) -> dict:
+    """Median time of each plan on each point (a KeySwitch with random inputs), and on
+    the point's lower levels (level views with the point's key: `levels` rows)."""
     import torch
     dev = torch.device("cuda")
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
+    plans = cands or CANDS
 
     def rand_limbs(mods, lead, n):
         t = torch.empty((*lead, len(mods), n), dtype=torch.int64, device=dev)
@@ -101,35 +144,60 @@ def sweep(points, reps: int = 5, seed: int = 0, log=print, cands=None) -> dict:
 
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms = []
-    for k, cfg in enumerate(points):
-        prm = W.make_params(*cfg)
-        ctx = ks.Context(prm)
-        d = rand_limbs(prm.q, (), prm.N)
-        evk = rand_limbs(prm.mods, (prm.beta, 2), prm.N)
-        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device=dev)
+
+    def measure(h, d, evk, out):
         row = []
-        for name, v, c in (cands or CANDS):
+        for name, v, c in plans:
             for _ in range(2):
-                ks.ks_switch(ctx.h, d, evk, out, v, c, None, stream)
+                ks.ks_switch(h, d, evk, out, v, c, None, stream)
             ts = []
             for _ in range(reps):
                 e0.record(stream)
-                ks.ks_switch(ctx.h, d, evk, out, v, c, None, stream)
+                ks.ks_switch(h, d, evk, out, v, c, None, stream)
                 e1.record(stream)
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
             row.append(float(np.median(ts)))
+        return row
+
+    ms, levels, level_ms = [], [], []
+    for k, cfg in enumerate(points):
+        prm = W.make_params(*cfg)
+        ctx = ks.Context(prm)
+        evk = rand_limbs(prm.mods, (prm.beta, 2), prm.N)
+        d = rand_limbs(prm.q, (), prm.N)
+        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device=dev)
+        row = measure(ctx.h, d, evk, out)
         ms.append(row)
+        for lv in sweep_levels(prm.L):
+            view = ctx.at_level(lv)
+            dl = rand_limbs(prm.q[:lv + 1], (), prm.N)
+            ol = torch.empty((2, lv + 1, prm.N), dtype=torch.uint64, device=dev)
+            levels.append([k, lv])
+            level_ms.append(measure(view.h, dl, evk, ol))
+            view.close()
         ctx.close()
         del d, evk, out
         if log and (k % 20 == 0 or k == len(points) - 1):
             log(f"sweep {k + 1}/{len(points)} {cfg}: " +
-                " ".join(f"{n}={t:.3f}ms" for (n, _, _), t in zip(cands or CANDS, row)))
+                " ".join(f"{n}={t:.3f}ms" for (n, _, _), t in zip(plans, row)))
     torch.cuda.empty_cache()
     return {"device": torch.cuda.get_device_name(dev), "l2": int(l2), "reps": reps,
-            "cands": [n for n, _, _ in (cands or CANDS)], "points": [list(p) for p in points],
-            "ms": ms}
+            "cands": [n for n, _, _ in plans], "points": [list(p) for p in points],
+            "ms": ms, "levels": levels, "level_ms": level_ms}
+
+
+def shapes_and_times(data: dict, idx):
+    """(shapes, times[rows][plans]) of the top-level points idx and of their level rows
+    (a sweep without level rows gives the points alone)."""
+    pts = [W.make_params(*data["points"][i]) for i in idx]
+    ms = [data["ms"][i] for i in idx]
+    keep = set(idx)
+    for (k, lv), row in zip(data.get("levels", []), data.get("level_ms", [])):
+        if k in keep:
+            pts.append(level_shape(W.make_params(*data["points"][k]), lv))
+            ms.append(row)
+    return pts, np.array(ms, dtype=np.float64)
 
 
 def split(n: int, n_test: int = 40, seed: int = 0):
@@ -195,11 +263,11 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
     """Fit the MLP on the sweep rows `idx` with the library's CUDA training kernel.
     Returns (Selector, per-step losses)."""
     import torch
-    prms = [W.make_params(*p) for p in data["points"]]
+    shapes, times = shapes_and_times(data, idx)
     l2 = data["l2"]
-    X = np.array([features(prms[i], l2) for i in idx], dtype=np.float64)
+    X = np.array([features(p, l2) for p in shapes], dtype=np.float64)
     cols = columns(data)
-    T = encode(np.log(np.array([data["ms"][i] for i in idx], dtype=np.float64)[:, cols]))
+    T = encode(np.log(times[:, cols]))
     x_mean, x_std = X.mean(0), X.std(0) + 1e-9
     t_mean, t_std = T.mean(0), T.std(0) + 1e-9
     sel = Selector(init_params(seed), x_mean, x_std, t_mean, t_std, l2)
@@ -219,22 +287,32 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
 
 
 def evaluate(data: dict, sel: Selector, test_idx, train_idx) -> dict:
-    """Regret t(chosen)/t(best) - 1 on test_idx, the best being the exhaustive minimum
-    over every measured plan, for the MLP, the best single fixed candidate (chosen on
-    train_idx) and the paper's footprint rule."""
-    prms = [W.make_params(*p) for p in data["points"]]
-    allms = np.array(data["ms"], dtype=np.float64)
-    best = allms.min(1)
-    ms = allms[:, columns(data)]
-    fixed = int(np.argmin(ms[train_idx].sum(0)))
-    choice_mlp = sel.choose([prms[i] for i in test_idx])
-    out = {}
-    for name, ch in (("mlp", choice_mlp), ("fixed_" + CANDS[fixed][0], [fixed] * len(test_idx)),
-                     ("footprint_rule", [footprint_rule(prms[i], data["l2"]) for i in test_idx])):
-        r = np.array([ms[i, c] / best[i] - 1 for i, c in zip(test_idx, ch)])
-        out[name] = {"mean_regret": float(r.mean()), "max_regret": float(r.max()),
-                     "total_ms": float(sum(ms[i, c] for i, c in zip(test_idx, ch)))}
-    out["exhaustive_total_ms"] = float(best[test_idx].sum())
+    """Regret t(chosen)/t(best) - 1 on the held-out points test_idx, the best being the
+    exhaustive minimum over every measured plan, for the MLP, the best single fixed
+    candidate (chosen on the training rows) and the paper's footprint rule; the same
+    over the held-out points' lower levels under "levels" (if the sweep has them)."""
+    _, tr_times = shapes_and_times(data, train_idx)
+    cols = columns(data)
+    fixed = int(np.argmin(tr_times[:, cols].sum(0)))
+
+    def score(shapes, times):
+        best = times.min(1)
+        ms = times[:, cols]
+        choice_mlp = sel.choose(shapes)
+        res = {}
+        for name, ch in (("mlp", choice_mlp), ("fixed_" + CANDS[fixed][0], [fixed] * len(shapes)),
+                         ("footprint_rule", [footprint_rule(p, data["l2"]) for p in shapes])):
+            r = np.array([ms[i, c] / best[i] - 1 for i, c in enumerate(ch)])
+            res[name] = {"mean_regret": float(r.mean()), "max_regret": float(r.max()),
+                         "total_ms": float(sum(ms[i, c] for i, c in enumerate(ch)))}
+        res["exhaustive_total_ms"] = float(best.sum())
+        return res
+
+    top = [W.make_params(*data["points"][i]) for i in test_idx]
+    out = score(top, np.array([data["ms"][i] for i in test_idx], dtype=np.float64))
+    shapes, times = shapes_and_times(data, test_idx)
+    if len(shapes) > len(top):
+        out["levels"] = dict(score(shapes[len(top):], times[len(top):]), rows=len(shapes) - len(top))
     return out
 
 

@@ -49,3 +49,16 @@ def test_selector_target_encoding_round_trips():
     assert np.allclose(E[:, 0], L[:, 0])
     assert np.allclose(E[:, 1:], L[:, 1:] - L[:, :1])
     assert np.allclose(S.decode(E), L)
+
+
+def test_level_shape_matches_the_level_view():
+    """A KeySwitch at level l keeps alpha and has ceil((l+1)/alpha) digits over
+    l+1+alpha limbs; at the top level it is the context's own shape."""
+    from paper_2603_16692_gb300 import selector as S
+    from paper_2603_16692_gb300 import workload as W
+    prm = W.make_params(4, 16, 35)
+    top = S.level_shape(prm, prm.L)
+    assert (top.beta, top.QP, top.N) == (prm.beta, prm.QP, prm.N)
+    assert S.features(top, 1 << 27)[3:] == S.features(prm, 1 << 27)[3:]
+    low = S.level_shape(prm, 10)
+    assert (low.beta, low.QP, low.dnum) == (2, 20, 2)

@@ -28,7 +28,7 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("b", [1, 7, 160, 256])
+@pytest.mark.parametrize("b", [1, 7, 160, 256, 257, 700])
 def test_mlp_forward_and_gradient_match_oracle(b):
     import torch
     p, x, t, mask = _case(b, b)
@@ -47,10 +47,12 @@ def test_mlp_forward_and_gradient_match_oracle(b):
     assert not bad.any(), f"{bad.sum()} gradient entries off, first {np.argwhere(bad)[:3].ravel()}"
 
 
-def test_mlp_training_step_is_adam_on_oracle_gradient():
-    """One ks_mlp_train step equals Adam applied to the oracle's gradient."""
+@pytest.mark.parametrize("b", [64, 600])
+def test_mlp_training_step_is_adam_on_oracle_gradient(b):
+    """One ks_mlp_train step equals Adam applied to the oracle's gradient (600 rows: the
+    rows pass through shared memory in three chunks)."""
     import torch
-    p, x, t, mask = _case(3, 64)
+    p, x, t, mask = _case(3, b)
     dp, m, v, g = _dev(p.copy()), _dev(np.zeros(M.NP, np.float32)), \
         _dev(np.zeros(M.NP, np.float32)), _dev(np.zeros(M.NP, np.float32))
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -97,6 +99,12 @@ def test_selector_gain_on_held_out_points():
     assert mlp < ev["footprint_rule"]["mean_regret"], ev
     assert ev["mlp"]["total_ms"] < ev[fixed]["total_ms"], ev
     assert mlp <= 0.05, ev
+    # the held-out points' lower levels (level views): the network picks per level
+    if "levels" in ev:
+        lv = ev["levels"]
+        assert lv["mlp"]["mean_regret"] < lv[fixed]["mean_regret"], lv
+        assert lv["mlp"]["total_ms"] < lv[fixed]["total_ms"], lv
+        assert lv["mlp"]["mean_regret"] <= 0.05, lv
 
 
 def test_binding_rejects_strided_tensors():
