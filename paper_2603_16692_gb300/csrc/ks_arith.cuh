@@ -109,7 +109,4 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// [0, 4m) -> [0, m)
-__device__ __forceinline__ u64 canon4(u64 x, u64 m) { return csub(csub(x, 2 * m), m); }
-
 __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 m) { return csub(a + b, m); }

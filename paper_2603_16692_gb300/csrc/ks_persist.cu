@@ -404,8 +404,6 @@ void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
     }
 }
 
-size_t persist_job_bytes() { return sizeof(PJob); }
-size_t persist_work_bytes() { return sizeof(PWork); }
 size_t persist_state_bytes(int ncnt) { return sizeof(PState) + sizeof(int) * (size_t)ncnt; }
 
 // Device image of a built batch: jobs | work | state (16-byte aligned pieces).
