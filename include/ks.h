@@ -140,17 +140,21 @@ int ks_keygen_galois(ks_context *ctx, const int8_t *s_dev, uint32_t galois_elt,
 /* Device bytes of scratch that ks_switch needs for (variant, chunks). */
 int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *bytes);
 
-/* One KeySwitch (Sec. II-A, Fig. 1) at level L.
+/* One KeySwitch (Sec. II-A, Fig. 1) at level L (at the view's level for a level view,
+ * whose evk is the top level's key).
  *   d_dev   [L+1][N]            input, NTT form
  *   evk_dev [beta][2][QP][N]    keys from ks_keygen (or any canonical keys)
  *   out_dev [2][L+1][N]         output pair, NTT form; must not alias the inputs
- *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED), or KS_AUTO (DPOB, fused)
+ *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16), or KS_AUTO (the
+ *           plan ks_tune chose for this context, else DPOB fused radix 8)
  *   chunks  2..10 for the OC variants (0 = 2); ignored for OB
  *   workspace_dev / workspace_bytes: caller scratch of at least
  *           ks_workspace_size() bytes, or NULL/0 to use the context's internal
  *           workspace (allocated on first use and grown as needed; calls that use it
  *           must then be ordered, e.g. issued on one stream).
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`. The kernels are chained by programmatic dependent launch
+ * (consecutive calls on a stream overlap their boundaries); for N <= 2^12 repeated
+ * calls with the same plan, buffers and stream replay a cached CUDA graph. */
 int ks_switch(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev,
               uint64_t *out_dev, int variant, int chunks, void *workspace_dev,
               size_t workspace_bytes, void *stream);
