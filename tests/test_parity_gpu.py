@@ -127,3 +127,25 @@ def test_bad_calls_return_errors():
         assert ks.ks_sync_status(ctx.h) == ks.KS_OK
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("cfg", [(2, 13, 127), (15, 13, 127)])
+def test_maximum_limb_count(cfg):
+    """L+1 = 128 ciphertext primes (the library's limit), with 2 and with 15 digits."""
+    vs = [ks.KS_DPOB, ks.KS_DSOB, ks.KS_DPOC, ks.KS_DPOB | ks.KS_UNFUSED]
+    check(cfg, 0, vs, chunk_list=(3,))
+
+
+def test_key_multiply_sum_bound_is_enforced():
+    """beta * max modulus must stay below 2^64 (one exact 128-bit sum per key multiply):
+    19 digits of ~2^60 special primes would overflow and are refused."""
+    prm = W.make_params(19, 13, 127)
+    assert prm.beta * max(prm.mods) >= 1 << 64
+    with pytest.raises(ks.KSError):
+        ks.Context(prm)
+
+
+def test_empty_batch_is_a_no_op():
+    ks.ks_switch_batch([], 0)
+    ks.ks_switch_batch([], ks.KS_BATCH_GRAPH)
+    ks.ks_switch_batch([], ks.KS_BATCH_PERSISTENT)
