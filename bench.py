@@ -51,6 +51,21 @@ NCU_PIPES = {("c2", "DPOB", "modup_row_keymult"): {"fmaheavy_pct": 30.7, "issue_
              ("c2", "DPOB-r4", "modup_row_keymult"): {"fmaheavy_pct": 34.9, "issue_pct": 40.5}}
 
 
+def measured_alu(ks, stream, dom, per_launch_ms):
+    """The dominant kernel against the measured ceiling of its own arithmetic: the
+    library's calibration kernels give butterflies/s and 128-bit multiply-accumulate
+    terms/s on this GPU with every SM busy and no memory traffic; the kernel's
+    operations at those rates take t_ceil, and frac = t_ceil / its event time."""
+    bf = max(ks.ks_calibrate(ks.KS_CAL_BUTTERFLY, 16384, stream) for _ in range(3))
+    mac = max(ks.ks_calibrate(ks.KS_CAL_MAC, 4096, stream) for _ in range(3))
+    n = dom["launches"]
+    macs, shoup = dom["macs"] / n, (dom["ops"] - dom["macs"]) / n
+    t_ceil_ms = (macs / mac + shoup / bf) * 1e3
+    return {"butterfly_per_s": bf, "mac_per_s": mac, "macs_per_launch": macs,
+            "shoup_per_launch": shoup, "t_ceil_ms": t_ceil_ms,
+            "frac": t_ceil_ms / per_launch_ms}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,9 +504,11 @@ def main():
     ws = torch.empty(ks.ks_workspace_size(ctx.h, variant, args.chunks) // 8 + 1,
                      dtype=torch.uint64, device=dev)
 
+    calls = [ks.prepare_switch(ctx.h, d, evk, out, variant, args.chunks, ws, stream)
+             for d, evk, out in sets]
+
     def step(k):
-        d, evk, out = sets[k % ring]
-        ks.ks_switch(ctx.h, d, evk, out, variant, args.chunks, ws, stream)
+        calls[k % ring]()
 
     props = torch.cuda.get_device_properties(dev)
     gpu_id = str(getattr(props, "uuid", local))
@@ -514,6 +531,18 @@ def main():
     sampler.mark(t_wall0, t_wall1)
     el_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     value = job_rate(world, args.steps, el_ms)
+
+    # host cost of one step (Python call + launches), enqueued ahead of an idle GPU: a
+    # short burst well inside the launch queue, so the host never waits for the device
+    host_us = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(32):
+            step(k)
+        host_us.append((time.perf_counter() - t0) * 1e6 / 32)
+    torch.cuda.synchronize()
+    host_us = min(host_us)
 
     # per-kernel event timing over a second pass of the same steps (kept out of `value`)
     kprof = min(args.steps, 500)
@@ -567,6 +596,7 @@ def main():
                 "hbm_frac": hbm_ach / hbm,
                 "share": dom["ms"] / sum(s["ms"] for s in stats),
                 "ncu_pipes": NCU_PIPES.get(nkey)}
+    roofline["measured_alu"] = measured_alu(ks, stream, dom, per_launch_ms)
     algo = prm.algo_bytes()
     ks_gbs = algo * value / world / 1e9
     line = {
@@ -583,6 +613,7 @@ def main():
         "kernels": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in s.items()}
                     for s in sorted(stats, key=lambda s: -s["ms"])],
         "gpu_launches": int(round(launches_per_step * args.steps)),
+        "host_us_per_step": host_us,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": (prm.L + 1) * prm.N * 8,
                 "d2h_bytes_per_step": 2 * (prm.L + 1) * prm.N * 8},

@@ -311,10 +311,27 @@ typedef struct {
   double ms;     /* summed event time */
   double bytes;  /* summed algorithmic bytes */
   double ops;    /* summed modular operations */
+  double macs;   /* of which exact 128-bit multiply-accumulate terms (basis conversion,
+                    key multiply); the rest are Shoup products (butterflies, scalings) */
 } ks_kernel_stat;
 
 int ks_profile_begin(void);
 int ks_profile_end(ks_kernel_stat *stats, int max_stats, int *count);
+
+/* Throughput ceiling of the library's modular arithmetic on the current device,
+ * measured: one launch of `iters` iterations on every SM at full occupancy, with no
+ * memory traffic, timed with CUDA events on `stream` (after one shorter warm-up
+ * launch; synchronizes `stream`). It is the measured denominator for kernels bound by
+ * the integer pipes, beside the one derived from unit counts and clocks.
+ *   KS_CAL_BUTTERFLY: forward lazy butterflies (one approximate-quotient Shoup
+ *                     product, an add and a subtract) per second;
+ *   KS_CAL_MAC:       exact 64x64->128-bit multiply-accumulate terms per second, one
+ *                     Montgomery reduction per 8 terms.
+ * *ops_per_s receives the rate. Returns KS_EINVAL (unknown kind, iters < 1, null
+ * pointer), KS_ENOMEM or KS_ECUDA. */
+#define KS_CAL_BUTTERFLY 1
+#define KS_CAL_MAC 2
+int ks_calibrate(int kind, int iters, double *ops_per_s, void *stream);
 
 const char *ks_strerror(int code);
 

@@ -113,7 +113,7 @@ int cuda_rc(cudaError_t e) {
 struct ProfRec {
   const char *name;
   cudaEvent_t a, b;
-  double bytes, ops;
+  double bytes, ops, macs;
 };
 
 struct Profiler {
@@ -136,13 +136,14 @@ thread_local Profiler g_prof;
 
 // Run one launcher; when profiling, bracket it with events on its stream.
 template <class F>
-cudaError_t timed(const char *name, double bytes, double ops, cudaStream_t s, F f) {
+cudaError_t timed(const char *name, double bytes, double ops, double macs, cudaStream_t s,
+                  F f) {
   if (!g_prof.on) return f();
   cudaEvent_t a = g_prof.get(), b = g_prof.get();
   cudaEventRecord(a, s);
   cudaError_t e = f();
   cudaEventRecord(b, s);
-  g_prof.recs.push_back({name, a, b, bytes, ops});
+  g_prof.recs.push_back({name, a, b, bytes, ops, macs});
   return e;
 }
 
@@ -169,10 +170,10 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
   // Input iNTT, fused with the per-limb factor N^-1 * Qhat_{j,i}^-1 of the ModUp BConv.
   {
     const double nl = c->nq;
-    KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), s,
+    KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), 0, s,
                  [&] { return L.intt_row(c, js, wo, 0, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(d)", 2 * nl * W, nl * (BF_A + NJ), s,
+      KS_TRY(timed("intt_col(d)", 2 * nl * W, nl * (BF_A + NJ), 0, s,
                    [&] { return L.intt_col(c, js, wo, 0, s); }));
   }
 
@@ -209,15 +210,15 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
       const double own = nd * nt - nconv;
       if (!pl.unfused) {
         if (!single)
-          KS_TRY(timed("modup_col", nconv * W + src_b, conv_ops + nconv * BF_A, s,
+          KS_TRY(timed("modup_col", nconv * W + src_b, conv_ops + nconv * BF_A, conv_ops, s,
                        [&] { return L.modup_col(c, js, wo, up, s); }));
       } else {
-        KS_TRY(timed("bconv_up", nconv * W + src_b, conv_ops, s,
+        KS_TRY(timed("bconv_up", nconv * W + src_b, conv_ops, conv_ops, s,
                      [&] { return launch_bconv_up(c, js, wo, up, nconv, s); }));
         if (!single)
-          KS_TRY(timed("ntt_col", 2 * nconv * W, nconv * BF_A, s,
+          KS_TRY(timed("ntt_col", 2 * nconv * W, nconv * BF_A, 0, s,
                        [&] { return L.ntt_col(c, js, wo, up, BUF_TMP, s); }));
-        KS_TRY(timed("ntt_row", 2 * nconv * W, nconv * BF_B, s,
+        KS_TRY(timed("ntt_row", 2 * nconv * W, nconv * BF_B, 0, s,
                      [&] { return L.ntt_row(c, js, wo, up, BUF_TMP, s); }));
       }
       // key multiply: evk 2 words per (digit, target); ext from tmp (or d on own limbs);
@@ -227,9 +228,11 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
       if (!pl.unfused) {
         const double b = km_bytes + (single ? src_b - nconv * W : 0);
         const double o = km_ops + nconv * BF_B + (single ? conv_ops : 0);
-        KS_TRY(timed("modup_row_keymult", b, o, s, [&] { return L.modup_row(c, js, wo, tg, s); }));
+        const double m = km_ops + (single ? conv_ops : 0);
+        KS_TRY(timed("modup_row_keymult", b, o, m, s,
+                     [&] { return L.modup_row(c, js, wo, tg, s); }));
       } else {
-        KS_TRY(timed("keymult", km_bytes, km_ops, s,
+        KS_TRY(timed("keymult", km_bytes, km_ops, km_ops, s,
                      [&] { return launch_keymult(c, js, wo, tg, s); }));
       }
     }
@@ -238,10 +241,10 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
   // iNTT of the P-limbs of both accumulators, fused with N^-1 * Phat_k^-1.
   {
     const double nl = 2.0 * c->np;
-    KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), s,
+    KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), 0, s,
                  [&] { return L.intt_row(c, js, wo, 1, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(accP)", 2 * nl * W, nl * (BF_A + NJ), s,
+      KS_TRY(timed("intt_col(accP)", 2 * nl * W, nl * (BF_A + NJ), 0, s,
                    [&] { return L.intt_col(c, js, wo, 1, s); }));
   }
 
@@ -260,20 +263,21 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
     const double n = 2.0 * (i1 - i0), vp_b = 2.0 * c->np * W, conv = n * NJ * (c->np + 1.0);
     if (!pl.unfused) {
       if (!single)
-        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, s,
+        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s,
                      [&] { return L.moddown_col(c, js, wo, dn, s); }));
       const double b = 3 * n * W + (single ? vp_b - n * W : 0);
       const double o = n * (BF_B + NJ) + (single ? conv : 0);
-      KS_TRY(timed("moddown_row", b, o, s, [&] { return L.moddown_row(c, js, wo, d1, s); }));
+      KS_TRY(timed("moddown_row", b, o, single ? conv : 0, s,
+                   [&] { return L.moddown_row(c, js, wo, d1, s); }));
     } else {
-      KS_TRY(timed("bconv_down", n * W + vp_b, conv, s,
+      KS_TRY(timed("bconv_down", n * W + vp_b, conv, conv, s,
                    [&] { return launch_bconv_down(c, js, wo, dn, (int)n, s); }));
       if (!single)
-        KS_TRY(timed("ntt_col", 2 * n * W, n * BF_A, s,
+        KS_TRY(timed("ntt_col", 2 * n * W, n * BF_A, 0, s,
                      [&] { return L.ntt_col(c, js, wo, dn, BUF_TMP2, s); }));
-      KS_TRY(timed("ntt_row", 2 * n * W, n * BF_B, s,
+      KS_TRY(timed("ntt_row", 2 * n * W, n * BF_B, 0, s,
                    [&] { return L.ntt_row(c, js, wo, dn, BUF_TMP2, s); }));
-      KS_TRY(timed("moddown_scale", 3 * n * W, n * NJ, s,
+      KS_TRY(timed("moddown_scale", 3 * n * W, n * NJ, 0, s,
                    [&] { return launch_moddown_scale(c, js, wo, dn, (int)n, s); }));
     }
   }
@@ -1267,6 +1271,7 @@ int ks_profile_end(ks_kernel_stat *stats, int max_stats, int *count) {
     hit->ms += ms;
     hit->bytes += r.bytes;
     hit->ops += r.ops;
+    hit->macs += r.macs;
     g_prof.pool.push_back(r.a);
     g_prof.pool.push_back(r.b);
   }

@@ -50,7 +50,7 @@ class ks_info(ctypes.Structure):
 
 class ks_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("ops", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("ops", ctypes.c_double), ("macs", ctypes.c_double)]
 
 
 class ks_job(ctypes.Structure):
@@ -69,7 +69,7 @@ SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_key
            "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune",
            "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status",
            "ks_context_at_level", "ks_keygen_relin", "ks_keygen_galois",
-           "ks_eval_workspace_size", "ks_hmul", "ks_hrot")
+           "ks_eval_workspace_size", "ks_hmul", "ks_hrot", "ks_calibrate")
 
 
 def lib_path() -> str:
@@ -108,6 +108,7 @@ def load(build: bool = True):
         l.ks_eval_workspace_size.argtypes = [vp, i, i, i, ctypes.POINTER(sz)]
         l.ks_hmul.argtypes = [vp, vp, vp, vp, vp, i, i, vp, sz, vp]
         l.ks_hrot.argtypes = [vp, vp, ctypes.c_uint32, vp, vp, i, i, vp, sz, vp]
+        l.ks_calibrate.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
         l.ks_noalloc_scratch_bytes.argtypes = []
@@ -239,6 +240,25 @@ def ks_switch(ctx: int, d, evk, out, variant: int = KS_AUTO, chunks: int = 0, wo
                             _ptr(workspace), ws_bytes, _stream(stream)), "ks_switch")
 
 
+def prepare_switch(ctx: int, d, evk, out, variant: int = KS_AUTO, chunks: int = 0,
+                   workspace=None, stream=None):
+    """A zero-argument callable that runs ks_switch on these buffers. Pointers, sizes and
+    the stream are marshalled once, so a loop over the same buffers pays one ctypes call
+    per KeySwitch; the buffers must stay alive while the callable is used."""
+    f = load().ks_switch
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    vp = ctypes.c_void_p
+    args = (vp(ctx), vp(_ptr(d)), vp(_ptr(evk)), vp(_ptr(out)), ctypes.c_int(variant),
+            ctypes.c_int(chunks), vp(_ptr(workspace)), ctypes.c_size_t(ws_bytes),
+            vp(_stream(stream)))
+
+    def call():
+        rc = f(*args)
+        if rc != KS_OK:
+            raise KSError(rc, "ks_switch")
+    return call
+
+
 def ks_noalloc_scratch_bytes() -> int:
     return load().ks_noalloc_scratch_bytes()
 
@@ -283,12 +303,24 @@ def ks_profile_begin():
 
 
 def ks_profile_end() -> list:
-    """[{name, launches, ms, bytes, ops}] aggregated over the profiled launches."""
+    """[{name, launches, ms, bytes, ops, macs}] aggregated over the profiled launches."""
     arr = (ks_kernel_stat * 64)()
     n = ctypes.c_int()
     _check(load().ks_profile_end(arr, 64, ctypes.byref(n)), "ks_profile_end")
     return [{"name": arr[k].name.decode(), "launches": arr[k].launches, "ms": arr[k].ms,
-             "bytes": arr[k].bytes, "ops": arr[k].ops} for k in range(min(n.value, 64))]
+             "bytes": arr[k].bytes, "ops": arr[k].ops, "macs": arr[k].macs}
+            for k in range(min(n.value, 64))]
+
+
+KS_CAL_BUTTERFLY, KS_CAL_MAC = 1, 2
+
+
+def ks_calibrate(kind: int, iters: int = 4096, stream=None) -> float:
+    """Measured ceiling of the library's modular arithmetic on this device: forward
+    butterflies/s (KS_CAL_BUTTERFLY) or 128-bit multiply-accumulate terms/s (KS_CAL_MAC)."""
+    r = ctypes.c_double()
+    _check(load().ks_calibrate(kind, iters, ctypes.byref(r), _stream(stream)), "ks_calibrate")
+    return r.value
 
 
 def ks_tune(ctx: int, d, evk, out, batch: int = 1, stream=None):

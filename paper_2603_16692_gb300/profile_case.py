@@ -7,6 +7,10 @@ kernel names all start with ``k_``, so ``ncu -k regex:^k_`` captures exactly the
 operation's launches.
 
     python -m paper_2603_16692_gb300.profile_case --cfg 4,16,30 --variant DPOB
+
+With ``--stats`` (not for profilers: it adds timing and calibration launches) it also
+prints, per kernel, the event time of a launch and its fraction of the measured
+ceiling of its own arithmetic (``ks_calibrate``), and the same for the whole operation.
 """
 from __future__ import annotations
 
@@ -26,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--op", default="switch", choices=["switch", "hmul", "hrot"])
     ap.add_argument("--level", type=int, default=-1, help="run on a level view (default: top)")
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--stats", action="store_true",
+                    help="print per-kernel time and fraction of the measured ALU ceiling")
     args = ap.parse_args(argv)
 
     import torch
@@ -44,18 +50,52 @@ def main(argv=None):
     ct2 = torch.from_numpy(W.uniform_limbs(g, prm.q[:nq] * 2, prm.N).reshape(2, nq, prm.N)).to(dev)
     out = torch.empty_like(ct)
     torch.cuda.synchronize()
-    for _ in range(args.reps):
+
+    def run():
         if args.op == "switch":
             ctx.switch(ct[1], evk, out, v, args.chunks)
         elif args.op == "hmul":
             ctx.hmul(ct, ct2, evk, out, v, args.chunks)
         else:
             ctx.hrot(ct, ks.galois_elt(1, prm.N), evk, out, v, args.chunks)
+
+    for _ in range(args.reps):
+        run()
     torch.cuda.synchronize()
     print(f"{args.op} {prm.name()} level {nq - 1} {ks.variant_name(v, args.chunks)}: ok")
+    if args.stats:
+        stats(run, max(args.reps, 20))
     if ctx is not top:
         ctx.close()
     top.close()
+
+
+def stats(run, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    op_ms = e0.elapsed_time(e1) / reps
+    ks.ks_profile_begin()
+    for _ in range(reps):
+        run()
+    rows = ks.ks_profile_end()
+    bf = max(ks.ks_calibrate(ks.KS_CAL_BUTTERFLY, 16384) for _ in range(3))
+    mac = max(ks.ks_calibrate(ks.KS_CAL_MAC, 4096) for _ in range(3))
+    print(f"measured ceiling: {bf / 1e12:.3f} T butterflies/s, {mac / 1e12:.3f} T MAC terms/s")
+    print(f"{'kernel':22s} {'us/launch':>10s} {'ceil us':>8s} {'frac':>6s} {'share':>6s}")
+    total = sum(r["ms"] for r in rows)
+    ceil_op = 0.0
+    for r in sorted(rows, key=lambda r: -r["ms"]):
+        ceil = (r["macs"] / mac + (r["ops"] - r["macs"]) / bf) * 1e6 / r["launches"]
+        us = r["ms"] * 1e3 / r["launches"]
+        ceil_op += ceil * r["launches"] / reps
+        print(f"{r['name']:22s} {us:10.2f} {ceil:8.2f} {ceil / us:6.1%} {r['ms'] / total:6.1%}")
+    print(f"operation: {op_ms * 1e3:.1f} us, arithmetic at the measured ceiling {ceil_op:.1f} us"
+          f" ({ceil_op / (op_ms * 1e3):.1%})")
 
 
 if __name__ == "__main__":
