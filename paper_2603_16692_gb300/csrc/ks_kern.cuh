@@ -366,12 +366,14 @@ __device__ __forceinline__ InttSet intt_set(const KArgs &a, const JobPtr &jp, co
   return r;
 }
 
-// Inverse NTT, row pass (global stages logN-1 .. logN1), all `outer` polynomials of
-// limb blockIdx.y in one CTA (shared twiddles). With a single pass (N1 == 1) it also
-// applies the per-limb scale (canonical output).
+// Inverse NTT, row pass (global stages logN-1 .. logN1) of limb `by`: all `outer`
+// polynomials in one CTA (shared twiddles), or only polynomial `only_o` when it is
+// >= 0. With a single pass (N1 == 1) it also applies the per-limb scale (canonical
+// output).
 template <int LOGN, int RL>
 __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
-                                             int which, int bx, int by, unsigned char *raw) {
+                                             int which, int bx, int by, unsigned char *raw,
+                                             int only_o = -1) {
   using GT = GeoT<LOGN, RL, 1>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
@@ -383,7 +385,8 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_i, prime, blk), GT::TWR);
   pdl_wait();
   const ulonglong2 sc = is.scale[ii];
-  for (int o = 0; o < is.outer; ++o) {
+  const int o0 = only_o < 0 ? 0 : only_o, o1 = only_o < 0 ? is.outer : only_o + 1;
+  for (int o = o0; o < o1; ++o) {
     if (which == 0 && jp.dsrc)
       load_rows_copy<GT>(sm, jp.dsrc + (size_t)ii * N, const_cast<u64 *>(jp.d) + (size_t)ii * N,
                          r0);
@@ -406,19 +409,36 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   }
 }
 
+// Grid row of an inverse-NTT launch: the limb, and with `split` the polynomial too
+// (blockIdx.y = o * limbs + limb), so that the two accumulator polynomials of the
+// P-limbs run in separate CTAs when one CTA per limb would leave SMs idle.
+__device__ __forceinline__ int inv_grid_row(const KArgs &a, int which, int split, int &only_o) {
+  int by = blockIdx.y;
+  only_o = -1;
+  if (split) {
+    const int inner = which == 0 ? a.nq : a.np;
+    only_o = by / inner;
+    by -= only_o * inner;
+  }
+  return by;
+}
+
 template <int LOGN, int RL>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
-    k_inv_row(KArgs a, JobSet js, WsOff wo, int which) {
+    k_inv_row(KArgs a, JobSet js, WsOff wo, int which, int split) {
   extern __shared__ __align__(16) unsigned char raw[];
-  inv_row_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
+  int only_o;
+  const int by = inv_grid_row(a, which, split, only_o);
+  inv_row_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, by, raw, only_o);
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
-// per-limb scale.
+// per-limb scale; `only_o` as in the row pass.
 template <int LOGN, int RL>
 __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
-                                             int which, int bx, int by, unsigned char *raw) {
+                                             int which, int bx, int by, unsigned char *raw,
+                                             int only_o = -1) {
   using GT = GeoT<LOGN, RL, 0>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
@@ -429,7 +449,8 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
   stage_tw<GT>(tws, col_table<GT>(a.tab.twc_i, prime), GT::TWC);
   pdl_wait();
   const ulonglong2 sc = is.scale[ii];
-  for (int o = 0; o < is.outer; ++o) {
+  const int o0 = only_o < 0 ? 0 : only_o, o1 = only_o < 0 ? is.outer : only_o + 1;
+  for (int o = o0; o < o1; ++o) {
     u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * (size_t)a.N;
     load_cols<GT>(sm, d, c0);
     __syncthreads();
@@ -451,9 +472,11 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
 template <int LOGN, int RL>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT,
                                   min_blocks(GeoT<LOGN, RL, 0>::NT, RL == 4 ? 512 : 768))
-    k_inv_col(KArgs a, JobSet js, WsOff wo, int which) {
+    k_inv_col(KArgs a, JobSet js, WsOff wo, int which, int split) {
   extern __shared__ __align__(16) unsigned char raw[];
-  inv_col_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, blockIdx.y, raw);
+  int only_o;
+  const int by = inv_grid_row(a, which, split, only_o);
+  inv_col_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, by, raw, only_o);
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
@@ -730,6 +753,11 @@ inline cudaError_t smem_attr(K kernel, int bytes) {
 
 inline KArgs args_of(const ks_context *c) { return make_args(c); }
 
+// Below four CTAs per SM of a GB300 (152 SMs) a launch is latency-bound on its few
+// CTAs' serial work (measured at (2, 2^15, 10): the accumulator iNTT passes 12.1 ->
+// 10.1 us and 12.0 -> 10.8 us with one CTA per polynomial).
+constexpr int kSplitCtas = 4 * 152;
+
 template <int LOGN, int RL>
 struct Launch {
   using GTC = GeoT<LOGN, RL, 0>;  // column-pass geometry
@@ -756,20 +784,28 @@ struct Launch {
 
   static int count(const ks_context *c, const Tasks &tk) { return count_tasks(c, tk); }
 
+  // The accumulator P-limbs (which = 1) hold two polynomials per limb: they get one CTA
+  // each when a CTA per limb would give fewer than kSplitCtas CTAs.
+  static int inv_split(int grid, int inner, int which, int jobs) {
+    return which == 1 && grid * inner * jobs < kSplitCtas ? 1 : 0;
+  }
+
   static cudaError_t intt_row(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
                               cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
     if (inner == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_inv_row<LOGN, RL>, dim3(GRID_ROW, inner, js.n), dim3(GTR::NT),
-                      GTR::SMEM_ROW, s, args_of(c), js, wo, which);
+    const int split = inv_split(GRID_ROW, inner, which, js.n);
+    return launch_pdl(k_inv_row<LOGN, RL>, dim3(GRID_ROW, inner << split, js.n), dim3(GTR::NT),
+                      GTR::SMEM_ROW, s, args_of(c), js, wo, which, split);
   }
 
   static cudaError_t intt_col(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
                               cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
     if (GTC::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_inv_col<LOGN, RL>, dim3(GRID_COL, inner, js.n), dim3(GTC::NT),
-                      GTC::SMEM_COL, s, args_of(c), js, wo, which);
+    const int split = inv_split(GRID_COL, inner, which, js.n);
+    return launch_pdl(k_inv_col<LOGN, RL>, dim3(GRID_COL, inner << split, js.n), dim3(GTC::NT),
+                      GTC::SMEM_COL, s, args_of(c), js, wo, which, split);
   }
 
   template <int PRO>

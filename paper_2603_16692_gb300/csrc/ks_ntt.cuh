@@ -28,14 +28,18 @@ namespace ks {
 // Compile-time geometry of the two passes for N = 2^LOGN (also used on the host
 // to lay out the row-pass twiddle table by row tile).
 __host__ __device__ constexpr int geo_loga(int logn) { return logn <= 12 ? 0 : logn / 2; }
-// Tiles: 2^10 points up to N = 2^15; above, 2^11 for the column pass and 2^10 for
-// the row pass (measured on GB300: at 2^15 the smaller tiles double the CTAs of the
-// one-wave launches, 94.8 -> 85.8 us per KeySwitch at (2, 2^15, 10); at 2^16 the row
-// passes are faster and the column passes slower with 2^10-point tiles).
+// Tiles (measured on GB300). Column pass: 2^10 points up to N = 2^15, 2^11 above (at
+// 2^15 the smaller tiles double the CTAs of the one-wave launches, 94.8 -> 85.8 us per
+// KeySwitch at (2, 2^15, 10); at 2^16 the column passes are slower with 2^10 points).
+// Row pass: 2^9 points up to N = 2^15, 2^10 above (2^9 against 2^10: 36.9 -> 33.3 us at
+// (2, 2^13, 7), 81.5 -> 77.8 us at (2, 2^14, 20), 13.4 k -> 14.0 k KeySwitch/s at
+// (2, 2^15, 10); at (4, 2^16, 35) 2^9 is 2% slower).
 __host__ __device__ constexpr int geo_tile_log_col(int logn) {
   return logn <= 12 ? logn : (logn >= 16 ? 11 : 10);
 }
-__host__ __device__ constexpr int geo_tile_log_row(int logn) { return logn <= 12 ? logn : 10; }
+__host__ __device__ constexpr int geo_tile_log_row(int logn) {
+  return logn <= 12 ? logn : (logn <= 15 ? 9 : 10);
+}
 __host__ __device__ constexpr int geo_loggr(int logn) {
   return geo_tile_log_row(logn) - (logn - geo_loga(logn));
 }
