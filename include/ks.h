@@ -196,11 +196,23 @@ int ks_hrot(ks_context *ctx, const uint64_t *ct_dev, uint32_t galois_elt,
  * device-resident; synchronizes `stream` before returning.
  *   Pinned (page-locked, device-mapped) buffers: the first kernel reads the input
  *   straight from host memory over the CPU-GPU link and the last kernel writes the
- *   result straight into host memory (no staging copies).
+ *   result straight into host memory (no staging copies); both must be 16-byte
+ *   aligned (else KS_EALIGN).
  *   Pageable buffers: copied through device staging buffers owned by the context.
  * Both host buffers must stay valid and unmodified by other threads until return. */
 int ks_switch_host(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
                    uint64_t *out_host, int variant, int chunks, void *stream);
+
+/* ks_switch_host without the synchronization, for streams of host-buffer KeySwitches:
+ * d_host and out_host must be pinned, device-mapped buffers (cudaHostAlloc /
+ * cudaHostRegister; anything else returns KS_EINVAL and launches nothing). The first
+ * kernel reads d_host over the CPU-GPU link and the last one writes out_host; the
+ * result is there once `stream` has passed this call (an event or a synchronize), and
+ * d_host must stay unmodified until then. Calls on one context share its staging
+ * buffer and workspace, so they must be ordered (issued on one stream); consecutive
+ * calls are chained like ks_switch's (N <= 2^12: cached graph replay). */
+int ks_switch_host_async(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
+                         uint64_t *out_host, int variant, int chunks, void *stream);
 
 /* ks_switch without any device allocation, for callers that cannot allocate device
  * memory when they switch keys: code running while a CUDA graph is captured

@@ -834,10 +834,15 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
   });
 }
 
-int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
-                   int variant, int chunks, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// ks_switch_host / ks_switch_host_async. `async`: pinned buffers only, no final
+// synchronization, and direct (chained) launches where ks_switch uses them.
+int switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
+                int variant, int chunks, cudaStream_t s, bool async) {
   if (!c || !d_host || !evk || !out_host) return KS_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
   const size_t in_b = (size_t)c->nq * c->N * 8, out_b = 2 * in_b;
   {
     std::lock_guard<std::mutex> lk(c->ws_mu);
@@ -869,6 +874,9 @@ int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, u
   const u64 *d_map = host_mapped(d_host);
   u64 *out_map = const_cast<u64 *>(host_mapped(out_host));
   const bool mapped = d_map && out_map;
+  if (async && !mapped) return KS_EINVAL;
+  // the kernels access mapped host buffers with 16-byte vector loads and stores
+  if (mapped && (!aligned16(d_map) || !aligned16(out_map))) return KS_EALIGN;
   rc = with_workspace(c, nullptr, 0, pl.total * 8, [&](u64 *base) {
     JobSet js = {};
     js.n = 1;
@@ -880,6 +888,7 @@ int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, u
     const std::array<uintptr_t, 10> key = {
         3, (uintptr_t)plan_code(pl), (uintptr_t)pl.chunks, (uintptr_t)d_host, (uintptr_t)evk,
         (uintptr_t)din, (uintptr_t)out_host, (uintptr_t)base, (uintptr_t)s, 0};
+    if (async && !use_graphs(c)) return run_plan(c, pl, js, s);
     return cached_launch(c, key, s, [&](cudaStream_t q) {
       if (!mapped) KS_TRY(cudaMemcpyAsync(din, d_host, in_b, cudaMemcpyHostToDevice, q));
       const int r = run_plan(c, pl, js, q);
@@ -888,9 +897,23 @@ int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, u
       return (int)KS_OK;
     });
   });
-  if (rc) return rc;
+  if (rc || async) return rc;
   KS_TRY(cudaStreamSynchronize(s));
   return KS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
+                   int variant, int chunks, void *stream) {
+  return switch_host(c, d_host, evk, out_host, variant, chunks, (cudaStream_t)stream, false);
+}
+
+int ks_switch_host_async(ks_context *c, const uint64_t *d_host, const uint64_t *evk,
+                         uint64_t *out_host, int variant, int chunks, void *stream) {
+  return switch_host(c, d_host, evk, out_host, variant, chunks, (cudaStream_t)stream, true);
 }
 
 int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uint64_t *a,

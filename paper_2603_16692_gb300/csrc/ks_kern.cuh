@@ -383,7 +383,12 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   const u64 m = a.tab.mod[prime].m, mu = a.tab.mod[prime].mu;
   const size_t N = a.N;
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_i, prime, blk), GT::TWR);
-  pdl_wait();
+  // Reading the input from host memory (`dsrc`), this pass writes only v and the device
+  // copy of d, which no kernel of the previous operation on the stream reads once its
+  // last kernel runs: it starts without waiting, so its host reads overlap that kernel's
+  // host writes, and waits for it at the end (keeping the chain's order for what follows).
+  const bool host_in = which == 0 && jp.dsrc;
+  if (!host_in) pdl_wait();
   const ulonglong2 sc = is.scale[ii];
   const int o0 = only_o < 0 ? 0 : only_o, o1 = only_o < 0 ? is.outer : only_o + 1;
   for (int o = o0; o < o1; ++o) {
@@ -407,6 +412,7 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
     }
     __syncthreads();
   }
+  if (host_in) pdl_wait();
 }
 
 // Grid row of an inverse-NTT launch: the limb, and with `split` the polynomial too
@@ -737,6 +743,10 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
     k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
+  // host-buffer operation: let the next one's input pass (which reads host memory and
+  // does not wait for this kernel before it ends) start while this one writes its result
+  // to host memory
+  if (js.j[blockIdx.z].dsrc) pdl_trigger();
   moddown_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }

@@ -69,7 +69,8 @@ SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_key
            "ks_profile_end", "ks_noalloc_scratch_bytes", "ks_switch_noalloc", "ks_tune",
            "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status",
            "ks_context_at_level", "ks_keygen_relin", "ks_keygen_galois",
-           "ks_eval_workspace_size", "ks_hmul", "ks_hrot", "ks_calibrate")
+           "ks_eval_workspace_size", "ks_hmul", "ks_hrot", "ks_calibrate",
+           "ks_switch_host_async")
 
 
 def lib_path() -> str:
@@ -95,6 +96,7 @@ def load(build: bool = True):
         l.ks_workspace_size.argtypes = [vp, i, i, ctypes.POINTER(sz)]
         l.ks_switch.argtypes = [vp, vp, vp, vp, i, i, vp, sz, vp]
         l.ks_switch_host.argtypes = [vp, vp, vp, vp, i, i, vp]
+        l.ks_switch_host_async.argtypes = [vp, vp, vp, vp, i, i, vp]
         l.ks_switch_batch.argtypes = [ctypes.POINTER(ks_job), i, i, vp]
         l.ks_tune.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp]
         l.ks_mlp_forward.argtypes = [vp, vp, i, vp, vp]
@@ -279,13 +281,43 @@ def ks_switch_noalloc(ctx: int, d, evk, out, variant: int = KS_AUTO, chunks: int
                                     _stream(stream)), "ks_switch_noalloc")
 
 
+def _host_ptr(x) -> int:
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("libks takes contiguous (row-major) host arrays")
+        return x.ctypes.data
+    return _ptr(x)
+
+
 def ks_switch_host(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO, chunks: int = 0,
                    stream=None):
     """d_host / out_host: CPU tensors (pinned for full bandwidth) or numpy arrays."""
-    def hp(x):
-        return x.ctypes.data if hasattr(x, "ctypes") else x.data_ptr()
-    _check(load().ks_switch_host(ctx, hp(d_host), _ptr(evk), hp(out_host), variant, chunks,
-                                 _stream(stream)), "ks_switch_host")
+    _check(load().ks_switch_host(ctx, _host_ptr(d_host), _ptr(evk), _host_ptr(out_host),
+                                 variant, chunks, _stream(stream)), "ks_switch_host")
+
+
+def ks_switch_host_async(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO,
+                         chunks: int = 0, stream=None):
+    """ks_switch_host without the synchronization; d_host / out_host must be pinned CPU
+    tensors. The result is in out_host once the stream has passed the call."""
+    _check(load().ks_switch_host_async(ctx, _host_ptr(d_host), _ptr(evk), _host_ptr(out_host),
+                                       variant, chunks, _stream(stream)), "ks_switch_host_async")
+
+
+def prepare_switch_host_async(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO,
+                              chunks: int = 0, stream=None):
+    """ks_switch_host_async on fixed buffers as a zero-argument callable (arguments
+    marshalled once, as prepare_switch does)."""
+    f = load().ks_switch_host_async
+    vp = ctypes.c_void_p
+    args = (vp(ctx), vp(_host_ptr(d_host)), vp(_ptr(evk)), vp(_host_ptr(out_host)),
+            ctypes.c_int(variant), ctypes.c_int(chunks), vp(_stream(stream)))
+
+    def call():
+        rc = f(*args)
+        if rc != KS_OK:
+            raise KSError(rc, "ks_switch_host_async")
+    return call
 
 
 def ks_switch_batch(jobs, flags: int = 0, stream=None):

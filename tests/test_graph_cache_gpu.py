@@ -101,3 +101,39 @@ def test_host_buffer_entry_replays(pinned):
             assert np.array_equal(got, c[7]), f"call {rep}: " + first_mismatch(got, c[7])
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("cfg", [(2, 12, 5), (2, 13, 6), (2, 15, 4)])
+def test_host_async_queue(cfg):
+    """ks_switch_host_async: several host-buffer KeySwitches queued on one stream with a
+    ring of pinned inputs and outputs (single-pass graph replay at 2^12, chained direct
+    launches above), synchronized once; every output is the oracle's for its input.
+    Pageable buffers are refused."""
+    import torch
+    cases = [oracle_case(cfg, s) for s in (0, 1, 2)]
+    prm = cases[0][0]
+    ctx = ks.Context(prm)
+    try:
+        evks = [dev(c[6]) for c in cases]
+        d_hs = [torch.from_numpy(c[5]).pin_memory() for c in cases]
+        out_hs = [torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64).pin_memory()
+                  for _ in range(6)]
+        for rep in range(6):
+            out_hs[rep].fill_(0)
+            ks.ks_switch_host_async(ctx.h, d_hs[rep % 3], evks[rep % 3], out_hs[rep])
+        torch.cuda.synchronize()
+        for rep in range(6):
+            got, want = out_hs[rep].numpy(), cases[rep % 3][7]
+            assert np.array_equal(got, want), f"call {rep}: " + first_mismatch(got, want)
+        d_pageable = np.array(cases[0][5])
+        with pytest.raises(ks.KSError):
+            ks.ks_switch_host_async(ctx.h, d_pageable, evks[0], out_hs[0])
+        # pinned but 8 bytes off a 16-byte boundary: refused before any launch
+        big = torch.empty(d_hs[0].numel() + 1, dtype=torch.uint64).pin_memory()
+        d_off = big[1:].view(prm.L + 1, prm.N)
+        assert d_off.data_ptr() % 16 == 8
+        with pytest.raises(ks.KSError) as err:
+            ks.ks_switch_host_async(ctx.h, d_off, evks[0], out_hs[0])
+        assert err.value.code == ks.KS_EALIGN
+    finally:
+        ctx.close()
