@@ -126,21 +126,22 @@ def workload_config(prm, variant_name, chunks, unfused, ring, ring_mb, l2_mb):
 # ---------------------------------------------------------------------------
 # CPU oracle (the reported baseline and the reference arm)
 
-def oracle_sample(prm, seconds: float, max_reps: int):
-    """Time oracle KeySwitches on all host cores for about `seconds` (at least one)."""
+def oracle_sample(prm, seconds: float, max_reps: int, nthreads: int | None = None):
+    """Time oracle KeySwitches on `nthreads` host threads (default: all cores) for about
+    `seconds` (at least one)."""
     from oracle import oracle as O
     s_from, s_to, a, e = W.gen_keys(prm, 0)
     d = W.gen_input(prm, 0)
     evk = O.keygen(prm, s_from, s_to, a, e)
-    O.keyswitch(prm, d, evk)  # warm (tables, threads)
+    O.keyswitch(prm, d, evk, nthreads=nthreads)  # warm (tables, threads)
     reps, t0 = 0, time.perf_counter()
     while reps < max_reps:
-        O.keyswitch(prm, d, evk)
+        O.keyswitch(prm, d, evk, nthreads=nthreads)
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    return reps, el, O.default_threads()
+    return reps, el, nthreads or O.default_threads()
 
 
 def run_reference(args, prm, rank: int, world: int):
@@ -390,6 +391,19 @@ def eval_measure(args, ks, torch, dev, stream, l2):
                          "keyswitch_per_s": 1e3 / t_ks, "hmul_per_s": 1e3 / t_mul,
                          "hrot_per_s": 1e3 / t_rot, "ks_ms": t_ks, "hmul_ms": t_mul,
                          "hrot_ms": t_rot}
+            if name == "c3":
+                # every dataflow x chunks 2..10 x fused/unfused (radix 8), one KeySwitch
+                table = {}
+                for base in (ks.KS_DSOB, ks.KS_DPOB, ks.KS_DSOC, ks.KS_DPOC):
+                    for unf in (0, ks.KS_UNFUSED):
+                        chunk_list = range(2, 11) if base in (ks.KS_DSOC, ks.KS_DPOC) else (0,)
+                        for ch in chunk_list:
+                            vv = base | unf
+                            table[ks.variant_name(vv, ch)] = per_call_ms(
+                                lambda k: ks.ks_switch(ctx.h, cts[k % 3][1], keys[k % 2], res, vv,
+                                                       ch, None, stream), 10)
+                out["c3_variants_ms"] = {k: round(t, 4) for k, t in
+                                         sorted(table.items(), key=lambda kv: kv[1])}
         finally:
             ctx.close()
 
@@ -532,6 +546,17 @@ def main():
     el_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     value = job_rate(world, args.steps, el_ms)
 
+    # warm L2: the same buffer set every step (reported beside the cold-L2 `value`)
+    kw = min(args.steps, 2000)
+    barrier()
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    for _ in range(kw):
+        calls[0]()
+    w1.record(stream)
+    barrier()
+    warm_value = job_rate(world, kw, max_over_ranks(w0.elapsed_time(w1), dist, dev))
+
     # host cost of one step (Python call + launches), enqueued ahead of an idle GPU: a
     # short burst well inside the launch queue, so the host never waits for the device
     host_us = []
@@ -636,6 +661,7 @@ def main():
                     for s in sorted(stats, key=lambda s: -s["ms"])],
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "host_us_per_step": host_us,
+        "warm_l2_value": warm_value,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": (prm.L + 1) * prm.N * 8,
                 "d2h_bytes_per_step": 2 * (prm.L + 1) * prm.N * 8,
@@ -649,10 +675,13 @@ def main():
         line["eval"] = eval_measure(args, ks, torch, dev, stream, l2)
     if world == 1 and not args.no_cpu:
         reps, el, cores = oracle_sample(prm, args.cpu_seconds, 10000)
+        r1, el1, _ = oracle_sample(prm, args.cpu_seconds / 2, 10000, nthreads=1)
         line["cpu_baseline"] = {"value": reps / el, "unit": UNIT, "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"{reps} full KeySwitches of the same workload in"
-                                          f" {el:.1f} s (bounded at ~{args.cpu_seconds:.0f} s)"}
+                                          f" {el:.1f} s (bounded at ~{args.cpu_seconds:.0f} s)",
+                                "single_thread": {"value": r1 / el1, "unit": UNIT,
+                                                  "sample": f"{r1} KeySwitches in {el1:.1f} s"}}
     else:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
