@@ -293,13 +293,20 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
         sel_info["sweep"] = f"{len(data['points'])} points (+ {len(data.get('levels', []))} " \
                             f"lower-level rows) x {len(data['cands'])} plans, {len(tr)} train / " \
                             f"{len(te)} held-out points"
-        picks = sel.choose([W.make_params(*cfg) for cfg in jobs])
-        arg_sel = [(h, d, evk, out, S.CANDS[k][1], S.CANDS[k][2])
-                   for (h, d, evk, out), k in zip(arg, picks)]
-        ms_sel = timed(lambda: ks.ks_switch_batch(arg_sel, ks.KS_BATCH_GRAPH, stream),
-                       args.batch_steps)
+        # the network installed in the library plans the batch itself (KS_BATCH_SELECT:
+        # one ks_mlp_forward launch per context, then the graph of the picked plans)
+        sel.install()
+        arg_auto = [(h, d, evk, out, ks.KS_AUTO, 0) for h, d, evk, out in arg]
+        sflags = ks.KS_BATCH_GRAPH | ks.KS_BATCH_SELECT
+        ms_sel = timed(lambda: ks.ks_switch_batch(arg_auto, sflags, stream), args.batch_steps)
         sel_info["batch_value"] = len(jobs) / (ms_sel / 1e3)
-        sel_info["batch_picks"] = {S.CANDS[k][0]: picks.count(k) for k in set(picks)}
+        names = {(v, c): n for n, v, c in S.CANDS}
+        lib_picks = [names.get((ks.ks_context_info(h)["selected_variant"],
+                                ks.ks_context_info(h)["selected_chunks"]), "?")
+                     for h, _, _, _ in arg]
+        py_picks = [S.CANDS[k][0] for k in sel.choose([W.make_params(*cfg) for cfg in jobs])]
+        sel_info["batch_picks"] = {n: lib_picks.count(n) for n in sorted(set(lib_picks))}
+        sel_info["library_picks_match_python"] = lib_picks == py_picks
     except (OSError, ValueError, KeyError) as ex:
         sel_info = {"error": str(ex)}
     flags = ks.KS_BATCH_GRAPH | ks.KS_BATCH_AUTOTUNE

@@ -87,6 +87,8 @@ typedef struct {
   float tuned_ms;     /* its time per KeySwitch in the tuning run */
   int L;              /* level of this context (nq = L+1) */
   int top_L;          /* level of the context whose keys it reads (= L unless a level view) */
+  int selected_variant; /* plan picked by ks_select (0 = none) */
+  int selected_chunks;
 } ks_info;
 
 typedef struct ks_context ks_context;
@@ -146,7 +148,8 @@ int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *by
  *   evk_dev [beta][2][QP][N]    keys from ks_keygen (or any canonical keys)
  *   out_dev [2][L+1][N]         output pair, NTT form; must not alias the inputs
  *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16), or KS_AUTO (the
- *           plan ks_tune chose for this context, else DPOB fused radix 8)
+ *           plan ks_tune chose for this context, else the one ks_select chose, else
+ *           DPOB fused radix 8)
  *   chunks  2..10 for the OC variants (0 = 2); ignored for OB
  *   workspace_dev / workspace_bytes: caller scratch of at least
  *           ks_workspace_size() bytes, or NULL/0 to use the context's internal
@@ -249,6 +252,9 @@ typedef struct {
 #define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph, replay it on later
                                  calls with the same jobs (same pointers) */
 #define KS_BATCH_AUTOTUNE 0x2 /* ks_tune each context first (once per group size) */
+#define KS_BATCH_SELECT 0x8  /* jobs naming KS_AUTO run the plan of the installed selector
+                                network (ks_select, run once per context and selector);
+                                not with KS_BATCH_AUTOTUNE or KS_BATCH_PERSISTENT */
 #define KS_BATCH_PERSISTENT 0x4 /* run the whole batch in one persistent kernel (every
                                    job's N in 2^13..2^17; plans DPOB, fused) */
 #define KS_BATCH_TEST_STALL 0x100 /* tests only, with KS_BATCH_PERSISTENT: make one
@@ -310,6 +316,37 @@ int ks_mlp_grad(const float *params_dev, const float *x_dev, const float *t_dev,
 int ks_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev, float *grad_scratch,
                  const float *x_dev, const float *t_dev, const float *mask_dev, int batch,
                  int steps, float lr, int step0, float *loss_dev, void *stream);
+
+/* The learned dataflow selector inside the library (a parameter-aware choice of the
+ * dataflow, as Sec. V proposes): a trained 6-64-64-4 network (KS_MLP_PARAMS floats in
+ * the layout of ks_mlp_forward), its standardisation and its four candidate plans.
+ *   Features of a context with n_Q = L+1 Q-limbs, alpha special primes, beta digits,
+ *   QP = n_Q + alpha and d = dnum (a level view: d = beta), against l2_bytes (0: the
+ *   current device's L2 size): log2 N, n_Q, d, log2(beta QP N 8 / l2),
+ *   log2(QP N 8 / l2), log2(2 beta QP N 8 / l2) (the DPOB and DSOB ModUp working sets
+ *   and the key bytes, Table III); the network sees (f - x_mean) / x_std.
+ *   Output k (standardised) decodes as e_k = y_k t_std[k] + t_mean[k]; the predicted
+ *   log-latency of candidate 0 is e_0, of candidate k >= 1 e_0 + e_k; the pick is the
+ *   smallest (the first on ties). */
+typedef struct {
+  float params[KS_MLP_PARAMS];
+  double x_mean[6], x_std[6];
+  double t_mean[4], t_std[4];
+  int variant[4], chunks[4]; /* candidate plans (as for ks_switch) */
+  long long l2_bytes;
+} ks_selector;
+
+/* Installs a copy of `sel` for this process, its parameters on the current device
+ * (synchronous). KS_EINVAL for a null pointer, a non-finite value, a standard
+ * deviation <= 0, a negative l2_bytes or an invalid plan; KS_ENOMEM / KS_ECUDA. */
+int ks_selector_load(const ks_selector *sel);
+
+/* Runs the installed network for `ctx` (one ks_mlp_forward launch on `stream`, which
+ * it then synchronizes) and records the pick as the context's selected plan: KS_AUTO
+ * uses it when ks_tune has not chosen one, and ks_switch_batch with KS_BATCH_SELECT
+ * uses it for jobs naming KS_AUTO. Writes the plan to *variant / *chunks when not
+ * null. KS_EINVAL when no selector is installed on the current device. */
+int ks_select(ks_context *ctx, int *variant, int *chunks, void *stream);
 
 /* Per-kernel timing with CUDA events, for measurement. Between ks_profile_begin and
  * ks_profile_end every kernel launch made by ks_switch on this thread is bracketed

@@ -42,11 +42,13 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16)) return KS_EINVAL;
   if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
-    // the tuned choice for single KeySwitches, else DPOB fused radix 8
-    const int tv = c->tuned_variant;
-    if (tv > 0) {
-      variant = tv | (variant & ~0xff);
+    // the tuned choice for single KeySwitches, else the selector's, else DPOB radix 8
+    if (c->tuned_variant > 0) {
+      variant = c->tuned_variant | (variant & ~0xff);
       if (chunks == 0) chunks = c->tuned_chunks;
+    } else if (c->sel_variant > 0) {
+      variant = c->sel_variant | (variant & ~0xff);
+      if (chunks == 0) chunks = c->sel_chunks;
     } else {
       variant = KS_DPOB | (variant & ~0xff);
     }
@@ -798,6 +800,8 @@ int ks_context_info(const ks_context *c, ks_info *info) {
   info->tuned_chunks = c->tuned_chunks;
   info->tuned_batch = c->tuned_batch;
   info->tuned_ms = c->tuned_ms;
+  info->selected_variant = c->sel_variant;
+  info->selected_chunks = c->sel_chunks;
   return KS_OK;
 }
 
@@ -1010,7 +1014,10 @@ int ks_hrot(ks_context *c, const uint64_t *ct, uint32_t galois_elt, const uint64
 
 int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
   if (njobs < 0 || (njobs > 0 && !jobs)) return KS_EINVAL;
-  if (flags & ~(KS_BATCH_GRAPH | KS_BATCH_AUTOTUNE | KS_BATCH_PERSISTENT | KS_BATCH_TEST_STALL))
+  if (flags & ~(KS_BATCH_GRAPH | KS_BATCH_AUTOTUNE | KS_BATCH_PERSISTENT | KS_BATCH_SELECT |
+                KS_BATCH_TEST_STALL))
+    return KS_EINVAL;
+  if ((flags & KS_BATCH_SELECT) && (flags & (KS_BATCH_AUTOTUNE | KS_BATCH_PERSISTENT)))
     return KS_EINVAL;
   if (njobs == 0) return KS_OK;
   for (int k = 0; k < njobs; ++k) {
@@ -1052,6 +1059,18 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       if (rc) return rc;
     }
   }
+  if (flags & KS_BATCH_SELECT) {
+    for (size_t g = 0; g < ctxs.size(); ++g) {
+      ks_context *c = ctxs[g];
+      if ((gplan[g].first & 0xff) != KS_AUTO) continue;  // the job names its plan
+      if (!selected_current(c)) {
+        int rc = ks_select(c, nullptr, nullptr, stream);
+        if (rc) return rc;
+      }
+      gplan[g] = {c->sel_variant | (gplan[g].first & ~0xff),
+                  gplan[g].second ? gplan[g].second : c->sel_chunks};
+    }
+  }
   std::vector<Plan> plans(ctxs.size());
   size_t total = 0;
   for (size_t g = 0; g < ctxs.size(); ++g) {
@@ -1086,9 +1105,13 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
       key.push_back((uintptr_t)jobs[k].out_dev);
       key.push_back(((uintptr_t)(uint32_t)jobs[k].variant << 32) | (uint32_t)jobs[k].chunks);
     }
+    // every input of a group's plan: its (selected) request and the context's choices
     for (size_t g = 0; g < ctxs.size(); ++g) {
-      key.push_back((uintptr_t)ctxs[g]->tuned_variant);
-      key.push_back((uintptr_t)ctxs[g]->tuned_chunks);
+      key.push_back(((uintptr_t)(uint32_t)gplan[g].first << 32) | (uint32_t)gplan[g].second);
+      key.push_back(((uintptr_t)(uint32_t)ctxs[g]->tuned_variant << 32) |
+                    (uint32_t)ctxs[g]->tuned_chunks);
+      key.push_back(((uintptr_t)(uint32_t)ctxs[g]->sel_variant << 32) |
+                    (uint32_t)ctxs[g]->sel_chunks);
     }
     auto it = g_batch.graphs.find(key);
     if (it != g_batch.graphs.end()) return g_batch.launch_ordered(it->second.exec, s);

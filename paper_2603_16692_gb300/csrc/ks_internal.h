@@ -125,6 +125,10 @@ struct ks_context {
   size_t ws_bytes = 0;
   // timing-based choice of the dataflow (ks_tune); 0 = not tuned
   int tuned_variant = 0, tuned_chunks = 0, tuned_batch = 0;
+  // the installed selector network's choice (ks_select); sel_gen = the selector it
+  // came from (0 = none)
+  int sel_variant = 0, sel_chunks = 0;
+  unsigned sel_gen = 0;
   float tuned_ms = 0;
   // staging buffers for ks_switch_host
   void *stage = nullptr;
@@ -201,6 +205,9 @@ struct LaunchTable {
   cudaError_t (*ntt_row)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
                          int buf, cudaStream_t);
 };
+// True when ctx's selected plan came from the selector installed now (ks_select.cu).
+bool selected_current(const ks_context *c);
+
 // rl = log2 of the radix of the register rounds (3: 8 points per thread, 2: 4 points
 // per thread, twice the threads per tile).
 const LaunchTable *launch_table(int logn, int rl);

@@ -18,7 +18,7 @@ KS_AUTO, KS_DSOB, KS_DPOB, KS_DSOC, KS_DPOC = 0, 1, 2, 3, 4
 KS_UNFUSED = 0x100
 KS_RADIX4 = 0x200
 KS_RADIX16 = 0x400
-KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE, KS_BATCH_PERSISTENT = 0x1, 0x2, 0x4
+KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE, KS_BATCH_PERSISTENT, KS_BATCH_SELECT = 0x1, 0x2, 0x4, 0x8
 KS_BATCH_TEST_STALL = 0x100
 VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
 
@@ -45,12 +45,23 @@ class ks_info(ctypes.Structure):
                 ("out_words", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t),
                 ("tuned_variant", ctypes.c_int), ("tuned_chunks", ctypes.c_int),
                 ("tuned_batch", ctypes.c_int), ("tuned_ms", ctypes.c_float),
-                ("L", ctypes.c_int), ("top_L", ctypes.c_int)]
+                ("L", ctypes.c_int), ("top_L", ctypes.c_int),
+                ("selected_variant", ctypes.c_int), ("selected_chunks", ctypes.c_int)]
 
 
 class ks_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("ops", ctypes.c_double), ("macs", ctypes.c_double)]
+
+
+KS_MLP_PARAMS, KS_MLP_MAX_BATCH = 4868, 4096
+
+
+class ks_selector(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_float * KS_MLP_PARAMS), ("x_mean", ctypes.c_double * 6),
+                ("x_std", ctypes.c_double * 6), ("t_mean", ctypes.c_double * 4),
+                ("t_std", ctypes.c_double * 4), ("variant", ctypes.c_int * 4),
+                ("chunks", ctypes.c_int * 4), ("l2_bytes", ctypes.c_longlong)]
 
 
 class ks_job(ctypes.Structure):
@@ -70,7 +81,7 @@ SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_key
            "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status",
            "ks_context_at_level", "ks_keygen_relin", "ks_keygen_galois",
            "ks_eval_workspace_size", "ks_hmul", "ks_hrot", "ks_calibrate",
-           "ks_switch_host_async")
+           "ks_switch_host_async", "ks_selector_load", "ks_select")
 
 
 def lib_path() -> str:
@@ -111,6 +122,8 @@ def load(build: bool = True):
         l.ks_hmul.argtypes = [vp, vp, vp, vp, vp, i, i, vp, sz, vp]
         l.ks_hrot.argtypes = [vp, vp, ctypes.c_uint32, vp, vp, i, i, vp, sz, vp]
         l.ks_calibrate.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), vp]
+        l.ks_selector_load.argtypes = [ctypes.POINTER(ks_selector)]
+        l.ks_select.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), vp]
         l.ks_strerror.argtypes = [i]
         l.ks_strerror.restype = ctypes.c_char_p
         l.ks_noalloc_scratch_bytes.argtypes = []
@@ -355,6 +368,33 @@ def ks_calibrate(kind: int, iters: int = 4096, stream=None) -> float:
     return r.value
 
 
+def ks_selector_load(params, x_mean, x_std, t_mean, t_std, plans, l2_bytes: int = 0):
+    """Installs a trained selector network in the library: params (KS_MLP_PARAMS floats),
+    the feature and target standardisation, and plans = four (variant, chunks)."""
+    import numpy as np
+    sel = ks_selector()
+    p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+    if p.size != KS_MLP_PARAMS or len(plans) != 4:
+        raise ValueError("ks_selector_load: 4868 parameters and four plans")
+    ctypes.memmove(sel.params, p.ctypes.data, p.nbytes)
+    for k in range(6):
+        sel.x_mean[k], sel.x_std[k] = float(x_mean[k]), float(x_std[k])
+    for k in range(4):
+        sel.t_mean[k], sel.t_std[k] = float(t_mean[k]), float(t_std[k])
+        sel.variant[k], sel.chunks[k] = int(plans[k][0]), int(plans[k][1])
+    sel.l2_bytes = int(l2_bytes)
+    _check(load().ks_selector_load(ctypes.byref(sel)), "ks_selector_load")
+
+
+def ks_select(ctx: int, stream=None):
+    """The installed selector's plan for the context (also recorded as its selected
+    plan). Returns (variant, chunks)."""
+    v, c = ctypes.c_int(), ctypes.c_int()
+    _check(load().ks_select(ctx, ctypes.byref(v), ctypes.byref(c), _stream(stream)),
+           "ks_select")
+    return v.value, c.value
+
+
 def ks_tune(ctx: int, d, evk, out, batch: int = 1, stream=None):
     """Times the dataflows on this job and makes the fastest the context's KS_AUTO plan.
     Returns (variant, chunks)."""
@@ -378,7 +418,6 @@ def variant_name(v: int, chunks: int = 0) -> str:
     return s
 
 
-KS_MLP_PARAMS, KS_MLP_MAX_BATCH = 4868, 4096
 
 
 def ks_mlp_forward(params, x, y, stream=None):

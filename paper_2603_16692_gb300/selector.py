@@ -240,6 +240,12 @@ class Selector:
     def choose(self, prms) -> list:
         return [int(k) for k in np.argmin(self.predict_ms(prms), axis=1)]
 
+    def install(self):
+        """Installs this network in the library (ks_selector_load): ks_select and
+        ks_switch_batch with KS_BATCH_SELECT then pick plans without Python."""
+        ks.ks_selector_load(self.params, self.x_mean, self.x_std, self.t_mean, self.t_std,
+                            [(v, c) for _, v, c in CANDS], self.l2)
+
     def to_json(self) -> dict:
         return {"params": self.params.tolist(), "x_mean": self.x_mean.tolist(),
                 "x_std": self.x_std.tolist(), "t_mean": self.t_mean.tolist(),

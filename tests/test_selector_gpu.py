@@ -10,6 +10,7 @@ import pytest
 from oracle import mlp_oracle as M
 from paper_2603_16692_gb300 import ks
 from paper_2603_16692_gb300 import selector as S
+from paper_2603_16692_gb300 import workload as W
 
 pytestmark = pytest.mark.gpu
 
@@ -114,3 +115,78 @@ def test_binding_rejects_strided_tensors():
     y = torch.empty((6, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(ValueError):
         ks.ks_mlp_forward(_dev(S.init_params(0)), x, y)
+
+
+@pytest.mark.skipif(not os.path.exists(SWEEP), reason="no committed GB300 sweep")
+def test_library_selector_matches_python_and_plans_a_batch():
+    """The network installed in the library (ks_selector_load) picks, through ks_select,
+    the plan the Python selector picks for the same workload (same kernel, features and
+    decoding), for top-level contexts and level views; a KS_BATCH_SELECT batch runs the
+    picked plans and stays bit-exact against the oracle."""
+    import torch
+    from oracle import oracle as O
+    data = S.load_json(SWEEP)
+    tr, te = S.split(len(data["points"]))
+    sel, _ = S.train(data, tr, steps=1500)
+    sel.install()
+    for i in te[:10]:
+        prm = W.make_params(*data["points"][i])
+        ctx = ks.Context(prm)
+        try:
+            want = S.CANDS[sel.choose([prm])[0]]
+            assert ks.ks_select(ctx.h) == (want[1], want[2]), (prm.name(), want[0])
+            assert ks.ks_context_info(ctx.h)["selected_variant"] == want[1]
+            lv = prm.L // 2
+            view = ctx.at_level(lv)
+            try:
+                want = S.CANDS[sel.choose([S.level_shape(prm, lv)])[0]]
+                assert ks.ks_select(view.h) == (want[1], want[2]), (prm.name(), lv, want[0])
+            finally:
+                view.close()
+        finally:
+            ctx.close()
+    # a batch of small jobs naming KS_AUTO, planned by the installed network
+    cfgs = [(2, 13, 7), (3, 14, 11), (2, 13, 7), (5, 12, 9)]
+    ctxs, arg, want = {}, [], []
+    try:
+        for k, cfg in enumerate(cfgs):
+            prm = W.make_params(*cfg)
+            if cfg not in ctxs:
+                ctxs[cfg] = ks.Context(prm)
+            g = W.rng(300 + k, 13)
+            d = W.uniform_limbs(g, prm.q, prm.N)
+            evk = W.uniform_limbs(g, prm.mods * (2 * prm.beta), prm.N).reshape(
+                prm.beta, 2, prm.QP, prm.N)
+            out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
+            arg.append((ctxs[cfg].h, _dev(d), _dev(evk), out))
+            want.append(O.keyswitch(prm, d, evk))
+        for flags in (ks.KS_BATCH_SELECT, ks.KS_BATCH_SELECT | ks.KS_BATCH_GRAPH):
+            for _, _, _, out in arg:
+                out.fill_(5)
+            ks.ks_switch_batch(arg, flags)
+            torch.cuda.synchronize()
+            for k, (_, _, _, out) in enumerate(arg):
+                assert np.array_equal(out.cpu().numpy(), want[k]), (flags, cfgs[k])
+        for cfg, c in ctxs.items():
+            v = ks.ks_context_info(c.h)["selected_variant"]
+            assert v == S.CANDS[sel.choose([W.make_params(*cfg)])[0]][1]
+        with pytest.raises(ks.KSError):
+            ks.ks_switch_batch(arg, ks.KS_BATCH_SELECT | ks.KS_BATCH_AUTOTUNE)
+    finally:
+        for c in ctxs.values():
+            c.close()
+
+
+def test_selector_load_rejects_bad_networks():
+    p = S.init_params(0)
+    ok = dict(x_mean=[0.0] * 6, x_std=[1.0] * 6, t_mean=[0.0] * 4, t_std=[1.0] * 4,
+              plans=[(v, c) for _, v, c in S.CANDS])
+    for bad in (dict(x_std=[1.0] * 5 + [0.0]), dict(t_std=[1.0, -1.0, 1.0, 1.0]),
+                dict(plans=[(9, 0)] + ok["plans"][1:]),
+                dict(plans=[(ks.KS_DPOB | ks.KS_RADIX4 | ks.KS_RADIX16, 0)] + ok["plans"][1:])):
+        with pytest.raises(ks.KSError):
+            ks.ks_selector_load(p, **{**ok, **bad})
+    q = p.copy()
+    q[7] = np.nan
+    with pytest.raises(ks.KSError):
+        ks.ks_selector_load(q, **ok)
