@@ -252,11 +252,11 @@ typedef struct {
 #define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph, replay it on later
                                  calls with the same jobs (same pointers) */
 #define KS_BATCH_AUTOTUNE 0x2 /* ks_tune each context first (once per group size) */
+#define KS_BATCH_PERSISTENT 0x4 /* run the whole batch in one persistent kernel (every
+                                   job's N in 2^13..2^17; plans DPOB, fused) */
 #define KS_BATCH_SELECT 0x8  /* jobs naming KS_AUTO run the plan of the installed selector
                                 network (ks_select, run once per context and selector);
                                 not with KS_BATCH_AUTOTUNE or KS_BATCH_PERSISTENT */
-#define KS_BATCH_PERSISTENT 0x4 /* run the whole batch in one persistent kernel (every
-                                   job's N in 2^13..2^17; plans DPOB, fused) */
 #define KS_BATCH_TEST_STALL 0x100 /* tests only, with KS_BATCH_PERSISTENT: make one
                                      dependency unreachable so that the bounded wait
                                      gives up and ks_batch_status reports KS_ETIMEOUT */
@@ -270,7 +270,8 @@ typedef struct {
  *
  * Runs njobs independent KeySwitches on `stream` (asynchronous). Jobs sharing a
  * context form a group: its jobs share every kernel launch (up to 16 jobs per
- * launch, grid z) with the context's tuned plan (KS_AUTO). Groups run concurrently on
+ * launch, grid z) with the job's plan (KS_AUTO: the context's tuned plan, or with
+ * KS_BATCH_SELECT the selector's). Groups run concurrently on
  * internal streams forked from and joined back to `stream`. The scratch is a
  * library-owned arena (grown on demand, outside any capture). Calls are serialized
  * internally; the arena is shared, so batches must not overlap on the GPU with other
