@@ -64,3 +64,28 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     # rank 1 of 2 returns at once, before looking at its arguments, timing or printing
     bench.run_reference(None, W.make_params(*W.C1), rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    """Rank 0 times the oracle and prints one JSON line with the contract's keys; its
+    cpu_baseline and e2e carry the line's own value (no transfers)."""
+    import json
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2603_16692_gb300 import workload as W
+    args = types.SimpleNamespace(steps=2, warmup=1)
+    bench.run_reference(args, W.make_params(*W.C1), rank=0, world=1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
+    assert line["config"]["workload"].endswith("(2,2^13,7)")
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == line["e2e"]["d2h_bytes_per_step"] == 0
