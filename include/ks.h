@@ -208,7 +208,8 @@ int ks_switch_host(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_
 
 /* ks_switch_host without the synchronization, for streams of host-buffer KeySwitches:
  * d_host and out_host must be pinned, device-mapped buffers (cudaHostAlloc /
- * cudaHostRegister; anything else returns KS_EINVAL and launches nothing). The first
+ * cudaHostRegister; anything else returns KS_EINVAL and launches nothing), 16-byte
+ * aligned (else KS_EALIGN). The first
  * kernel reads d_host over the CPU-GPU link and the last one writes out_host; the
  * result is there once `stream` has passed this call (an event or a synchronize), and
  * d_host must stay unmodified until then. Calls on one context share its staging
