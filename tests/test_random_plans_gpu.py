@@ -1,0 +1,56 @@
+"""Seeded random parity sweep: workloads (dnum, N, L) and plans (dataflow, chunks,
+fused/unfused, radix 4/8/16, caller workspace or the context's) drawn together, so
+that combinations the structured tests do not list (odd dnum with ragged digits,
+many chunks with radix 16, unfused OutputChunked at two-pass sizes, ...) are checked
+bit for bit against the oracle. Keys are uniform residues (the KeySwitch is the same
+arithmetic for any key), so the oracle's cost is one KeySwitch per case."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2603_16692_gb300 import ks
+from paper_2603_16692_gb300 import workload as W
+from tests.gpu_util import dev, first_mismatch, host
+
+pytestmark = pytest.mark.gpu
+
+BASES = (ks.KS_DSOB, ks.KS_DPOB, ks.KS_DSOC, ks.KS_DPOC)
+RADIX = (0, ks.KS_RADIX4, ks.KS_RADIX16)
+
+
+def draw(k: int):
+    """Case k: a workload with N in 2^5..2^16 and L+1 up to 48, and a plan."""
+    g = W.rng(7000 + k, 15)
+    logn = int(g.integers(5, 17))
+    L = int(g.integers(0, 48 if logn <= 13 else 24))
+    dnum = int(g.integers(1, min(L + 1, 12) + 1))
+    base = int(BASES[g.integers(0, 4)])
+    v = base | int(RADIX[g.integers(0, 3)]) | (ks.KS_UNFUSED if g.random() < 0.3 else 0)
+    chunks = int(g.integers(1, 11)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0
+    own_ws = bool(g.random() < 0.5)
+    return (dnum, logn, L), v, chunks, own_ws
+
+
+@pytest.mark.parametrize("k", range(48))
+def test_random_workload_and_plan(k):
+    import torch
+    cfg, v, chunks, own_ws = draw(k)
+    prm = W.make_params(*cfg)
+    g = W.rng(8000 + k, 16)
+    d = W.uniform_limbs(g, prm.q, prm.N)
+    evk = W.uniform_limbs(g, prm.mods * (2 * prm.beta), prm.N).reshape(prm.beta, 2, prm.QP,
+                                                                       prm.N)
+    want = O.keyswitch(prm, d, evk)
+    ctx = ks.Context(prm)
+    try:
+        ws = None
+        if own_ws:
+            n = ks.ks_workspace_size(ctx.h, v, chunks)
+            ws = torch.empty(n // 8 + 1, dtype=torch.uint64, device="cuda")
+        out = ctx.switch(dev(d), dev(evk), variant=v, chunks=chunks, workspace=ws)
+        torch.cuda.synchronize()
+        got = host(out)
+    finally:
+        ctx.close()
+    name = ks.variant_name(v, chunks)
+    assert np.array_equal(got, want), f"{prm.name()} {name}: " + first_mismatch(got, want)
