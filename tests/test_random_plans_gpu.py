@@ -54,3 +54,59 @@ def test_random_workload_and_plan(k):
         ctx.close()
     name = ks.variant_name(v, chunks)
     assert np.array_equal(got, want), f"{prm.name()} {name}: " + first_mismatch(got, want)
+
+
+def draw_eval(k: int):
+    """Case k of the evaluation sweep: a workload, a level below the top (or the top),
+    an operation (KeySwitch, HMUL, HROT with a random Galois element) and a plan."""
+    g = W.rng(9000 + k, 17)
+    logn = int(g.integers(5, 15))
+    L = int(g.integers(1, 40 if logn <= 12 else 20))
+    dnum = int(g.integers(1, min(L + 1, 10) + 1))
+    level = int(g.integers(0, L + 1))
+    op = ("switch", "hmul", "hrot")[int(g.integers(0, 3))]
+    base = int(BASES[g.integers(0, 4)])
+    v = base | int(RADIX[g.integers(0, 3)]) | (ks.KS_UNFUSED if g.random() < 0.3 else 0)
+    chunks = int(g.integers(1, 8)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0
+    rot = 2 * int(g.integers(0, 1 << logn)) + 1  # odd in [1, 2N)
+    return (dnum, logn, L), level, op, v, chunks, rot
+
+
+@pytest.mark.parametrize("k", range(24))
+def test_random_level_and_operation(k):
+    """KeySwitch, HMUL and HROT at random levels (level views with the top level's key)
+    under random plans, against the oracle's level-aware functions."""
+    import torch
+    cfg, level, op, v, chunks, rot = draw_eval(k)
+    prm = W.make_params(*cfg)
+    g = W.rng(10000 + k, 18)
+    key = W.uniform_limbs(g, prm.mods * (2 * prm.beta), prm.N).reshape(prm.beta, 2, prm.QP,
+                                                                       prm.N)
+    qs = prm.q[:level + 1]
+    x = W.uniform_limbs(g, qs * 2, prm.N).reshape(2, level + 1, prm.N)
+    y = W.uniform_limbs(g, qs * 2, prm.N).reshape(2, level + 1, prm.N)
+    if op == "switch":
+        want = O.keyswitch_level(prm, level, x[1], key)
+    elif op == "hmul":
+        want = O.hmul(prm, level, x, y, key)
+    else:
+        want = O.hrot(prm, level, x, rot, key)
+    top = ks.Context(prm)
+    view = top.at_level(level) if level < prm.L else top
+    try:
+        kk = dev(key)
+        if op == "switch":
+            out = view.switch(dev(x[1]), kk, variant=v, chunks=chunks)
+        elif op == "hmul":
+            out = view.hmul(dev(x), dev(y), kk, variant=v, chunks=chunks)
+        else:
+            out = view.hrot(dev(x), rot, kk, variant=v, chunks=chunks)
+        torch.cuda.synchronize()
+        got = host(out)
+    finally:
+        if view is not top:
+            view.close()
+        top.close()
+    name = ks.variant_name(v, chunks)
+    assert np.array_equal(got, want), f"{prm.name()} level {level} {op} {name}: " + \
+        first_mismatch(got, want)
