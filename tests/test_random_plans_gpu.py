@@ -110,3 +110,59 @@ def test_random_level_and_operation(k):
     name = ks.variant_name(v, chunks)
     assert np.array_equal(got, want), f"{prm.name()} level {level} {op} {name}: " + \
         first_mismatch(got, want)
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_random_batches(k):
+    """Random batches (1-12 jobs, some sharing a context, random plans or KS_AUTO) in
+    every batch mode: streams, graph (run twice: capture, then replay), autotuned, and
+    the persistent kernel (N >= 2^13); every job's output against the oracle."""
+    import torch
+    g = W.rng(11000 + k, 19)
+    persistent = k % 3 == 2
+    njobs = int(g.integers(1, 13))
+    cfgs, plans = [], []
+    for _ in range(njobs):
+        if cfgs and g.random() < 0.3:
+            cfgs.append(cfgs[int(g.integers(0, len(cfgs)))])
+        else:
+            logn = int(g.integers(13 if persistent else 6, 15))
+            L = int(g.integers(0, 20))
+            cfgs.append((int(g.integers(1, min(L + 1, 8) + 1)), logn, L))
+        if g.random() < 0.3:
+            plans.append((ks.KS_AUTO, 0))
+        else:
+            base = int(BASES[g.integers(0, 4)])
+            v = base | int(RADIX[g.integers(0, 3)]) | (ks.KS_UNFUSED if g.random() < 0.3 else 0)
+            plans.append((v, int(g.integers(1, 6)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0))
+    ctxs, arg, want = {}, [], []
+    try:
+        for j, cfg in enumerate(cfgs):
+            prm = W.make_params(*cfg)
+            if cfg not in ctxs:
+                ctxs[cfg] = ks.Context(prm)
+            gj = W.rng(12000 + 100 * k + j, 20)
+            d = W.uniform_limbs(gj, prm.q, prm.N)
+            evk = W.uniform_limbs(gj, prm.mods * (2 * prm.beta), prm.N).reshape(
+                prm.beta, 2, prm.QP, prm.N)
+            out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
+            arg.append((ctxs[cfg].h, dev(d), dev(evk), out, *plans[j]))
+            want.append(O.keyswitch(prm, d, evk))
+        modes = [0, ks.KS_BATCH_GRAPH, ks.KS_BATCH_GRAPH, ks.KS_BATCH_AUTOTUNE]
+        if persistent:
+            modes += [ks.KS_BATCH_PERSISTENT, ks.KS_BATCH_PERSISTENT | ks.KS_BATCH_GRAPH]
+        for flags in modes:
+            for a in arg:
+                a[3].fill_(3)
+            ks.ks_switch_batch(arg, flags)
+            if flags & ks.KS_BATCH_PERSISTENT:
+                assert ks.ks_batch_status() == ks.KS_OK
+            torch.cuda.synchronize()
+            for j, a in enumerate(arg):
+                got = host(a[3])
+                assert np.array_equal(got, want[j]), \
+                    f"flags {flags:#x} job {j} {cfgs[j]} {ks.variant_name(*plans[j])}: " + \
+                    first_mismatch(got, want[j])
+    finally:
+        for c in ctxs.values():
+            c.close()
