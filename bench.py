@@ -40,15 +40,15 @@ WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 # multiplication (one 64x64 high product ~4 IMAD + two 64-bit low products ~3 each).
 SMS, IMAD_PER_SM_CLK, IMAD_PER_MODOP = 152, 64, 10
 # DRAM bytes (read + write) per launch of the dominant kernel, from one cold-cache ncu
-# capture of the same kernel on the same workload (radix 8: 35.686144 MB read, 512 B
-# written; radix 4: 35.658752 MB read, 256 B written); keyed by (workload, plan,
+# capture of the same kernel on the same workload (radix 8: 35.6864 MB read, 768 B
+# written; radix 4: 35.658752 MB read, 0 B written); keyed by (workload, plan,
 # kernel). Missing = not captured for the current kernel code and plan (null).
-NCU_TRAFFIC = {("c2", "DPOB", "modup_row_keymult"): 35686656,
-               ("c2", "DPOB-r4", "modup_row_keymult"): 35659008}
+NCU_TRAFFIC = {("c2", "DPOB", "modup_row_keymult"): 35687168,
+               ("c2", "DPOB-r4", "modup_row_keymult"): 35658752}
 # From the same captures: the busiest integer pipe (sm__pipe_fmaheavy_cycles_active, %
 # of peak) and the issue activity (smsp__issue_active, % of peak) of that launch.
-NCU_PIPES = {("c2", "DPOB", "modup_row_keymult"): {"fmaheavy_pct": 29.9, "issue_pct": 31.5},
-             ("c2", "DPOB-r4", "modup_row_keymult"): {"fmaheavy_pct": 37.8, "issue_pct": 42.8}}
+NCU_PIPES = {("c2", "DPOB", "modup_row_keymult"): {"fmaheavy_pct": 30.6, "issue_pct": 32.0},
+             ("c2", "DPOB-r4", "modup_row_keymult"): {"fmaheavy_pct": 37.6, "issue_pct": 43.9}}
 
 
 def measured_alu(ks, stream, dom, per_launch_ms):
