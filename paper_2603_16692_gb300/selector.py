@@ -10,7 +10,7 @@ over the training rows): the latencies span three orders of magnitude across
 workloads while the choice depends on differences of a few percent, which an
 absolute-log target leaves almost unweighted. Training and inference run in the
 library's CUDA kernels (ks_mlp_train, ks_mlp_forward). Exhaustive timing of all
-ten plans stays the fallback and judges the regret. The selector never touches
+ten plans stays the fallback and the yardstick of the regret. The selector never touches
 the KeySwitch arithmetic.
 
 Features of (dnum, N, L) on a GPU with L2 bytes: log2 N, L+1, dnum, and log2 of
