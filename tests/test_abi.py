@@ -72,3 +72,26 @@ def test_switch_rejects_null_context():
     assert lib.ks_switch(None, None, None, None, 0, 0, None, 0, None) == ks.KS_EINVAL
     assert lib.ks_keygen(None, None, None, None, None, None, None) == ks.KS_EINVAL
     assert lib.ks_switch_batch(None, -1, 0, None) == ks.KS_EINVAL
+
+
+def test_new_entry_points_reject_bad_arguments_on_host():
+    """Argument checks that run before any CUDA call."""
+    lib = ks.load()
+    d = ctypes.c_double()
+    assert lib.ks_calibrate(0, 16, ctypes.byref(d), None) == ks.KS_EINVAL
+    assert lib.ks_calibrate(ks.KS_CAL_MAC, 0, ctypes.byref(d), None) == ks.KS_EINVAL
+    assert lib.ks_calibrate(ks.KS_CAL_BUTTERFLY, 16, None, None) == ks.KS_EINVAL
+    assert lib.ks_selector_load(None) == ks.KS_EINVAL
+    assert lib.ks_select(None, None, None, None) == ks.KS_EINVAL
+    assert lib.ks_switch_host_async(None, None, None, None, 0, 0, None) == ks.KS_EINVAL
+    sel = ks.ks_selector()
+    for k in range(6):
+        sel.x_std[k] = 1.0
+    for k in range(4):
+        sel.t_std[k] = 1.0
+        sel.variant[k] = ks.KS_DPOB
+    sel.x_std[2] = 0.0  # a zero standard deviation is refused before anything is copied
+    assert lib.ks_selector_load(ctypes.byref(sel)) == ks.KS_EINVAL
+    sel.x_std[2] = 1.0
+    sel.variant[1] = 7  # not a dataflow
+    assert lib.ks_selector_load(ctypes.byref(sel)) == ks.KS_EINVAL
