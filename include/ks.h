@@ -66,7 +66,7 @@ extern "C" {
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
-  uint32_t log2n;    /* N = 2^log2n, 4 <= log2n <= 17 */
+  uint32_t log2n;    /* N = 2^log2n, 1 <= log2n <= 17 */
   uint32_t L;        /* level: the input has L+1 limbs (1 <= L+1 <= 128) */
   const uint64_t *q; /* host array of the L+1 ciphertext primes */
   uint32_t nq;       /* must equal L+1 */
