@@ -150,7 +150,8 @@ int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *by
  *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16), or KS_AUTO (the
  *           plan ks_tune chose for this context, else the one ks_select chose, else
  *           DPOB fused radix 8)
- *   chunks  2..10 for the OC variants (0 = 2); ignored for OB
+ *   chunks  1..64 output groups for the OC variants (0 = 2; the paper searches 2..10);
+ *           ignored for OB
  *   workspace_dev / workspace_bytes: caller scratch of at least
  *           ks_workspace_size() bytes, or NULL/0 to use the context's internal
  *           workspace (allocated on first use and grown as needed; calls that use it
@@ -209,10 +210,9 @@ int ks_switch_host(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_
 /* ks_switch_host without the synchronization, for streams of host-buffer KeySwitches:
  * d_host and out_host must be pinned, device-mapped buffers (cudaHostAlloc /
  * cudaHostRegister; anything else returns KS_EINVAL and launches nothing), 16-byte
- * aligned (else KS_EALIGN). The first
- * kernel reads d_host over the CPU-GPU link and the last one writes out_host; the
- * result is there once `stream` has passed this call (an event or a synchronize), and
- * d_host must stay unmodified until then. Calls on one context share its staging
+ * aligned (else KS_EALIGN). The first kernel reads d_host over the CPU-GPU link and
+ * the last one writes out_host; the result is there once `stream` has passed this call
+ * (an event or a synchronize), and d_host must stay unmodified until then. Calls on one context share its staging
  * buffer and workspace, so they must be ordered (issued on one stream); consecutive
  * calls are chained like ks_switch's (N <= 2^12: cached graph replay). */
 int ks_switch_host_async(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
