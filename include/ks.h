@@ -272,8 +272,8 @@ typedef struct {
  * Runs njobs independent KeySwitches on `stream` (asynchronous). Jobs sharing a
  * context form a group: its jobs share every kernel launch (up to 16 jobs per
  * launch, grid z) with the job's plan (KS_AUTO: the context's tuned plan, or with
- * KS_BATCH_SELECT the selector's). Groups run concurrently on
- * internal streams forked from and joined back to `stream`. The scratch is a
+ * KS_BATCH_SELECT the selector's). Groups run concurrently on internal streams
+ * forked from and joined back to `stream`. The scratch is a
  * library-owned arena (grown on demand, outside any capture). Calls are serialized
  * internally; the arena is shared, so batches must not overlap on the GPU with other
  * batches (issue them on one stream). With KS_BATCH_GRAPH the whole batch is one
@@ -285,8 +285,8 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream);
 int ks_batch_status(void *stream);
 
 /* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
- * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one launch set)
- * and stores the fastest as the context's KS_AUTO plan. Writes the switched result to
+ * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one
+ * launch set) and stores the fastest as the context's KS_AUTO plan. Writes the switched result to
  * out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
 int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,
             int batch, int *variant, int *chunks, void *stream);
@@ -296,7 +296,8 @@ int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uin
 int ks_sync_status(ks_context *ctx, void *stream);
 
 /* Dataflow selector: an MLP 6 -> 64 -> 64 -> 4 (ReLU, FP32) that maps workload
- * features to the predicted log-latency of the four dataflows. The paper motivates
+ * features to predicted latencies of four candidate plans (the encoding and the
+ * features are those of ks_selector below). The paper motivates
  * it (parameter-aware choice of the dataflow, Sec. V) but gives no model; it never
  * touches the KeySwitch arithmetic. Parameters: KS_MLP_PARAMS floats,
  *   W1[6][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
