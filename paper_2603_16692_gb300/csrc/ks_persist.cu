@@ -52,7 +52,7 @@ constexpr int kStages = 8;
 constexpr int kPNT = 256;  // threads per CTA of the persistent kernel
 
 // The radix of the rounds for each N and pass: 256 threads per tile at every size
-// (tiles of 2^10 points take radix 4, tiles of 2^11 radix 8).
+// (tiles of 2^9 points take radix 2, 2^10 radix 4, 2^11 radix 8).
 __host__ __device__ constexpr int prl_col(int logn) { return geo_tile_log_col(logn) - 8; }
 __host__ __device__ constexpr int prl_row(int logn) { return geo_tile_log_row(logn) - 8; }
 
