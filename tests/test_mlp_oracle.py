@@ -62,3 +62,24 @@ def test_level_shape_matches_the_level_view():
     assert S.features(top, 1 << 27)[3:] == S.features(prm, 1 << 27)[3:]
     low = S.level_shape(prm, 10)
     assert (low.beta, low.QP, low.dnum) == (2, 20, 2)
+
+
+def test_selector_features_follow_the_working_set_definitions():
+    """The six features of a workload (the library computes the same in ks_select):
+    log2 N, L+1, dnum (digits for a level view), and log2 of the DPOB ModUp working set
+    beta*QP*N*8, the DSOB one QP*N*8 and the key bytes 2*beta*QP*N*8 over the L2 size;
+    here at (2, 2^15, 10) (alpha = 6, beta = 2, QP = 17) against a 2^27-byte L2."""
+    import math
+    from paper_2603_16692_gb300 import selector as S
+    from paper_2603_16692_gb300 import workload as W
+    prm = W.make_params(2, 15, 10)
+    f = S.features(prm, 1 << 27)
+    n8 = (1 << 15) * 8
+    assert f[:3] == [15, 11, 2]
+    assert f[3] == math.log2(2 * 17 * n8 / (1 << 27))
+    assert f[4] == math.log2(17 * n8 / (1 << 27))
+    assert f[5] == f[3] + 1.0
+    # a level view: 5 Q-limbs of a dnum-2 context keep alpha = 6, so one digit
+    lv = S.features(S.level_shape(prm, 4), 1 << 27)
+    assert lv[:3] == [15, 5, 1]
+    assert lv[4] == math.log2((5 + 6) * n8 / (1 << 27))
