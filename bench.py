@@ -7,7 +7,9 @@ through the C-ABI (ks_switch) on device-resident buffers. Each step uses the
 next (d, evk, out) set from a ring of distinct buffers larger than twice the L2
 cache, so every step reads its inputs from HBM.
 
-Default workload: plain KeySwitch (dnum, N, L) = (2, 2^15, 10). With --gpus N > 1
+Default workload: plain KeySwitch (dnum, N, L) = (4, 2^16, 35), the configuration
+the HBM-roofline target is stated on; --workload c1 / c2 selects (2, 2^13, 7) or
+(2, 2^15, 10). With --gpus N > 1
 (torchrun, one process per GPU) every rank runs an independent replica: the
 KeySwitches of different ranks share nothing ("replicas only", weak scaling).
 
@@ -35,35 +37,40 @@ METRIC = "KeySwitch/s per (dnum,N,L) on 1 GB300, % HBM roofline, selector regret
 UNIT = "KeySwitch/s"
 WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 
-# Integer-pipe peak used for the ALU roofline: 152 SMs x 64 32-bit IMAD lanes per SM
-# per clock x the maximum SM clock, divided by 10 IMADs per 64-bit Shoup modular
-# multiplication (one 64x64 high product ~4 IMAD + two 64-bit low products ~3 each).
-SMS, IMAD_PER_SM_CLK, IMAD_PER_MODOP = 152, 64, 10
-# DRAM bytes (read + write) per launch of the dominant kernel, from one cold-cache ncu
-# capture of the same kernel on the same workload (radix 8: 35.6864 MB read, 768 B
-# written; radix 4: 35.658752 MB read, 0 B written); keyed by (workload, plan,
-# kernel). Missing = not captured for the current kernel code and plan (null).
-NCU_TRAFFIC = {("c2", "DPOB", "modup_row_keymult"): 35687168,
-               ("c2", "DPOB-r4", "modup_row_keymult"): 35658752}
-# From the same captures: the busiest integer pipe (sm__pipe_fmaheavy_cycles_active, %
-# of peak) and the issue activity (smsp__issue_active, % of peak) of that launch.
-NCU_PIPES = {("c2", "DPOB", "modup_row_keymult"): {"fmaheavy_pct": 30.6, "issue_pct": 32.0},
-             ("c2", "DPOB-r4", "modup_row_keymult"): {"fmaheavy_pct": 37.6, "issue_pct": 43.9}}
+# Per-kernel DRAM bytes (read + write) per launch and the busiest integer pipe, from one
+# cold-cache ncu capture of every kernel of one KeySwitch of the workload (profile_case,
+# `--metrics dram__bytes_read.sum,dram__bytes_write.sum,...`); keyed by (workload,
+# kernel), with the plan the capture ran. Missing = not captured for the current kernels.
+NCU = {("c3", k): {"traffic": t, "plan": "DPOB", **pipes} for k, t, pipes in (
+    ("intt_row(d)", 57072640, {"issue_pct": 39.6, "alu_pct": 33.0, "fma_cycles_pct": 22.2}),
+    ("intt_col(d)", 19061760, {"issue_pct": 39.6, "alu_pct": 32.0, "fma_cycles_pct": 24.1}),
+    ("modup_col", 38981888, {"issue_pct": 59.5, "alu_pct": 47.8, "fma_cycles_pct": 36.2}),
+    ("modup_row_keymult", 360252416, {"issue_pct": 53.3, "alu_pct": 44.3, "fma_cycles_pct": 35.3}),
+    ("intt_row(accP)", 18875648, {"issue_pct": 41.0, "alu_pct": 36.4, "fma_cycles_pct": 22.2}),
+    ("intt_col(accP)", 9512192, {"issue_pct": 40.2, "alu_pct": 35.7, "fma_cycles_pct": 23.6}),
+    ("moddown_col", 9656064, {"issue_pct": 57.2, "alu_pct": 45.1, "fma_cycles_pct": 35.3}),
+    ("moddown_row", 129248512, {"issue_pct": 42.8, "alu_pct": 33.9, "fma_cycles_pct": 27.2}))}
 
 
-def measured_alu(ks, stream, dom, per_launch_ms):
-    """The dominant kernel against the measured ceiling of its own arithmetic: the
-    library's calibration kernels give butterflies/s and 128-bit multiply-accumulate
-    terms/s on this GPU with every SM busy and no memory traffic; the kernel's
-    operations at those rates take t_ceil, and frac = t_ceil / its event time."""
+def measured_alu(ks, stream):
+    """The library's measured arithmetic ceiling on this GPU: its own butterfly and
+    128-bit multiply-accumulate kernels at full occupancy with no memory traffic."""
     bf = max(ks.ks_calibrate(ks.KS_CAL_BUTTERFLY, 16384, stream) for _ in range(3))
     mac = max(ks.ks_calibrate(ks.KS_CAL_MAC, 4096, stream) for _ in range(3))
+    return bf, mac
+
+
+def alu_roofline(dom, per_launch_ms, bf, mac):
+    """A kernel against the measured ceiling of its own arithmetic. Its MAC terms are
+    converted to butterfly-equivalents at the measured rate ratio, so achieved / peak
+    = t_ceil / t with t_ceil = MACs / mac_rate + Shoup products / butterfly_rate."""
     n = dom["launches"]
     macs, shoup = dom["macs"] / n, (dom["ops"] - dom["macs"]) / n
     t_ceil_ms = (macs / mac + shoup / bf) * 1e3
-    return {"butterfly_per_s": bf, "mac_per_s": mac, "macs_per_launch": macs,
-            "shoup_per_launch": shoup, "t_ceil_ms": t_ceil_ms,
-            "frac": t_ceil_ms / per_launch_ms}
+    eq_ops = shoup + macs * bf / mac
+    return {"achieved": eq_ops / (per_launch_ms / 1e3) / 1e9, "peak": bf / 1e9,
+            "frac": t_ceil_ms / per_launch_ms, "t_ceil_ms": t_ceil_ms,
+            "macs_per_launch": macs, "shoup_per_launch": shoup}
 
 
 def parse():
@@ -72,7 +79,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
     ap.add_argument("--variant", default="tuned",
                     help="tuned (ks_tune picks), or DSOB/DPOB/DSOC/DPOC")
     ap.add_argument("--chunks", type=int, default=0)
@@ -115,12 +122,12 @@ def job_rate(world: int, units_per_rank: int, ms: float) -> float:
     return world * units_per_rank / (ms / 1e3)
 
 
-def workload_config(prm, variant_name, chunks, unfused, ring, ring_mb, l2_mb):
+def workload_config(prm):
+    """The workload, identical on both arms (the plan and the L2 protocol are reported
+    beside it, under "plan")."""
     return {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
             "N": prm.N, "L": prm.L, "alpha": prm.alpha, "beta": prm.beta, "QP": prm.QP,
-            "qbits": 50, "pbits": 60, "variant": variant_name + ("-unfused" if unfused else ""),
-            "chunks": chunks, "l2": f"ring of {ring} distinct (d, evk, out) sets, {ring_mb:.0f} MB"
-            f" > 2 x L2 ({l2_mb:.0f} MB): every step reads HBM"}
+            "qbits": 50, "pbits": 60}
 
 
 # ---------------------------------------------------------------------------
@@ -165,10 +172,8 @@ def run_reference(args, prm, rank: int, world: int):
             "n_gpus": world, "steps": reps, "warmup": warm, "ms_per_step": el / reps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
-                       "N": prm.N, "L": prm.L, "alpha": prm.alpha, "beta": prm.beta,
-                       "QP": prm.QP, "qbits": 50, "pbits": 60,
-                       "variant": "oracle (schoolbook, host cores)"},
+            "config": workload_config(prm),
+            "plan": {"variant": "oracle (schoolbook, host cores)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -290,6 +295,13 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
         sel, losses = S.train(data, tr)
         sel_info = S.evaluate(data, sel, te, tr)
         sel_info["train_final_loss"] = float(losses[-1])
+        # the regret judged on timings taken now, on this GPU: every plan re-timed on the
+        # 40 held-out points and their lower levels
+        live = S.sweep([data["points"][i] for i in te], reps=3, cands=S.ALL_PLANS, log=None)
+        sel_info["live"] = S.evaluate_live(live, sel, S.fixed_choice(data, tr))
+        sel_info["live"]["how"] = f"{len(te)} held-out points + {len(live['levels'])} lower-" \
+                                  f"level rows x {len(S.ALL_PLANS)} plans re-timed in this run " \
+                                  "(median of 3); network trained on the committed sweep"
         sel_info["sweep"] = f"{len(data['points'])} points (+ {len(data.get('levels', []))} " \
                             f"lower-level rows) x {len(data['cands'])} plans, {len(tr)} train / " \
                             f"{len(te)} held-out points"
@@ -341,6 +353,56 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
         out["selector_speedup_vs_best_fixed"] = sel_info["batch_value"] / plain[best_name]
     for c in ctxs.values():
         c.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The other plain workloads, (2, 2^13, 7) and (2, 2^15, 10): the tuned plan over a ring of
+# buffer sets larger than twice L2, device-resident, like the headline.
+
+def other_workloads(names, ks, torch, dev, stream, l2, steps):
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(99)
+
+    def rand_limbs(mods, lead, n):
+        t = torch.empty((*lead, len(mods), n), dtype=torch.int64, device=dev)
+        for i, m in enumerate(mods):
+            t[..., i, :] = torch.randint(0, m, (*lead, n), generator=gen, device=dev,
+                                         dtype=torch.int64)
+        return t.view(torch.uint64)
+
+    out = {}
+    for name in names:
+        prm = W.make_params(*WORKLOADS[name])
+        ctx = ks.Context(prm)
+        try:
+            evk = rand_limbs(prm.mods, (prm.beta, 2), prm.N)
+            d = rand_limbs(prm.q, (), prm.N)
+            set_bytes = (evk.numel() + 3 * d.numel()) * 8
+            ring = max(2, -(-2 * l2 // set_bytes) + 1)
+            sets = [(d.clone(), evk.clone(), torch.empty((2, prm.L + 1, prm.N),
+                                                         dtype=torch.uint64, device=dev))
+                    for _ in range(ring)]
+            v, c = ks.ks_tune(ctx.h, sets[0][0], sets[0][1], sets[0][2], 1, stream)
+            ws = torch.empty(ks.ks_workspace_size(ctx.h, v, c) // 8 + 1, dtype=torch.uint64,
+                             device=dev)
+            calls = [ks.prepare_switch(ctx.h, dd, ee, oo, v, c, ws, stream) for dd, ee, oo in sets]
+            for k in range(20):
+                calls[k % ring]()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(steps):
+                calls[k % ring]()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            out[name] = {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}",
+                         "plan": ks.variant_name(v, c), "value": 1e3 / ms, "unit": UNIT,
+                         "ms_per_step": ms, "steps": steps,
+                         "l2": f"ring of {ring} sets > 2 x L2"}
+        finally:
+            ctx.close()
     return out
 
 
@@ -527,6 +589,11 @@ def main():
 
     calls = [ks.prepare_switch(ctx.h, d, evk, out, variant, args.chunks, ws, stream)
              for d, evk, out in sets]
+    plan_info = {"variant": ks.variant_name(variant, args.chunks), "chunks": args.chunks,
+                 "chosen_by": "ks_tune (timed over dataflows x radices)"
+                 if args.variant.lower() == "tuned" else "--variant",
+                 "l2": f"ring of {ring} distinct (d, evk, out) sets, {ring * set_bytes / 1e6:.0f}"
+                       f" MB > 2 x L2 ({l2 / 1e6:.0f} MB): every step reads HBM"}
 
     def step(k):
         calls[k % ring]()
@@ -634,38 +701,73 @@ def main():
     peaks = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SMS * IMAD_PER_SM_CLK * sm_mhz * 1e6 / IMAD_PER_MODOP / 1e9  # Gmodop/s
+    sms = props.multi_processor_count
+    # Per-kernel durations: the profiling pass brackets every launch with events, which
+    # breaks the programmatic-dependent-launch overlap of consecutive kernels, so their
+    # sum exceeds the timed step; each kernel's event time is scaled by step / sum.
+    step_ms = el_ms / args.steps
+    ev_sum = sum(s["ms"] for s in stats) / kprof
+    scale = step_ms / ev_sum
     dom = max(stats, key=lambda s: s["ms"])
-    per_launch_ms = dom["ms"] / dom["launches"]
-    ops_l, bytes_l = dom["ops"] / dom["launches"], dom["bytes"] / dom["launches"]
-    alu_ach = ops_l / (per_launch_ms / 1e3) / 1e9
+    per_launch_ms = dom["ms"] / dom["launches"] * scale
+    bytes_l = dom["bytes"] / dom["launches"]
     hbm_ach = bytes_l / (per_launch_ms / 1e3) / 1e9
-    nkey = (args.workload, ks.variant_name(variant, args.chunks), dom["name"])
-    traffic = NCU_TRAFFIC.get(nkey)
-    roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu_ach, "peak": alu_peak,
-                "unit": "Gmodop/s", "frac": alu_ach / alu_peak, "traffic": traffic,
-                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_mhz:.0f}"
-                               f" MHz / {IMAD_PER_MODOP} IMAD per modop",
+    bf, mac = measured_alu(ks, stream)
+    alu = alu_roofline(dom, per_launch_ms, bf, mac)
+    # the recipe's unit counts for context: SMs x 64 IMAD lanes x max clock / 10 IMAD per
+    # 64-bit Shoup product
+    derived = sms * 64 * sm_mhz * 1e6 / 10 / 1e9
+    ncu = NCU.get((args.workload, dom["name"]))
+    roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu["achieved"],
+                "peak": alu["peak"], "unit": "Gop/s (butterfly-equivalent)",
+                "frac": alu["frac"], "traffic": ncu["traffic"] if ncu else None,
+                "peak_source": "measured in this run: ks_calibrate, the library's butterfly "
+                               f"({bf / 1e12:.3f} T/s) and 128-bit MAC ({mac / 1e12:.3f} T "
+                               f"terms/s) on all {sms} SMs; MAC terms counted at the ratio",
+                "t_ceil_ms": alu["t_ceil_ms"], "duration_ms": per_launch_ms,
+                "duration_source": f"event time x {scale:.3f} (step / sum of event-bracketed "
+                                   "launches)",
+                "share": dom["ms"] / sum(s["ms"] for s in stats),
+                "macs_per_launch": alu["macs_per_launch"],
+                "shoup_per_launch": alu["shoup_per_launch"],
                 "algo_bytes_per_launch": bytes_l, "hbm_achieved_gbs": hbm_ach,
                 "hbm_frac": hbm_ach / hbm,
-                "share": dom["ms"] / sum(s["ms"] for s in stats),
-                "ncu_pipes": NCU_PIPES.get(nkey)}
-    roofline["measured_alu"] = measured_alu(ks, stream, dom, per_launch_ms)
+                "derived_peak": {"value": derived, "unit": "Gmodop/s",
+                                 "source": f"{sms} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz / 10 IMAD"
+                                           " per modop"},
+                "ncu": ncu}
+    # the whole KeySwitch at the measured ceiling: every kernel's arithmetic
+    t_ceil_step = sum((s["macs"] / mac + (s["ops"] - s["macs"]) / bf) for s in stats) / kprof * 1e3
     algo = prm.algo_bytes()
     ks_gbs = algo * value / world / 1e9
+    kernels = []
+    for s_ in sorted(stats, key=lambda s: -s["ms"]):
+        n = s_["launches"]
+        t = s_["ms"] / n * scale
+        tc = (s_["macs"] / mac + (s_["ops"] - s_["macs"]) / bf) / n * 1e3
+        k = {"name": s_["name"], "launches_per_step": n / kprof, "ms_per_launch": round(t, 5),
+             "event_ms_per_launch": round(s_["ms"] / n, 5), "alu_frac": round(tc / t, 4),
+             "share": round(s_["ms"] / sum(x["ms"] for x in stats), 4)}
+        nc = NCU.get((args.workload, s_["name"]))
+        if nc:
+            k["dram_bytes"] = nc["traffic"]
+            k["algo_bytes"] = s_["bytes"] / n
+        kernels.append(k)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded uniform d, ternary keys, rounded-Gaussian errors)",
-        "config": workload_config(prm, ks.variant_name(variant, args.chunks), args.chunks,
-                                  False, ring, ring * set_bytes / 1e6, l2 / 1e6),
+        "config": workload_config(prm),
+        "plan": plan_info,
         "roofline": roofline,
+        "ks_alu_roofline": {"bound": "alu", "t_ceil_ms": t_ceil_step, "ms_per_step": step_ms,
+                            "frac": t_ceil_step / step_ms,
+                            "what": "the whole KeySwitch's arithmetic at the measured ceiling"},
         "ks_hbm_roofline": {"bound": "hbm", "achieved": ks_gbs, "peak": hbm, "unit": "GB/s",
                             "frac": ks_gbs / hbm, "algo_bytes_per_ks": algo,
                             "peak_source": peaks["source"]},
-        "kernels": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in s.items()}
-                    for s in sorted(stats, key=lambda s: -s["ms"])],
+        "kernels": kernels,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "host_us_per_step": host_us,
         "warm_l2_value": warm_value,
@@ -676,6 +778,9 @@ def main():
                 "sync_per_call_value": e2e_sync_value},
         "clocks": clocks,
     }
+    others = [w for w in ("c2", "c1") if w != args.workload]
+    line["other_workloads"] = other_workloads(others, ks, torch, dev, stream, l2,
+                                              max(100, min(args.steps, 2000)))
     if not args.no_batch:
         line["batch64"] = batch_measure(args, ks, torch, dev, stream, hbm)
     if not args.no_eval:

@@ -219,23 +219,27 @@ int ks_switch_host_async(ks_context *ctx, const uint64_t *d_host, const uint64_t
                          uint64_t *out_host, int variant, int chunks, void *stream);
 
 /* ks_switch without any device allocation, for callers that cannot allocate device
- * memory when they switch keys: code running while a CUDA graph is captured
- * (cudaMalloc cannot be captured), callers held to a fixed allocator or memory-pool
- * budget, and real-time integrations that must not call the allocator after
- * start-up. The paper has no counterpart; this is a deployment variant of
- * ks_switch (same arguments, same result bits).
+ * memory when they switch keys: callers held to a fixed allocator or memory-pool
+ * budget that forbids new device allocations, and real-time or embedded integrations
+ * that must not call the allocator (which can block and synchronize the device) after
+ * start-up. The paper has no counterpart; this is a deployment variant of ks_switch
+ * (same arguments, same result bits).
  *   Scratch: a static device array of ks_noalloc_scratch_bytes() bytes (128 MiB) in
  *   this library; every GPU that loads it holds it until the process exits. The
  *   caller still passes the inputs and the output.
  *   Limit: if ks_workspace_size(ctx, variant, chunks) exceeds that size, returns
  *   KS_EINVAL and launches nothing (e.g. (4,2^16,35) fits with KS_DSOC and
  *   chunks >= 4, not with KS_DPOB).
+ *   Device: the current device must be the context's (else KS_EINVAL).
  *   Set-up: the first call on a device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current) and keeps it for the life of the process; make that first
+ *   call before any stream capture. A device reset (cudaDeviceReset) is not supported.
  *   Sharing: every call uses the same array and leaves its contents behind; no part
  *   of it needs to start at zero. Calls that overlap on the GPU (other streams,
  *   other threads) race on it: order them, e.g. on one stream.
- *   Calls no cudaMalloc, cudaFree or other allocating routine. */
+ *   Launches the KeySwitch kernels directly on `stream` at every size (no graph cache
+ *   and no context arena), and calls no cudaMalloc, cudaFree or other allocating
+ *   routine. */
 size_t ks_noalloc_scratch_bytes(void);
 int ks_switch_noalloc(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev,
                       uint64_t *out_dev, int variant, int chunks, void *stream);

@@ -840,6 +840,29 @@ int ks_switch(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *o
 
 }  // extern "C"
 
+namespace ks {
+
+// ks_switch on a caller workspace with every kernel launched directly on `stream`: no
+// graph cache (no capture, instantiation or stream creation) and no context arena.
+int switch_launch_only(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out,
+                       int variant, int chunks, void *ws, size_t ws_bytes, void *stream) {
+  if (!c || !d || !evk || !out || !ws) return KS_EINVAL;
+  if (!aligned16(d) || !aligned16(evk) || !aligned16(out) || !aligned16(ws)) return KS_EALIGN;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
+  if (rc) return rc;
+  if (ws_bytes < pl.total * 8) return KS_EINVAL;
+  JobSet js = {};
+  js.n = 1;
+  js.j[0].d = (const u64 *)d;
+  js.j[0].evk = (const u64 *)evk;
+  js.j[0].out = (u64 *)out;
+  js.j[0].ws = (u64 *)ws;
+  return run_plan(c, pl, js, (cudaStream_t)stream);
+}
+
+}  // namespace ks
+
 namespace {
 
 // ks_switch_host / ks_switch_host_async. `async`: pinned buffers only, no final

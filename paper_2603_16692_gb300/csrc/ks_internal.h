@@ -205,6 +205,10 @@ struct LaunchTable {
   cudaError_t (*ntt_row)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
                          int buf, cudaStream_t);
 };
+// ks_switch on the caller's workspace `ws` (ws_bytes >= ks_workspace_size) that only
+// launches kernels on `stream`: no graph cache, no arena (ks_api.cu).
+int switch_launch_only(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out,
+                       int variant, int chunks, void *ws, size_t ws_bytes, void *stream);
 // True when ctx's selected plan came from the selector installed now (ks_select.cu).
 bool selected_current(const ks_context *c);
 

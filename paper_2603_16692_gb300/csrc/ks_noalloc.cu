@@ -1,13 +1,13 @@
 // ks_switch_noalloc: a KeySwitch whose scratch memory is a fixed, file-scope
 // device array instead of memory the caller or the library allocates.
 //
-// Some callers cannot allocate device memory at the time they switch keys: code
-// running while a CUDA graph is being captured (cudaMalloc is not capturable),
-// callers inside a memory-pool or allocator budget that forbids new device
-// allocations, and real-time or embedded integrations that must not touch the
-// allocator after start-up. For them this entry point uses a static scratch of
-// kScratchBytes, which every GPU that loads this module holds until the process
-// exits.
+// Some callers cannot allocate device memory at the time they switch keys: callers
+// held to a memory-pool or allocator budget that forbids new device allocations
+// once the budget is reached, and real-time or embedded integrations that must not
+// touch the allocator (whose calls can block and synchronize the device) after
+// start-up. For them this entry point uses a static scratch of kScratchBytes, which
+// every GPU that loads this module holds until the process exits, and only launches
+// kernels: no graph cache, no context arena.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,14 +27,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per device
-// with that device current.
-int scratch_address(void **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return KS_ECUDA;
-  }
+// Device address of the scratch on device `dev`, looked up once per device with that
+// device current (the caller has checked that it is). The address is cached for the
+// life of the process: a device reset (cudaDeviceReset) is not supported with this
+// entry point.
+int scratch_address(int dev, void **out) {
+  if (dev < 0 || dev >= kMaxDevices) return KS_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
     void *p = nullptr;
@@ -61,11 +59,18 @@ int ks_switch_noalloc(ks_context *ctx, const uint64_t *d_dev, const uint64_t *ev
   int rc = ks_workspace_size(ctx, variant, chunks, &need);
   if (rc) return rc;
   if (need > kScratchBytes) return KS_EINVAL;  // does not fit the static scratch
+  // The scratch address belongs to the current device: it must be the context's.
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return KS_ECUDA;
+  }
+  if (dev != ctx->device) return KS_EINVAL;
   void *scratch = nullptr;
-  rc = scratch_address(&scratch);
+  rc = scratch_address(dev, &scratch);
   if (rc) return rc;
-  // A caller workspace makes ks_switch launch kernels only; it never allocates.
-  return ks_switch(ctx, d_dev, evk_dev, out_dev, variant, chunks, scratch, kScratchBytes, stream);
+  return ks::switch_launch_only(ctx, d_dev, evk_dev, out_dev, variant, chunks, scratch,
+                                kScratchBytes, stream);
 }
 
 }  // extern "C"

@@ -1,7 +1,9 @@
 """ks_switch_noalloc, the entry point for callers that cannot allocate device memory
-(e.g. while a CUDA graph is being captured, or under a fixed memory budget): its
-scratch is a static device array in the library. Its output must equal ks_switch's
-on two calls in a row (the second call sees the first call's leftover scratch).
+when they switch keys (a fixed allocator or memory-pool budget, or a real-time
+integration that must not call the allocator after start-up): its scratch is a
+static device array in the library. Its output must equal ks_switch's on two calls
+in a row (the second call sees the first call's leftover scratch), at every size,
+including the single-pass sizes N <= 2^12 for which ks_switch replays cached graphs.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
@@ -22,7 +24,9 @@ def _dev(a):
 
 
 @pytest.mark.parametrize("cfg,variant,chunks", [(W.C2, ks.KS_DPOB, 0), (W.C3, ks.KS_DSOC, 4),
-                                                (W.C1, ks.KS_DPOC | ks.KS_UNFUSED, 3)])
+                                                (W.C1, ks.KS_DPOC | ks.KS_UNFUSED, 3),
+                                                ((2, 12, 5), ks.KS_DPOB, 0),
+                                                ((3, 11, 8), ks.KS_DSOC, 2)])
 def test_noalloc_equals_ks_switch_two_calls(cfg, variant, chunks):
     import torch
     prm = W.make_params(*cfg)
@@ -32,10 +36,14 @@ def test_noalloc_equals_ks_switch_two_calls(cfg, variant, chunks):
         evk = ctx.keygen(_dev(s_from), _dev(s_to), _dev(a), _dev(e))
         lib = ks.load()
         stream = torch.cuda.current_stream().cuda_stream
+        # the same output buffer on both calls (a repeated call with the same buffers
+        # is the case ks_switch hands to its graph cache at N <= 2^12)
+        got = torch.full((2, prm.L + 1, prm.N), 7, dtype=torch.uint64, device="cuda")
+        d = torch.empty((prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
         for call, seed in enumerate((11, 12)):
-            d = _dev(W.gen_input(prm, seed))
+            d.copy_(_dev(W.gen_input(prm, seed)))
             want = ctx.switch(d, evk, variant=variant, chunks=chunks)
-            got = torch.full((2, prm.L + 1, prm.N), 7, dtype=torch.uint64, device="cuda")
+            got.fill_(7)
             rc = lib.ks_switch_noalloc(ctx.h, d.data_ptr(), evk.data_ptr(), got.data_ptr(),
                                        variant, chunks, stream)
             assert rc == ks.KS_OK, ks.strerror(rc)
