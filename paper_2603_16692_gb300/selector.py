@@ -105,6 +105,12 @@ def footprint_rule(prm, l2: int) -> int:
     return order[-1]
 
 
+def threshold_rule(prm, l2: int = 0) -> int:
+    """A one-line rule read off the GB300 sweep: DPOB with radix-4 rounds up to
+    N = 2^15, DPOB with radix-8 rounds above (the baseline the network must beat)."""
+    return 2 if prm.N <= 1 << 15 else 0
+
+
 def columns(data: dict) -> list:
     """Indices of the candidate plans among the sweep's measured plans."""
     return [data["cands"].index(n) for n, _, _ in CANDS]
@@ -292,33 +298,58 @@ def train(data: dict, idx, steps: int = 4000, lr: float = 3e-3, seed: int = 0):
     return sel, loss.cpu().numpy()
 
 
-def evaluate(data: dict, sel: Selector, test_idx, train_idx) -> dict:
-    """Regret t(chosen)/t(best) - 1 on the held-out points test_idx, the best being the
-    exhaustive minimum over every measured plan, for the MLP, the best single fixed
-    candidate (chosen on the training rows) and the paper's footprint rule; the same
-    over the held-out points' lower levels under "levels" (if the sweep has them)."""
+def fixed_choice(data: dict, train_idx) -> int:
+    """The best single fixed candidate on the training rows (least total time)."""
     _, tr_times = shapes_and_times(data, train_idx)
+    return int(np.argmin(tr_times[:, columns(data)].sum(0)))
+
+
+def score(sel: Selector, shapes, times, cols, fixed: int, l2: int) -> dict:
+    """Regret t(chosen)/t(best) - 1 per row, the best being the exhaustive minimum over
+    every measured plan (times[rows][plans]; cols = the candidates' columns), for the
+    MLP, the fixed candidate, the paper's footprint rule and the one-line threshold
+    rule."""
+    times = np.asarray(times, dtype=np.float64)
+    best = times.min(1)
+    ms = times[:, cols]
+    res = {}
+    for name, ch in (("mlp", sel.choose(shapes)),
+                     ("fixed_" + CANDS[fixed][0], [fixed] * len(shapes)),
+                     ("footprint_rule", [footprint_rule(p, l2) for p in shapes]),
+                     ("threshold_rule", [threshold_rule(p) for p in shapes])):
+        r = np.array([ms[i, c] / best[i] - 1 for i, c in enumerate(ch)])
+        res[name] = {"mean_regret": float(r.mean()), "max_regret": float(r.max()),
+                     "total_ms": float(sum(ms[i, c] for i, c in enumerate(ch)))}
+    res["exhaustive_total_ms"] = float(best.sum())
+    return res
+
+
+def evaluate(data: dict, sel: Selector, test_idx, train_idx) -> dict:
+    """Regret on the held-out points test_idx of the sweep `data` (and, under "levels",
+    on their lower levels if the sweep has them); see score()."""
+    fixed = fixed_choice(data, train_idx)
     cols = columns(data)
-    fixed = int(np.argmin(tr_times[:, cols].sum(0)))
-
-    def score(shapes, times):
-        best = times.min(1)
-        ms = times[:, cols]
-        choice_mlp = sel.choose(shapes)
-        res = {}
-        for name, ch in (("mlp", choice_mlp), ("fixed_" + CANDS[fixed][0], [fixed] * len(shapes)),
-                         ("footprint_rule", [footprint_rule(p, data["l2"]) for p in shapes])):
-            r = np.array([ms[i, c] / best[i] - 1 for i, c in enumerate(ch)])
-            res[name] = {"mean_regret": float(r.mean()), "max_regret": float(r.max()),
-                         "total_ms": float(sum(ms[i, c] for i, c in enumerate(ch)))}
-        res["exhaustive_total_ms"] = float(best.sum())
-        return res
-
     top = [W.make_params(*data["points"][i]) for i in test_idx]
-    out = score(top, np.array([data["ms"][i] for i in test_idx], dtype=np.float64))
+    out = score(sel, top, [data["ms"][i] for i in test_idx], cols, fixed, data["l2"])
     shapes, times = shapes_and_times(data, test_idx)
     if len(shapes) > len(top):
-        out["levels"] = dict(score(shapes[len(top):], times[len(top):]), rows=len(shapes) - len(top))
+        out["levels"] = dict(score(sel, shapes[len(top):], times[len(top):], cols, fixed,
+                                   data["l2"]), rows=len(shapes) - len(top))
+    return out
+
+
+def evaluate_live(live: dict, sel: Selector, fixed: int) -> dict:
+    """Regret judged on a sweep `live` re-timed now (every plan of ALL_PLANS on the
+    held-out points and their lower levels), with the network and the fixed candidate
+    chosen from the training sweep."""
+    idx = list(range(len(live["points"])))
+    cols = columns(live)
+    top = [W.make_params(*p) for p in live["points"]]
+    out = score(sel, top, live["ms"], cols, fixed, live["l2"])
+    shapes, times = shapes_and_times(live, idx)
+    if len(shapes) > len(top):
+        out["levels"] = dict(score(sel, shapes[len(top):], times[len(top):], cols, fixed,
+                                   live["l2"]), rows=len(shapes) - len(top))
     return out
 
 

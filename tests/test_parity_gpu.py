@@ -81,6 +81,53 @@ def test_c3_every_variant(seed):
     check(W.C3, seed, vs, chunk_list=chunks)
 
 
+RADIX_PLANS = [ks.KS_DPOB, ks.KS_DSOB, ks.KS_DPOC]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("cfg", [W.C2, W.C3])
+@pytest.mark.parametrize("radix", [ks.KS_RADIX4, ks.KS_RADIX16])
+def test_plain_workloads_radix4_and_radix16(cfg, seed, radix):
+    """The radix-4 and radix-16 register rounds (the tuner's other radix schedules) at the
+    full (2,2^15,10) and (4,2^16,35) sizes: DPOB, DSOB and DPOC with 2 chunks."""
+    check(cfg, seed, [v | radix for v in RADIX_PLANS], chunk_list=(2,))
+
+
+@pytest.mark.parametrize("radix", [0, ks.KS_RADIX4, ks.KS_RADIX16])
+@pytest.mark.parametrize("cfg", [W.C2, W.C3])
+def test_host_entry_points_with_each_radix(cfg, radix):
+    """ks_switch_host and ks_switch_host_async (pinned buffers: the input iNTT reads the
+    host input over the CPU-GPU link, the last kernel writes the host output) with the
+    DPOB plan of each radix, over a ring of three host buffers and three calls each."""
+    import torch
+    prm = W.make_params(*cfg)
+    cases = [oracle_case(cfg, seed) for seed in (0, 1, 2)]
+    evk_o = cases[0][6]
+    ctx = ks.Context(prm)
+    try:
+        evk = dev(evk_o)
+        v = ks.KS_DPOB | radix
+        d_hs = [torch.from_numpy(c[5].copy()).pin_memory() for c in cases]
+        # one key for the three inputs: seed 0's; the oracle switches the inputs of seeds
+        # 1 and 2 under that key
+        from oracle import oracle as O
+        want = [cases[0][7]] + [O.keyswitch(prm, c[5], evk_o) for c in cases[1:]]
+        outs = [torch.full((2, prm.L + 1, prm.N), 3, dtype=torch.uint64).pin_memory()
+                for _ in cases]
+        for k in range(3):
+            ks.ks_switch_host(ctx.h, d_hs[k], evk, outs[k], v, 0)
+            assert np.array_equal(outs[k].numpy(), want[k]), f"sync call {k}"
+        for o in outs:
+            o.fill_(3)
+        for k in range(3):
+            ks.ks_switch_host_async(ctx.h, d_hs[k], evk, outs[k], v, 0)
+        torch.cuda.synchronize()
+        for k in range(3):
+            assert np.array_equal(outs[k].numpy(), want[k]), f"async call {k}"
+    finally:
+        ctx.close()
+
+
 def test_host_entry_point_and_workspace():
     import torch
     prm, s_from, s_to, a, e, d, evk_o, out_o = oracle_case(W.C2, 0)

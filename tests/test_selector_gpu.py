@@ -100,11 +100,16 @@ def test_selector_gain_on_held_out_points():
     assert mlp < ev["footprint_rule"]["mean_regret"], ev
     assert ev["mlp"]["total_ms"] < ev[fixed]["total_ms"], ev
     assert mlp <= 0.05, ev
-    # the held-out points' lower levels (level views): the network picks per level
+    # the one-line rule (radix 4 up to N = 2^15, DPOB throughout) is within a few percent
+    # of exhaustive on top-level points; the network must stay close to it there
+    assert mlp <= ev["threshold_rule"]["mean_regret"] + 0.01, ev
+    # the held-out points' lower levels (level views): the network picks per level, where
+    # the rule misses (few digits, small L) and the network must beat it
     if "levels" in ev:
         lv = ev["levels"]
         assert lv["mlp"]["mean_regret"] < lv[fixed]["mean_regret"], lv
         assert lv["mlp"]["total_ms"] < lv[fixed]["total_ms"], lv
+        assert lv["mlp"]["mean_regret"] < lv["threshold_rule"]["mean_regret"], lv
         assert lv["mlp"]["mean_regret"] <= 0.05, lv
 
 
