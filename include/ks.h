@@ -63,6 +63,25 @@ extern "C" {
 /* OR-ed into the variant: register rounds of radix 16 (16 points per thread, half the
  * threads per tile): fewer shared-memory round trips for large workloads. */
 #define KS_RADIX16 0x400
+/* Radix schedule, OR-ed into the variant: the register-round radix of one kernel stage,
+ * overriding the plan's for that stage only. Stages: KS_ST_INV (the input iNTT and the
+ * iNTT of the accumulators' P-limbs), KS_ST_UPC (ModUp BConv + first NTT pass),
+ * KS_ST_KM (second NTT pass + key multiply), KS_ST_DNC (ModDown BConv + first NTT
+ * pass), KS_ST_DNR (second NTT pass + P^{-1} scaling). Radix codes: KS_R4, KS_R8,
+ * KS_R16. Every schedule computes the same bits. */
+#define KS_STAGE_SHIFT 16
+#define KS_ST_INV 0
+#define KS_ST_UPC 1
+#define KS_ST_KM 2
+#define KS_ST_DNC 3
+#define KS_ST_DNR 4
+#define KS_R4 1
+#define KS_R8 2
+#define KS_R16 3
+#define KS_STAGE_RADIX(stage, code) ((code) << (KS_STAGE_SHIFT + 2 * (stage)))
+/* OR-ed into the variant: the column passes (N >= 2^13) use the alternative column tile
+ * (2^11 points instead of 2^10 up to N = 2^15, 2^10 instead of 2^11 above). */
+#define KS_COLTILE_ALT 0x4000000
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -147,7 +166,8 @@ int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *by
  *   d_dev   [L+1][N]            input, NTT form
  *   evk_dev [beta][2][QP][N]    keys from ks_keygen (or any canonical keys)
  *   out_dev [2][L+1][N]         output pair, NTT form; must not alias the inputs
- *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16), or KS_AUTO (the
+ *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | a radix schedule
+ *           KS_STAGE_RADIX(..) | KS_COLTILE_ALT), or KS_AUTO (the
  *           plan ks_tune chose for this context, else the one ks_select chose, else
  *           DPOB fused radix 8)
  *   chunks  1..64 output groups for the OC variants (0 = 2; the paper searches 2..10);
@@ -290,8 +310,11 @@ int ks_batch_status(void *stream);
 
 /* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
  * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one
- * launch set) and stores the fastest as the context's KS_AUTO plan. Writes the switched result to
- * out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
+ * launch set); then, for N >= 2^13, refines the winner's schedule one coordinate at a
+ * time: each stage's radix (KS_STAGE_RADIX) and the column tile (KS_COLTILE_ALT), a
+ * change kept when the KeySwitch gets more than 1% faster. Stores the result as the
+ * context's KS_AUTO plan and writes it to *variant / *chunks. Writes the switched
+ * result to out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
 int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,
             int batch, int *variant, int *chunks, void *stream);
 

@@ -25,10 +25,16 @@ using namespace ks;
 
 namespace {
 
+// Kernel stages whose register-round radix a schedule sets separately.
+enum { ST_INV = 0, ST_UPC = 1, ST_KM = 2, ST_DNC = 3, ST_DNR = 4, ST_COUNT = 5 };
+
 struct Plan {
   int base;      // KS_DSOB..KS_DPOC
   bool unfused;
-  int rl;        // register-round radix: 3 (8 points per thread) or 2 (4 points)
+  int rl;        // register-round radix of the plan: 3 (8 points per thread), 2 or 4
+  int srl[ST_COUNT];  // per stage (the plan's unless the variant's schedule sets one)
+  int ca;        // 1: alternative column tile
+  int code;      // every variant bit that changes the launches (graph-cache key)
   int chunks;    // phase-1 and phase-2 group counts (1 for OB)
   int clen;      // max QP-limbs per phase-1 group
   int clq;       // max Q-limbs per phase-2 group
@@ -38,8 +44,11 @@ struct Plan {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
+constexpr int kSchedMask = 0x3ff << KS_STAGE_SHIFT;
+
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
-  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16)) return KS_EINVAL;
+  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT))
+    return KS_EINVAL;
   if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
     // the tuned choice for single KeySwitches, else the selector's, else DPOB radix 8
@@ -65,6 +74,12 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   pl->base = base;
   pl->unfused = (variant & KS_UNFUSED) != 0;
   pl->rl = (variant & KS_RADIX4) ? 2 : (variant & KS_RADIX16) ? 4 : 3;
+  for (int st = 0; st < ST_COUNT; ++st) {
+    const int code = (variant >> (KS_STAGE_SHIFT + 2 * st)) & 3;  // 0: the plan's radix
+    pl->srl[st] = code == 0 ? pl->rl : code + 1;
+  }
+  pl->ca = (variant & KS_COLTILE_ALT) ? 1 : 0;
+  pl->code = variant & ~0xff;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
   pl->clq = (c->nq + chunks - 1) / chunks;
@@ -158,7 +173,9 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
   const double BF_B = (double)N / 2 * c->logb * J;       // butterflies, row pass
   const double NJ = (double)N * J;
   const bool single = c->loga == 0;
-  const LaunchTable &L = pl.rl == 2 ? *c->lt4 : pl.rl == 4 ? *c->lt16 : *c->lt;
+  auto stage = [&](int st) -> const LaunchTable & { return *c->ltab[pl.srl[st] - 2][pl.ca]; };
+  const LaunchTable &L = stage(ST_INV), &LU = stage(ST_UPC), &LK = stage(ST_KM),
+                    &LDC = stage(ST_DNC), &LDR = stage(ST_DNR);
   WsOff wo;
   wo.v = (long long)pl.off_v;
   wo.tmp = (long long)pl.off_tmp;
@@ -213,15 +230,15 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
       if (!pl.unfused) {
         if (!single)
           KS_TRY(timed("modup_col", nconv * W + src_b, conv_ops + nconv * BF_A, conv_ops, s,
-                       [&] { return L.modup_col(c, js, wo, up, s); }));
+                       [&] { return LU.modup_col(c, js, wo, up, s); }));
       } else {
         KS_TRY(timed("bconv_up", nconv * W + src_b, conv_ops, conv_ops, s,
                      [&] { return launch_bconv_up(c, js, wo, up, nconv, s); }));
         if (!single)
           KS_TRY(timed("ntt_col", 2 * nconv * W, nconv * BF_A, 0, s,
-                       [&] { return L.ntt_col(c, js, wo, up, BUF_TMP, s); }));
+                       [&] { return LU.ntt_col(c, js, wo, up, BUF_TMP, s); }));
         KS_TRY(timed("ntt_row", 2 * nconv * W, nconv * BF_B, 0, s,
-                     [&] { return L.ntt_row(c, js, wo, up, BUF_TMP, s); }));
+                     [&] { return LU.ntt_row(c, js, wo, up, BUF_TMP, s); }));
       }
       // key multiply: evk 2 words per (digit, target); ext from tmp (or d on own limbs);
       // acc written (and read when accumulating over digit launches)
@@ -232,7 +249,7 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
         const double o = km_ops + nconv * BF_B + (single ? conv_ops : 0);
         const double m = km_ops + (single ? conv_ops : 0);
         KS_TRY(timed("modup_row_keymult", b, o, m, s,
-                     [&] { return L.modup_row(c, js, wo, tg, s); }));
+                     [&] { return LK.modup_row(c, js, wo, tg, s); }));
       } else {
         KS_TRY(timed("keymult", km_bytes, km_ops, km_ops, s,
                      [&] { return launch_keymult(c, js, wo, tg, s); }));
@@ -266,19 +283,19 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
     if (!pl.unfused) {
       if (!single)
         KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s,
-                     [&] { return L.moddown_col(c, js, wo, dn, s); }));
+                     [&] { return LDC.moddown_col(c, js, wo, dn, s); }));
       const double b = 3 * n * W + (single ? vp_b - n * W : 0);
       const double o = n * (BF_B + NJ) + (single ? conv : 0);
       KS_TRY(timed("moddown_row", b, o, single ? conv : 0, s,
-                   [&] { return L.moddown_row(c, js, wo, d1, s); }));
+                   [&] { return LDR.moddown_row(c, js, wo, d1, s); }));
     } else {
       KS_TRY(timed("bconv_down", n * W + vp_b, conv, conv, s,
                    [&] { return launch_bconv_down(c, js, wo, dn, (int)n, s); }));
       if (!single)
         KS_TRY(timed("ntt_col", 2 * n * W, n * BF_A, 0, s,
-                     [&] { return L.ntt_col(c, js, wo, dn, BUF_TMP2, s); }));
+                     [&] { return LDC.ntt_col(c, js, wo, dn, BUF_TMP2, s); }));
       KS_TRY(timed("ntt_row", 2 * n * W, n * BF_B, 0, s,
-                   [&] { return L.ntt_row(c, js, wo, dn, BUF_TMP2, s); }));
+                   [&] { return LDR.ntt_row(c, js, wo, dn, BUF_TMP2, s); }));
       KS_TRY(timed("moddown_scale", 3 * n * W, n * NJ, 0, s,
                    [&] { return launch_moddown_scale(c, js, wo, dn, (int)n, s); }));
     }
@@ -416,15 +433,17 @@ int create_context(int dnum, int logn, int L, const u64 *q, const u64 *p, int al
   c->loga = ks::geo_loga(logn);
   c->logb = logn - c->loga;
   c->loggr = ks::geo_loggr(logn);
-  c->lt = ks::launch_table(logn, 3);
-  c->lt4 = ks::launch_table(logn, 2);
-  c->lt16 = ks::launch_table(logn, 4);
-  if (!c->lt || !c->lt4 || !c->lt16 || c->lt->prepare() != cudaSuccess ||
-      c->lt4->prepare() != cudaSuccess || c->lt16->prepare() != cudaSuccess) {
-    cudaGetLastError();
-    delete c;
-    return KS_ECUDA;
-  }
+  for (int r = 0; r < 3; ++r)
+    for (int ca = 0; ca < 2; ++ca) {
+      const LaunchTable *t = ks::launch_table(logn, r + 2, ca);
+      if (!t || t->prepare() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return KS_ECUDA;
+      }
+      c->ltab[r][ca] = t;
+    }
+  c->lt = c->ltab[1][0];
   c->mods = mods;
   // basis-conversion sums: run * max_source * m < m 2^64
   c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
@@ -566,7 +585,7 @@ int cached_launch(ks_context *c, const std::array<uintptr_t, 10> &key, cudaStrea
   return cuda_rc(cudaGraphLaunch(exec, s));
 }
 
-int plan_code(const Plan &pl) { return pl.base | (pl.rl << 8) | (pl.unfused ? 1 << 12 : 0); }
+int plan_code(const Plan &pl) { return pl.base | pl.code; }
 
 // Galois elements are odd residues k in [1, 2N).
 bool galois_ok(const ks_context *c, uint32_t k) {
@@ -1254,36 +1273,67 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
   cudaEventCreate(&e1);
   const bool prof = g_prof.on;
   g_prof.on = false;
+  int rc = KS_OK;
+  // best of three timed launch sets (after one untimed) of plan (v, ch), ms
+  auto time_plan = [&](int v, int ch) -> float {
+    Plan pl;
+    if (make_plan(c, v, ch, &pl) != KS_OK) return 1e30f;
+    JobSet js = {};
+    js.n = batch;
+    for (int q = 0; q < batch; ++q) {
+      char *base = (char *)mem + q * (ws_max + out_b);
+      js.j[q].d = (const u64 *)d;
+      js.j[q].evk = (const u64 *)evk;
+      js.j[q].out = (u64 *)(base + ws_max);
+      js.j[q].ws = (u64 *)base;
+    }
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 4 && rc == KS_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = run_plan(c, pl, js, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = KS_ECUDA;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_min = std::min(ms_min, ms);
+    }
+    return ms_min;
+  };
+  // 1) dataflow x radix
   float best = 1e30f;
-  int best_v = KS_DPOB, best_c = 0, rc = KS_OK;
-  for (auto &b : bases) {
+  int best_v = KS_DPOB, best_c = 0;
+  for (auto &b : bases)
     for (int ri = 0; ri < 3 && rc == KS_OK; ++ri) {
       const int v = b[0] | radix[ri];
-      Plan pl;
-      if (make_plan(c, v, b[1], &pl) != KS_OK) continue;
-      JobSet js = {};
-      js.n = batch;
-      for (int q = 0; q < batch; ++q) {
-        char *base = (char *)mem + q * (ws_max + out_b);
-        js.j[q].d = (const u64 *)d;
-        js.j[q].evk = (const u64 *)evk;
-        js.j[q].out = (u64 *)(base + ws_max);
-        js.j[q].ws = (u64 *)base;
-      }
-      float ms_min = 1e30f;
-      for (int rep = 0; rep < 4 && rc == KS_OK; ++rep) {
-        cudaEventRecord(e0, s);
-        rc = run_plan(c, pl, js, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = KS_ECUDA;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) ms_min = std::min(ms_min, ms);
-      }
-      if (ms_min < best) {
-        best = ms_min;
+      const float ms = time_plan(v, b[1]);
+      if (ms < best) {
+        best = ms;
         best_v = v;
         best_c = b[1];
+      }
+    }
+  // 2) the schedule of the winner, one coordinate at a time: each stage's radix, then
+  // the column tile (a change is kept only if the whole KeySwitch gets faster by more
+  // than the timing noise, 1%)
+  if (rc == KS_OK && c->loga > 0) {
+    const int plan_code3 = (best_v & KS_RADIX4) ? KS_R4 : (best_v & KS_RADIX16) ? KS_R16 : KS_R8;
+    for (int st = 0; st < ST_COUNT && rc == KS_OK; ++st)
+      for (int code = KS_R4; code <= KS_R16 && rc == KS_OK; ++code) {
+        if (code == plan_code3) continue;
+        const int cur = (best_v >> (KS_STAGE_SHIFT + 2 * st)) & 3;
+        if (cur == code) continue;
+        const int v = (best_v & ~KS_STAGE_RADIX(st, 3)) | KS_STAGE_RADIX(st, code);
+        const float ms = time_plan(v, best_c);
+        if (ms < 0.99f * best) {
+          best = ms;
+          best_v = v;
+        }
+      }
+    if (rc == KS_OK) {
+      const float ms = time_plan(best_v ^ KS_COLTILE_ALT, best_c);
+      if (ms < 0.99f * best) {
+        best = ms;
+        best_v ^= KS_COLTILE_ALT;
       }
     }
   }

@@ -5,113 +5,107 @@
 #include "ks_internal.h"
 
 namespace ks {
-const LaunchTable &launch_table_1_3();
-const LaunchTable &launch_table_1_2();
-const LaunchTable &launch_table_1_4();
-const LaunchTable &launch_table_2_3();
-const LaunchTable &launch_table_2_2();
-const LaunchTable &launch_table_2_4();
-const LaunchTable &launch_table_3_3();
-const LaunchTable &launch_table_3_2();
-const LaunchTable &launch_table_3_4();
-const LaunchTable &launch_table_4_3();
-const LaunchTable &launch_table_4_2();
-const LaunchTable &launch_table_4_4();
-const LaunchTable &launch_table_5_3();
-const LaunchTable &launch_table_5_2();
-const LaunchTable &launch_table_5_4();
-const LaunchTable &launch_table_6_3();
-const LaunchTable &launch_table_6_2();
-const LaunchTable &launch_table_6_4();
-const LaunchTable &launch_table_7_3();
-const LaunchTable &launch_table_7_2();
-const LaunchTable &launch_table_7_4();
-const LaunchTable &launch_table_8_3();
-const LaunchTable &launch_table_8_2();
-const LaunchTable &launch_table_8_4();
-const LaunchTable &launch_table_9_3();
-const LaunchTable &launch_table_9_2();
-const LaunchTable &launch_table_9_4();
-const LaunchTable &launch_table_10_3();
-const LaunchTable &launch_table_10_2();
-const LaunchTable &launch_table_10_4();
-const LaunchTable &launch_table_11_3();
-const LaunchTable &launch_table_11_2();
-const LaunchTable &launch_table_11_4();
-const LaunchTable &launch_table_12_3();
-const LaunchTable &launch_table_12_2();
-const LaunchTable &launch_table_12_4();
-const LaunchTable &launch_table_13_3();
-const LaunchTable &launch_table_13_2();
-const LaunchTable &launch_table_13_4();
-const LaunchTable &launch_table_14_3();
-const LaunchTable &launch_table_14_2();
-const LaunchTable &launch_table_14_4();
-const LaunchTable &launch_table_15_3();
-const LaunchTable &launch_table_15_2();
-const LaunchTable &launch_table_15_4();
-const LaunchTable &launch_table_16_3();
-const LaunchTable &launch_table_16_2();
-const LaunchTable &launch_table_16_4();
-const LaunchTable &launch_table_17_3();
-const LaunchTable &launch_table_17_2();
-const LaunchTable &launch_table_17_4();
+const LaunchTable &launch_table_1_3_0();
+const LaunchTable &launch_table_1_2_0();
+const LaunchTable &launch_table_1_4_0();
+const LaunchTable &launch_table_2_3_0();
+const LaunchTable &launch_table_2_2_0();
+const LaunchTable &launch_table_2_4_0();
+const LaunchTable &launch_table_3_3_0();
+const LaunchTable &launch_table_3_2_0();
+const LaunchTable &launch_table_3_4_0();
+const LaunchTable &launch_table_4_3_0();
+const LaunchTable &launch_table_4_2_0();
+const LaunchTable &launch_table_4_4_0();
+const LaunchTable &launch_table_5_3_0();
+const LaunchTable &launch_table_5_2_0();
+const LaunchTable &launch_table_5_4_0();
+const LaunchTable &launch_table_6_3_0();
+const LaunchTable &launch_table_6_2_0();
+const LaunchTable &launch_table_6_4_0();
+const LaunchTable &launch_table_7_3_0();
+const LaunchTable &launch_table_7_2_0();
+const LaunchTable &launch_table_7_4_0();
+const LaunchTable &launch_table_8_3_0();
+const LaunchTable &launch_table_8_2_0();
+const LaunchTable &launch_table_8_4_0();
+const LaunchTable &launch_table_9_3_0();
+const LaunchTable &launch_table_9_2_0();
+const LaunchTable &launch_table_9_4_0();
+const LaunchTable &launch_table_10_3_0();
+const LaunchTable &launch_table_10_2_0();
+const LaunchTable &launch_table_10_4_0();
+const LaunchTable &launch_table_11_3_0();
+const LaunchTable &launch_table_11_2_0();
+const LaunchTable &launch_table_11_4_0();
+const LaunchTable &launch_table_12_3_0();
+const LaunchTable &launch_table_12_2_0();
+const LaunchTable &launch_table_12_4_0();
+const LaunchTable &launch_table_13_3_0();
+const LaunchTable &launch_table_13_3_1();
+const LaunchTable &launch_table_13_2_0();
+const LaunchTable &launch_table_13_2_1();
+const LaunchTable &launch_table_13_4_0();
+const LaunchTable &launch_table_13_4_1();
+const LaunchTable &launch_table_14_3_0();
+const LaunchTable &launch_table_14_3_1();
+const LaunchTable &launch_table_14_2_0();
+const LaunchTable &launch_table_14_2_1();
+const LaunchTable &launch_table_14_4_0();
+const LaunchTable &launch_table_14_4_1();
+const LaunchTable &launch_table_15_3_0();
+const LaunchTable &launch_table_15_3_1();
+const LaunchTable &launch_table_15_2_0();
+const LaunchTable &launch_table_15_2_1();
+const LaunchTable &launch_table_15_4_0();
+const LaunchTable &launch_table_15_4_1();
+const LaunchTable &launch_table_16_3_0();
+const LaunchTable &launch_table_16_3_1();
+const LaunchTable &launch_table_16_2_0();
+const LaunchTable &launch_table_16_2_1();
+const LaunchTable &launch_table_16_4_0();
+const LaunchTable &launch_table_16_4_1();
+const LaunchTable &launch_table_17_3_0();
+const LaunchTable &launch_table_17_3_1();
+const LaunchTable &launch_table_17_2_0();
+const LaunchTable &launch_table_17_2_1();
+const LaunchTable &launch_table_17_4_0();
+const LaunchTable &launch_table_17_4_1();
 
-const LaunchTable *launch_table(int logn, int rl) {
-  switch (rl == 4 ? logn * 4 + 4 + 128 : logn * 4 + rl) {
-    case 7: return &launch_table_1_3();
-    case 6: return &launch_table_1_2();
-    case 136: return &launch_table_1_4();
-    case 11: return &launch_table_2_3();
-    case 10: return &launch_table_2_2();
-    case 140: return &launch_table_2_4();
-    case 15: return &launch_table_3_3();
-    case 14: return &launch_table_3_2();
-    case 144: return &launch_table_3_4();
-    case 19: return &launch_table_4_3();
-    case 18: return &launch_table_4_2();
-    case 148: return &launch_table_4_4();
-    case 23: return &launch_table_5_3();
-    case 22: return &launch_table_5_2();
-    case 152: return &launch_table_5_4();
-    case 27: return &launch_table_6_3();
-    case 26: return &launch_table_6_2();
-    case 156: return &launch_table_6_4();
-    case 31: return &launch_table_7_3();
-    case 30: return &launch_table_7_2();
-    case 160: return &launch_table_7_4();
-    case 35: return &launch_table_8_3();
-    case 34: return &launch_table_8_2();
-    case 164: return &launch_table_8_4();
-    case 39: return &launch_table_9_3();
-    case 38: return &launch_table_9_2();
-    case 168: return &launch_table_9_4();
-    case 43: return &launch_table_10_3();
-    case 42: return &launch_table_10_2();
-    case 172: return &launch_table_10_4();
-    case 47: return &launch_table_11_3();
-    case 46: return &launch_table_11_2();
-    case 176: return &launch_table_11_4();
-    case 51: return &launch_table_12_3();
-    case 50: return &launch_table_12_2();
-    case 180: return &launch_table_12_4();
-    case 55: return &launch_table_13_3();
-    case 54: return &launch_table_13_2();
-    case 184: return &launch_table_13_4();
-    case 59: return &launch_table_14_3();
-    case 58: return &launch_table_14_2();
-    case 188: return &launch_table_14_4();
-    case 63: return &launch_table_15_3();
-    case 62: return &launch_table_15_2();
-    case 192: return &launch_table_15_4();
-    case 67: return &launch_table_16_3();
-    case 66: return &launch_table_16_2();
-    case 196: return &launch_table_16_4();
-    case 71: return &launch_table_17_3();
-    case 70: return &launch_table_17_2();
-    case 200: return &launch_table_17_4();
-    default: return nullptr;
+namespace {
+// [log N][radix log 2..4][column tile 0/1]; sizes with one pass (N <= 2^12) have no
+// column pass, so both column-tile entries name the same launchers.
+using TableFn = const LaunchTable &(*)();
+struct TableSet {
+  TableFn fn[18][5][2] = {};
+  TableSet() {
+#define KS_T0(N)                                \
+  for (int c = 0; c < 2; ++c) {                 \
+    fn[N][3][c] = &launch_table_##N##_3_0;      \
+    fn[N][2][c] = &launch_table_##N##_2_0;      \
+    fn[N][4][c] = &launch_table_##N##_4_0;      \
   }
+#define KS_T1(N)                            \
+  fn[N][3][0] = &launch_table_##N##_3_0;    \
+  fn[N][2][0] = &launch_table_##N##_2_0;    \
+  fn[N][4][0] = &launch_table_##N##_4_0;    \
+  fn[N][3][1] = &launch_table_##N##_3_1;    \
+  fn[N][2][1] = &launch_table_##N##_2_1;    \
+  fn[N][4][1] = &launch_table_##N##_4_1;
+    KS_T0(1) KS_T0(2) KS_T0(3) KS_T0(4) KS_T0(5) KS_T0(6) KS_T0(7) KS_T0(8) KS_T0(9)
+    KS_T0(10) KS_T0(11) KS_T0(12)
+    KS_T1(13) KS_T1(14) KS_T1(15) KS_T1(16) KS_T1(17)
+#undef KS_T0
+#undef KS_T1
+  }
+};
+}  // namespace
+
+const LaunchTable *launch_table(int logn, int rl, int ca) {
+  static const TableSet t;
+  if (logn < 1 || logn > 17 || rl < 2 || rl > 4 || ca < 0 || ca > 1) return nullptr;
+  const TableFn f = t.fn[logn][rl][ca];
+  return f ? &f() : nullptr;
 }
 
 namespace kern {

@@ -2,7 +2,10 @@
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_13_3() { return kern::Launch<13, 3>::table(); }
-const LaunchTable &launch_table_13_2() { return kern::Launch<13, 2>::table(); }
-const LaunchTable &launch_table_13_4() { return kern::Launch<13, 4>::table(); }
+#define KS_INST(N, R, C) \
+  const LaunchTable &launch_table_##N##_##R##_##C() { return kern::Launch<N, R, C>::table(); }
+KS_INST(13, 3, 0)
+KS_INST(13, 2, 0)
+KS_INST(13, 4, 0)
+#undef KS_INST
 }  // namespace ks

@@ -2,7 +2,10 @@
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_15_3() { return kern::Launch<15, 3>::table(); }
-const LaunchTable &launch_table_15_2() { return kern::Launch<15, 2>::table(); }
-const LaunchTable &launch_table_15_4() { return kern::Launch<15, 4>::table(); }
+#define KS_INST(N, R, C) \
+  const LaunchTable &launch_table_##N##_##R##_##C() { return kern::Launch<N, R, C>::table(); }
+KS_INST(15, 3, 0)
+KS_INST(15, 2, 0)
+KS_INST(15, 4, 0)
+#undef KS_INST
 }  // namespace ks

@@ -2,16 +2,19 @@
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_7_3() { return kern::Launch<7, 3>::table(); }
-const LaunchTable &launch_table_7_2() { return kern::Launch<7, 2>::table(); }
-const LaunchTable &launch_table_7_4() { return kern::Launch<7, 4>::table(); }
-const LaunchTable &launch_table_8_3() { return kern::Launch<8, 3>::table(); }
-const LaunchTable &launch_table_8_2() { return kern::Launch<8, 2>::table(); }
-const LaunchTable &launch_table_8_4() { return kern::Launch<8, 4>::table(); }
-const LaunchTable &launch_table_9_3() { return kern::Launch<9, 3>::table(); }
-const LaunchTable &launch_table_9_2() { return kern::Launch<9, 2>::table(); }
-const LaunchTable &launch_table_9_4() { return kern::Launch<9, 4>::table(); }
-const LaunchTable &launch_table_10_3() { return kern::Launch<10, 3>::table(); }
-const LaunchTable &launch_table_10_2() { return kern::Launch<10, 2>::table(); }
-const LaunchTable &launch_table_10_4() { return kern::Launch<10, 4>::table(); }
+#define KS_INST(N, R, C) \
+  const LaunchTable &launch_table_##N##_##R##_##C() { return kern::Launch<N, R, C>::table(); }
+KS_INST(7, 3, 0)
+KS_INST(7, 2, 0)
+KS_INST(7, 4, 0)
+KS_INST(8, 3, 0)
+KS_INST(8, 2, 0)
+KS_INST(8, 4, 0)
+KS_INST(9, 3, 0)
+KS_INST(9, 2, 0)
+KS_INST(9, 4, 0)
+KS_INST(10, 3, 0)
+KS_INST(10, 2, 0)
+KS_INST(10, 4, 0)
+#undef KS_INST
 }  // namespace ks

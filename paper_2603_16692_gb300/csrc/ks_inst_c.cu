@@ -2,10 +2,13 @@
 #include "ks_kern.cuh"
 
 namespace ks {
-const LaunchTable &launch_table_11_3() { return kern::Launch<11, 3>::table(); }
-const LaunchTable &launch_table_11_2() { return kern::Launch<11, 2>::table(); }
-const LaunchTable &launch_table_11_4() { return kern::Launch<11, 4>::table(); }
-const LaunchTable &launch_table_12_3() { return kern::Launch<12, 3>::table(); }
-const LaunchTable &launch_table_12_2() { return kern::Launch<12, 2>::table(); }
-const LaunchTable &launch_table_12_4() { return kern::Launch<12, 4>::table(); }
+#define KS_INST(N, R, C) \
+  const LaunchTable &launch_table_##N##_##R##_##C() { return kern::Launch<N, R, C>::table(); }
+KS_INST(11, 3, 0)
+KS_INST(11, 2, 0)
+KS_INST(11, 4, 0)
+KS_INST(12, 3, 0)
+KS_INST(12, 2, 0)
+KS_INST(12, 4, 0)
+#undef KS_INST
 }  // namespace ks

@@ -110,9 +110,11 @@ struct ks_context {
   int top_L = -1;  // level of the context whose keys this one uses (-1: itself)
   int N;
   int loga, logb, loggr;  // two-pass split N = 2^loga * 2^logb; rows per row tile 2^loggr
-  const ks::LaunchTable *lt = nullptr;   // radix-8 kernels
-  const ks::LaunchTable *lt4 = nullptr;  // radix-4 kernels (twice the threads per tile)
-  const ks::LaunchTable *lt16 = nullptr; // radix-16 kernels (half the threads per tile)
+  // Launchers by register-round radix (index log2 radix - 2: radix 4 has twice the
+  // threads per tile of radix 8, radix 16 half) and column tile (0: default, 1: the
+  // alternative); lt = radix 8, default tiles.
+  const ks::LaunchTable *ltab[3][2] = {};
+  const ks::LaunchTable *lt = nullptr;
   int run_up = 1, run_down = 1;  // max terms per exact 128-bit BConv sum
   std::vector<u64> mods;  // host copy, Q then P
   void *table_mem = nullptr;
@@ -213,8 +215,9 @@ int switch_launch_only(ks_context *c, const uint64_t *d, const uint64_t *evk, ui
 bool selected_current(const ks_context *c);
 
 // rl = log2 of the radix of the register rounds (3: 8 points per thread, 2: 4 points
-// per thread, twice the threads per tile).
-const LaunchTable *launch_table(int logn, int rl);
+// per thread, twice the threads per tile; 4: 16 points); ca = 1: the alternative
+// column tile (geo_tile_log_col_alt).
+const LaunchTable *launch_table(int logn, int rl, int ca);
 
 // Element-wise kernels (ks_elem.cu): the unfused building blocks and keygen.
 cudaError_t launch_bconv_up(const ks_context *c, const JobSet &js, const WsOff &o,

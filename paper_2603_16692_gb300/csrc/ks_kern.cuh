@@ -441,11 +441,11 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
 
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
 // per-limb scale; `only_o` as in the row pass.
-template <int LOGN, int RL>
+template <int LOGN, int RL, int CA>
 __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              int which, int bx, int by, unsigned char *raw,
                                              int only_o = -1) {
-  using GT = GeoT<LOGN, RL, 0>;
+  using GT = GeoT<LOGN, RL, 0, CA>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
   const InttSet is = intt_set(a, jp, wo, which);
@@ -475,14 +475,14 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
   }
 }
 
-template <int LOGN, int RL>
-__global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT,
-                                  min_blocks(GeoT<LOGN, RL, 0>::NT, RL == 4 ? 512 : 768))
+template <int LOGN, int RL, int CA>
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 0, CA>::NT,
+                                  min_blocks(GeoT<LOGN, RL, 0, CA>::NT, RL == 4 ? 512 : 768))
     k_inv_col(KArgs a, JobSet js, WsOff wo, int which, int split) {
   extern __shared__ __align__(16) unsigned char raw[];
   int only_o;
   const int by = inv_grid_row(a, which, split, only_o);
-  inv_col_body<LOGN, RL>(a, js.j[blockIdx.z], wo, which, blockIdx.x, by, raw, only_o);
+  inv_col_body<LOGN, RL, CA>(a, js.j[blockIdx.z], wo, which, blockIdx.x, by, raw, only_o);
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
@@ -504,11 +504,11 @@ __device__ __forceinline__ void fwd_bufs(const JobPtr &jp, const WsOff &wo, int 
 
 // Forward NTT, column pass (global stages 0 .. logN1-1) with a tile producer; the
 // lazy ([0, 4m)) result goes to the output buffer's slot.
-template <int LOGN, int RL, int PRO>
+template <int LOGN, int RL, int PRO, int CA>
 __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int buf, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
-  using GT = GeoT<LOGN, RL, 0>;
+  using GT = GeoT<LOGN, RL, 0, CA>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
   const u64 *src;
@@ -528,14 +528,15 @@ __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, c
 // Tiles of 256+ threads: 4 CTAs per SM (64 registers, a few spilled words) measured
 // 1-3% faster on GB300 at N >= 2^16 than the compiler's 78-register choice; smaller
 // tiles keep that choice.
-template <int LOGN, int RL, int PRO>
-__global__ void __launch_bounds__(GeoT<LOGN, RL, 0>::NT,
-                                  min_blocks(GeoT<LOGN, RL, 0>::NT,
-                                             GeoT<LOGN, RL, 0>::NT >= 256 ? 1024 : 0))
+template <int LOGN, int RL, int PRO, int CA>
+__global__ void __launch_bounds__(GeoT<LOGN, RL, 0, CA>::NT,
+                                  min_blocks(GeoT<LOGN, RL, 0, CA>::NT,
+                                             GeoT<LOGN, RL, 0, CA>::NT >= 256 ? 1024 : 0))
     k_fwd_col(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
-  fwd_col_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, buf, blockIdx.x, blockIdx.y, raw, cst);
+  fwd_col_body<LOGN, RL, PRO, CA>(a, js.j[blockIdx.z], wo, tk, buf, blockIdx.x, blockIdx.y, raw,
+                                  cst);
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
@@ -567,15 +568,24 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
 // target limb t (TASK_TARGET), over digits j0..j1-1:
 //   acc_c[t] (+)= sum_j ext_j[t] * evk[j][c][t],  c = 0, 1,
 // with ext_j[t] = NTT(BConv_j)[t] (Montgomery-scaled) or, on digit j's own limbs,
-// the input d_t (put in Montgomery form here), so that REDC of each exact
-// 128-bit product is the plain product mod m. The row twiddles of (t, tile) are
-// staged once.
+// the input d_t (put in Montgomery form here), so that REDC of a sum of exact
+// 128-bit products is the plain sum of products mod m. The row twiddles of (t, tile)
+// are staged once.
+//
+// The products take ext as the forward pass leaves it (below kFwdLazy * m with the
+// fast butterflies; exact moduli: brought below m by two conditional subtractions),
+// since REDC only needs its input below m 2^64. With at most four elements per
+// thread the products of all digits are summed exactly in 128 bits and reduced once
+// per output word (needs (bound of ext) * (digits) * m < 2^64, checked per CTA; the
+// context guarantees digits * m < 2^64 for canonical ext); with more elements per
+// thread (register budget) each product is reduced and the residues summed lazily.
 template <int LOGN, int RL, int PRO>
 __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
   using GT = GeoT<LOGN, RL, 1>;
   constexpr int EPT = GT::EPT;
+  constexpr bool WIDE = EPT <= 4;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
   const u64 *v = jp.ws + wo.v, *tmp = jp.ws + wo.tmp;
@@ -602,11 +612,36 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
   pdl_wait();
   const u64 pol = l2_stream();
-  // Per-digit products are reduced by REDC and summed lazily in [0, 2m).
-  u64 s0[EPT], s1[EPT];
+  const bool fast = mi.m < kFastModulus;
+  // ext stays lazy when the exact digit sum of its products fits one REDC
+  const int nd = tk.j1 - tk.j0;
+  const bool lazy = fast && (unsigned __int128)(kFwdLazy * (WIDE ? nd : 1)) * mi.m <
+                                (unsigned __int128)1 << 64;
   const u64 m2 = 2 * mi.m;
+  auto ext_word = [&](u64 y) -> u64 {
+    if (lazy) return y;
+    if (!fast) return csub(csub(y, m2), mi.m);  // exact butterflies: below 4m
+    return reduce_full(y, mi.m, mi.mu);
+  };
+  U128 w0[WIDE ? EPT : 1], w1[WIDE ? EPT : 1];  // exact digit sums (WIDE)
+  u64 s0[WIDE ? 1 : EPT], s1[WIDE ? 1 : EPT];    // lazy residue sums in [0, 2m)
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) s0[k] = s1[k] = 0;
+  for (int k = 0; k < (WIDE ? EPT : 1); ++k) w0[k] = w1[k] = U128{0, 0};
+#pragma unroll
+  for (int k = 0; k < (WIDE ? 1 : EPT); ++k) s0[k] = s1[k] = 0;
+  auto mac_word = [&](int k, u64 y, const u64 *e0, const u64 *e1, int e) {
+    if (WIDE) {
+      mac128(w0[k], y, ldg_pol(e0 + e, pol));
+      mac128(w1[k], y, ldg_pol(e1 + e, pol));
+    } else {
+      U128 p0 = {0, 0}, p1 = {0, 0};
+      mac128(p0, y, ldg_pol(e0 + e, pol));
+      mac128(p1, y, ldg_pol(e1 + e, pol));
+      const u64 a0v = s0[k] + redc(p0, mi.m, mi.minv), a1v = s1[k] + redc(p1, mi.m, mi.minv);
+      s0[k] = a0v >= m2 ? a0v - m2 : a0v;
+      s1[k] = a1v >= m2 ? a1v - m2 : a1v;
+    }
+  };
   for (int j = tk.j0; j < tk.j1; ++j) {
     prefetch_digit(j + 1);
     const int lo = j * a.alpha, hi = min(lo + a.alpha, a.nq);
@@ -619,13 +654,9 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
       for (int k = 0; k < EPT; ++k) {
         const int e = threadIdx.x + k * GT::NT;
         if (GT::TILE % GT::NT == 0 || e < GT::TILE) {
-          const u64 y = csub(shoup(__ldg(dt + e), mi.r1, mi.r1s, mi.m), mi.m);
-          U128 p0 = {0, 0}, p1 = {0, 0};
-          mac128(p0, y, ldg_pol(e0 + e, pol));
-          mac128(p1, y, ldg_pol(e1 + e, pol));
-          const u64 a0v = s0[k] + redc(p0, mi.m, mi.minv), a1v = s1[k] + redc(p1, mi.m, mi.minv);
-          s0[k] = a0v >= m2 ? a0v - m2 : a0v;
-          s1[k] = a1v >= m2 ? a1v - m2 : a1v;
+          u64 y = shoup(__ldg(dt + e), mi.r1, mi.r1s, mi.m);  // [0, 2m)
+          if (!lazy) y = csub(y, mi.m);
+          mac_word(k, y, e0, e1, e);
         }
       }
     } else {
@@ -641,13 +672,7 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
         const int e = threadIdx.x + k * GT::NT;
         if (GT::TILE % GT::NT == 0 || e < GT::TILE) {
           const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
-          const u64 y = reduce_full(sm[x * GT::PR + g], mi.m, mi.mu);
-          U128 p0 = {0, 0}, p1 = {0, 0};
-          mac128(p0, y, ldg_pol(e0 + e, pol));
-          mac128(p1, y, ldg_pol(e1 + e, pol));
-          const u64 a0v = s0[k] + redc(p0, mi.m, mi.minv), a1v = s1[k] + redc(p1, mi.m, mi.minv);
-          s0[k] = a0v >= m2 ? a0v - m2 : a0v;
-          s1[k] = a1v >= m2 ? a1v - m2 : a1v;
+          mac_word(k, ext_word(sm[x * GT::PR + g]), e0, e1, e);
         }
       }
       __syncthreads();
@@ -659,8 +684,14 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
   for (int k = 0; k < EPT; ++k) {
     const int e = threadIdx.x + k * GT::NT;
     if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
-    u64 r0v = csub(s0[k], mi.m);
-    u64 r1v = csub(s1[k], mi.m);
+    u64 r0v, r1v;
+    if (WIDE) {
+      r0v = csub(redc(w0[k], mi.m, mi.minv), mi.m);
+      r1v = csub(redc(w1[k], mi.m, mi.minv), mi.m);
+    } else {
+      r0v = csub(s0[k], mi.m);
+      r1v = csub(s1[k], mi.m);
+    }
     if (!tk.first) {
       r0v = addmod(r0v, a0[e], mi.m);
       r1v = addmod(r1v, a1[e], mi.m);
@@ -698,10 +729,15 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
   const u64 *vp = jp.ws + wo.vp, *tmp2 = jp.ws + wo.tmp2, *acc = jp.ws + wo.acc;
   const uint32_t w = decode(a, tk, by);
   const int i = task_limb(w), blk = bx, r0 = blk * GT::GR;
-  const u64 m = a.tab.mod[i].m, mu = a.tab.mod[i].mu;
+  const u64 m = a.tab.mod[i].m;
   const ulonglong2 pv = a.tab.pinv[i];
   const size_t N = a.N;
   const size_t off0 = (size_t)r0 << GT::LOGB;
+  // The NTT output z enters the scaling lazy: below kFwdLazy * m (fast butterflies) or,
+  // after one conditional subtraction, below 2m (exact); acc + zb - z is then positive
+  // and below (kFwdLazy + 1) m < 2^64, and the Shoup product by P^-1 takes any word.
+  const bool fast = m < kFastModulus;
+  const u64 m2 = 2 * m, zb = fast ? kFwdLazy * m : m2;
   if (threadIdx.x == 0)
     for (int c = 0; c < 2; ++c) prefetch_l2(acc + ((size_t)c * a.qp + i) * N + off0, GT::TILE * 8);
   stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
@@ -724,8 +760,8 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
         const int e = threadIdx.x + k * GT::NT;
         if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
         const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
-        const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
-        o[e] = addmod(csub(shoup(ac[e] + m - z, pv.x, pv.y, m), m), ad[e], m);
+        const u64 z = fast ? sm[x * GT::PR + g] : csub(sm[x * GT::PR + g], m2);
+        o[e] = addmod(csub(shoup(ac[e] + zb - z, pv.x, pv.y, m), m), ad[e], m);
       }
     } else {
 #pragma unroll
@@ -733,8 +769,8 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
         const int e = threadIdx.x + k * GT::NT;
         if (GT::TILE % GT::NT != 0 && e >= GT::TILE) break;
         const int g = e >> GT::LOGB, x = e & (GT::N2 - 1);
-        const u64 z = reduce_full(sm[x * GT::PR + g], m, mu);
-        o[e] = csub(shoup(ac[e] + m - z, pv.x, pv.y, m), m);
+        const u64 z = fast ? sm[x * GT::PR + g] : csub(sm[x * GT::PR + g], m2);
+        o[e] = csub(shoup(ac[e] + zb - z, pv.x, pv.y, m), m);
       }
     }
     __syncthreads();
@@ -772,9 +808,9 @@ inline KArgs args_of(const ks_context *c) { return make_args(c); }
 // 10.1 us and 12.0 -> 10.8 us with one CTA per polynomial).
 constexpr int kSplitCtas = 4 * 152;
 
-template <int LOGN, int RL>
+template <int LOGN, int RL, int CA = 0>
 struct Launch {
-  using GTC = GeoT<LOGN, RL, 0>;  // column-pass geometry
+  using GTC = GeoT<LOGN, RL, 0, CA>;  // column-pass geometry (CA: alternative tile)
   using GTR = GeoT<LOGN, RL, 1>;  // row-pass geometry
   static constexpr int GRID_COL = GTC::LOGA == 0 ? 1 : GTC::N2 / GTC::GC;
   static constexpr int GRID_ROW = GTR::N1 / GTR::GR;
@@ -788,10 +824,10 @@ struct Launch {
     if ((e = smem_attr(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, GTR::SMEM_ROW))) return e;
     if ((e = smem_attr(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, GTR::SMEM_ROW))) return e;
     if (GTC::LOGA > 0) {
-      if ((e = smem_attr(k_inv_col<LOGN, RL>, GTC::SMEM_COL))) return e;
-      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_LOAD>, GTC::SMEM_COL))) return e;
-      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_UP>, GTC::SMEM_COL))) return e;
-      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_DOWN>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_inv_col<LOGN, RL, CA>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_LOAD, CA>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_UP, CA>, GTC::SMEM_COL))) return e;
+      if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_DOWN, CA>, GTC::SMEM_COL))) return e;
     }
     return cudaSuccess;
   }
@@ -818,7 +854,7 @@ struct Launch {
     const int inner = which == 0 ? c->nq : c->np;
     if (GTC::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
     const int split = inv_split(GRID_COL, inner, which, js.n);
-    return launch_pdl(k_inv_col<LOGN, RL>, dim3(GRID_COL, inner << split, js.n), dim3(GTC::NT),
+    return launch_pdl(k_inv_col<LOGN, RL, CA>, dim3(GRID_COL, inner << split, js.n), dim3(GTC::NT),
                       GTC::SMEM_COL, s, args_of(c), js, wo, which, split);
   }
 
@@ -827,7 +863,7 @@ struct Launch {
                          const Tasks &tk, int buf, cudaStream_t s) {
     const int n = count_tasks(c, tk);
     if (GTC::LOGA == 0 || n == 0 || js.n == 0) return cudaSuccess;
-    return launch_pdl(k_fwd_col<LOGN, RL, PRO>, dim3(GRID_COL, n, js.n), dim3(GTC::NT),
+    return launch_pdl(k_fwd_col<LOGN, RL, PRO, CA>, dim3(GRID_COL, n, js.n), dim3(GTC::NT),
                       GTC::SMEM_COL, s, args_of(c), js, wo, tk, buf);
   }
 

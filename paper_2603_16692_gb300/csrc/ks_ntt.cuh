@@ -37,6 +37,10 @@ __host__ __device__ constexpr int geo_loga(int logn) { return logn <= 12 ? 0 : l
 __host__ __device__ constexpr int geo_tile_log_col(int logn) {
   return logn <= 12 ? logn : (logn >= 16 ? 11 : 10);
 }
+// The alternative column tile the tuner may pick (CA = 1): the other of 2^10 / 2^11.
+__host__ __device__ constexpr int geo_tile_log_col_alt(int logn) {
+  return logn <= 12 ? logn : (logn >= 16 ? 10 : 11);
+}
 __host__ __device__ constexpr int geo_tile_log_row(int logn) {
   return logn <= 12 ? logn : (logn <= 15 ? 9 : 10);
 }
@@ -46,13 +50,14 @@ __host__ __device__ constexpr int geo_loggr(int logn) {
 
 // RL: log2 of the radix of the register rounds; a thread holds 2^RL points.
 // ROW: geometry of the row pass (1) or of the column pass (0); a kernel runs one pass
-// and uses only that pass's fields.
-template <int LOGN, int RL_, int ROW>
+// and uses only that pass's fields. CA: the column pass uses the alternative tile.
+template <int LOGN, int RL_, int ROW, int CA = 0>
 struct GeoT {
   static constexpr int RL = RL_;
   static constexpr int LOGA = geo_loga(LOGN);  // log N1
   static constexpr int LOGB = LOGN - LOGA;     // log N2
-  static constexpr int TILE_LOG = ROW ? geo_tile_log_row(LOGN) : geo_tile_log_col(LOGN);
+  static constexpr int TILE_LOG =
+      ROW ? geo_tile_log_row(LOGN) : (CA ? geo_tile_log_col_alt(LOGN) : geo_tile_log_col(LOGN));
   static constexpr int LOGGC = LOGA == 0 ? 0 : TILE_LOG - LOGA;  // columns per column tile
   static constexpr int LOGGR = TILE_LOG - LOGB;                  // rows per row tile
   static constexpr int TILE = 1 << TILE_LOG;
@@ -178,8 +183,13 @@ __device__ __forceinline__ void tile_fwd_t(u64 *s, const ulonglong2 *tw, u64 m) 
   }
 }
 
+// Bound of the lazy forward outputs with the fast butterflies: every forward pass
+// (column then row, or one single pass) of the library ends below kFwdLazy * m.
+constexpr u64 kFwdLazy = 70;
+
 // Forward stages on the tile; fast butterflies when m < kFastModulus. Outputs are
-// lazy (below 70m fast, 4m exact): reduce with reduce_full before use.
+// lazy (below kFwdLazy * m fast, 4m exact): reduce before use, or feed them to a
+// reduction whose input bound allows it.
 template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM = 3>
 __device__ __forceinline__ void tile_fwd(u64 *s, const ulonglong2 *tw, u64 m) {
   if (m < kFastModulus)

@@ -18,6 +18,15 @@ KS_AUTO, KS_DSOB, KS_DPOB, KS_DSOC, KS_DPOC = 0, 1, 2, 3, 4
 KS_UNFUSED = 0x100
 KS_RADIX4 = 0x200
 KS_RADIX16 = 0x400
+KS_STAGE_SHIFT = 16
+KS_ST_INV, KS_ST_UPC, KS_ST_KM, KS_ST_DNC, KS_ST_DNR = 0, 1, 2, 3, 4
+KS_R4, KS_R8, KS_R16 = 1, 2, 3
+KS_COLTILE_ALT = 0x4000000
+STAGE_NAMES = ("inv", "upc", "km", "dnc", "dnr")
+
+
+def KS_STAGE_RADIX(stage: int, code: int) -> int:
+    return code << (KS_STAGE_SHIFT + 2 * stage)
 KS_BATCH_GRAPH, KS_BATCH_AUTOTUNE, KS_BATCH_PERSISTENT, KS_BATCH_SELECT = 0x1, 0x2, 0x4, 0x8
 KS_BATCH_TEST_STALL = 0x100
 VARIANTS = {"DSOB": KS_DSOB, "DPOB": KS_DPOB, "DSOC": KS_DSOC, "DPOC": KS_DPOC}
@@ -415,6 +424,12 @@ def variant_name(v: int, chunks: int = 0) -> str:
         s += "-r16"
     if v & KS_UNFUSED:
         s += "-unfused"
+    sched = [f"{STAGE_NAMES[st]}{(4, 8, 16)[code - 1]}" for st in range(5)
+             if (code := (v >> (KS_STAGE_SHIFT + 2 * st)) & 3)]
+    if sched:
+        s += "[" + ",".join(sched) + "]"
+    if v & KS_COLTILE_ALT:
+        s += "-colalt"
     return s
 
 

@@ -27,6 +27,9 @@ def main(argv=None):
     ap.add_argument("--chunks", type=int, default=0)
     ap.add_argument("--unfused", action="store_true")
     ap.add_argument("--radix", type=int, default=8, choices=[4, 8, 16])
+    ap.add_argument("--sched", default="",
+                    help="per-stage radix and column tile, e.g. km4,dnr16,colalt "
+                         "(stages inv, upc, km, dnc, dnr); 'tuned' = ks_tune's choice")
     ap.add_argument("--op", default="switch", choices=["switch", "hmul", "hrot"])
     ap.add_argument("--level", type=int, default=-1, help="run on a level view (default: top)")
     ap.add_argument("--reps", type=int, default=1)
@@ -39,7 +42,7 @@ def main(argv=None):
     prm = W.make_params(dnum, logn, L)
     dev = torch.device("cuda", 0)
     v = ks.VARIANTS[args.variant.upper()] | (ks.KS_UNFUSED if args.unfused else 0) | \
-        {4: ks.KS_RADIX4, 8: 0, 16: ks.KS_RADIX16}[args.radix]
+        {4: ks.KS_RADIX4, 8: 0, 16: ks.KS_RADIX16}[args.radix] | parse_sched(args.sched)
     top = ks.Context(prm)
     ctx = top.at_level(args.level) if args.level >= 0 else top
     nq = ctx.nq
@@ -50,6 +53,8 @@ def main(argv=None):
     ct2 = torch.from_numpy(W.uniform_limbs(g, prm.q[:nq] * 2, prm.N).reshape(2, nq, prm.N)).to(dev)
     out = torch.empty_like(ct)
     torch.cuda.synchronize()
+    if args.sched == "tuned":
+        v, args.chunks = ks.ks_tune(ctx.h, ct[1].contiguous(), evk, out, 1)
 
     def run():
         if args.op == "switch":
@@ -68,6 +73,21 @@ def main(argv=None):
     if ctx is not top:
         ctx.close()
     top.close()
+
+
+def parse_sched(text: str) -> int:
+    """'km4,dnr16,colalt' -> KS_STAGE_RADIX(KS_ST_KM, KS_R4) | ... | KS_COLTILE_ALT."""
+    v = 0
+    for item in filter(None, text.split(",")):
+        if item == "colalt":
+            v |= ks.KS_COLTILE_ALT
+        elif item == "tuned":
+            continue
+        else:
+            name = item.rstrip("0123456789")
+            v |= ks.KS_STAGE_RADIX(ks.STAGE_NAMES.index(name),
+                                   {4: ks.KS_R4, 8: ks.KS_R8, 16: ks.KS_R16}[int(item[len(name):])])
+    return v
 
 
 def stats(run, reps):

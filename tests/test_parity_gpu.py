@@ -93,6 +93,23 @@ def test_plain_workloads_radix4_and_radix16(cfg, seed, radix):
     check(cfg, seed, [v | radix for v in RADIX_PLANS], chunk_list=(2,))
 
 
+SCHEDULES = [
+    ks.KS_DPOB | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4),
+    ks.KS_DPOB | ks.KS_RADIX4 | ks.KS_STAGE_RADIX(ks.KS_ST_UPC, ks.KS_R8)
+    | ks.KS_STAGE_RADIX(ks.KS_ST_DNC, ks.KS_R16) | ks.KS_COLTILE_ALT,
+    ks.KS_DSOB | ks.KS_STAGE_RADIX(ks.KS_ST_INV, ks.KS_R4)
+    | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R16),
+    ks.KS_DPOC | ks.KS_COLTILE_ALT | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R16),
+    ks.KS_DPOB | ks.KS_UNFUSED | ks.KS_STAGE_RADIX(ks.KS_ST_UPC, ks.KS_R4) | ks.KS_COLTILE_ALT,
+]
+
+
+@pytest.mark.parametrize("cfg", [W.C1, W.C2, W.C3])
+def test_plain_workloads_radix_schedules(cfg):
+    """Per-stage radix schedules and the alternative column tile at full size."""
+    check(cfg, 0, SCHEDULES, chunk_list=(3,))
+
+
 @pytest.mark.parametrize("radix", [0, ks.KS_RADIX4, ks.KS_RADIX16])
 @pytest.mark.parametrize("cfg", [W.C2, W.C3])
 def test_host_entry_points_with_each_radix(cfg, radix):

@@ -56,6 +56,47 @@ def test_random_workload_and_plan(k):
     assert np.array_equal(got, want), f"{prm.name()} {name}: " + first_mismatch(got, want)
 
 
+def draw_schedule(k: int):
+    """Case k of the schedule sweep: a workload with N in 2^5..2^17 and a plan whose
+    stages each take a random radix (or the plan's), with the default or the
+    alternative column tile."""
+    g = W.rng(11000 + k, 19)
+    logn = int(g.integers(5, 18))
+    L = int(g.integers(0, 40 if logn <= 13 else (16 if logn <= 16 else 6)))
+    dnum = int(g.integers(1, min(L + 1, 10) + 1))
+    base = int(BASES[g.integers(0, 4)])
+    v = base | int(RADIX[g.integers(0, 3)]) | (ks.KS_UNFUSED if g.random() < 0.25 else 0)
+    for st in range(5):
+        v |= ks.KS_STAGE_RADIX(st, int(g.integers(0, 4)))
+    if g.random() < 0.5:
+        v |= ks.KS_COLTILE_ALT
+    chunks = int(g.integers(1, 8)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0
+    return (dnum, logn, L), v, chunks
+
+
+@pytest.mark.parametrize("k", range(32))
+def test_random_radix_schedule_and_column_tile(k):
+    """Per-stage radix schedules and the alternative column tile (the tuner's search
+    space) on random workloads, bit for bit against the oracle."""
+    import torch
+    cfg, v, chunks = draw_schedule(k)
+    prm = W.make_params(*cfg)
+    g = W.rng(12000 + k, 20)
+    d = W.uniform_limbs(g, prm.q, prm.N)
+    evk = W.uniform_limbs(g, prm.mods * (2 * prm.beta), prm.N).reshape(prm.beta, 2, prm.QP,
+                                                                       prm.N)
+    want = O.keyswitch(prm, d, evk)
+    ctx = ks.Context(prm)
+    try:
+        out = ctx.switch(dev(d), dev(evk), variant=v, chunks=chunks)
+        torch.cuda.synchronize()
+        got = host(out)
+    finally:
+        ctx.close()
+    name = ks.variant_name(v, chunks)
+    assert np.array_equal(got, want), f"{prm.name()} {name}: " + first_mismatch(got, want)
+
+
 def draw_eval(k: int):
     """Case k of the evaluation sweep: a workload, a level below the top (or the top),
     an operation (KeySwitch, HMUL, HROT with a random Galois element) and a plan."""
