@@ -79,9 +79,14 @@ extern "C" {
 #define KS_R8 2
 #define KS_R16 3
 #define KS_STAGE_RADIX(stage, code) ((code) << (KS_STAGE_SHIFT + 2 * (stage)))
-/* OR-ed into the variant: the column passes (N >= 2^13) use the alternative column tile
- * (2^11 points instead of 2^10 up to N = 2^15, 2^10 instead of 2^11 above). */
-#define KS_COLTILE_ALT 0x4000000
+/* OR-ed into the variant: a stage's column pass (N >= 2^13) uses the alternative column
+ * tile (2^11 points instead of 2^10 up to N = 2^15, 2^10 instead of 2^11 above): the
+ * inverse NTTs (KS_COLALT_INV), the ModUp BConv pass (KS_COLALT_UPC), the ModDown BConv
+ * pass (KS_COLALT_DNC), or all three (KS_COLTILE_ALT). */
+#define KS_COLALT_INV 0x4000000
+#define KS_COLALT_UPC 0x8000000
+#define KS_COLALT_DNC 0x10000000
+#define KS_COLTILE_ALT (KS_COLALT_INV | KS_COLALT_UPC | KS_COLALT_DNC)
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -311,8 +316,8 @@ int ks_batch_status(void *stream);
 /* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
  * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one
  * launch set); then, for N >= 2^13, refines the winner's schedule one coordinate at a
- * time: each stage's radix (KS_STAGE_RADIX) and the column tile (KS_COLTILE_ALT), a
- * change kept when the KeySwitch gets more than 1% faster. Stores the result as the
+ * time: each stage's radix (KS_STAGE_RADIX) and each column pass's tile (KS_COLALT_*),
+ * a change kept when the KeySwitch gets more than 1% faster. Stores the result as the
  * context's KS_AUTO plan and writes it to *variant / *chunks. Writes the switched
  * result to out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
 int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,

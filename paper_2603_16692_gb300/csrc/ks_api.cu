@@ -33,7 +33,7 @@ struct Plan {
   bool unfused;
   int rl;        // register-round radix of the plan: 3 (8 points per thread), 2 or 4
   int srl[ST_COUNT];  // per stage (the plan's unless the variant's schedule sets one)
-  int ca;        // 1: alternative column tile
+  int ca[ST_COUNT];   // per stage: 1 = alternative column tile (stages with column passes)
   int code;      // every variant bit that changes the launches (graph-cache key)
   int chunks;    // phase-1 and phase-2 group counts (1 for OB)
   int clen;      // max QP-limbs per phase-1 group
@@ -78,7 +78,10 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
     const int code = (variant >> (KS_STAGE_SHIFT + 2 * st)) & 3;  // 0: the plan's radix
     pl->srl[st] = code == 0 ? pl->rl : code + 1;
   }
-  pl->ca = (variant & KS_COLTILE_ALT) ? 1 : 0;
+  for (int st = 0; st < ST_COUNT; ++st) pl->ca[st] = 0;
+  pl->ca[ST_INV] = (variant & KS_COLALT_INV) ? 1 : 0;
+  pl->ca[ST_UPC] = (variant & KS_COLALT_UPC) ? 1 : 0;
+  pl->ca[ST_DNC] = (variant & KS_COLALT_DNC) ? 1 : 0;
   pl->code = variant & ~0xff;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
@@ -173,7 +176,9 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
   const double BF_B = (double)N / 2 * c->logb * J;       // butterflies, row pass
   const double NJ = (double)N * J;
   const bool single = c->loga == 0;
-  auto stage = [&](int st) -> const LaunchTable & { return *c->ltab[pl.srl[st] - 2][pl.ca]; };
+  auto stage = [&](int st) -> const LaunchTable & {
+    return *c->ltab[pl.srl[st] - 2][pl.ca[st]];
+  };
   const LaunchTable &L = stage(ST_INV), &LU = stage(ST_UPC), &LK = stage(ST_KM),
                     &LDC = stage(ST_DNC), &LDR = stage(ST_DNR);
   WsOff wo;
@@ -1329,11 +1334,12 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
           best_v = v;
         }
       }
-    if (rc == KS_OK) {
-      const float ms = time_plan(best_v ^ KS_COLTILE_ALT, best_c);
+    for (int bit : {KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC}) {
+      if (rc != KS_OK) break;
+      const float ms = time_plan(best_v ^ bit, best_c);
       if (ms < 0.99f * best) {
         best = ms;
-        best_v ^= KS_COLTILE_ALT;
+        best_v ^= bit;
       }
     }
   }

@@ -95,6 +95,29 @@ __device__ __forceinline__ u64 ldg_pol(const u64 *p, u64 pol) {
   return r;
 }
 
+// Asynchronous global -> shared copies (cp.async): each thread's copies form groups
+// (commit), and wait<N> returns once at most the N most recent groups of this thread
+// are still in flight; a barrier then makes every thread's copies visible.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+// 16 bytes, cached in L2 only (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Programmatic dependent launch. Every KeySwitch kernel lets the next kernel of its
 // stream launch once all its CTAs reach their end (pdl_trigger), and waits for the
 // previous kernel to complete, with its memory visible, before it reads or writes any

@@ -701,18 +701,173 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
   }
 }
 
+// Shared memory of the pipelined key multiply: the row twiddles, two ext tiles (odd
+// pitch) and two digits' key tiles (c = 0, 1, contiguous).
+template <class GT>
+struct KmSmem {
+  static constexpr int TW = GT::TWR * 16;
+  static constexpr int TILEW = GT::N2 * GT::PR;  // words of one pitched tile
+  static constexpr int KEYW = 2 * GT::TILE;      // words of one digit's two key tiles
+  static constexpr int BYTES = TW + 2 * TILEW * 8 + 2 * KEYW * 8;
+};
+
+// Which row kernels (key multiply, ModDown) are pipelined: two-pass sizes with radix-4
+// rounds (twice the threads per tile). With radix 8 or 16 the double buffers cost more
+// occupancy than the overlap gains (measured on GB300 at (4, 2^16, 35): key multiply
+// radix 4 115 -> 109 us but radix 8 119 -> 140 us; ModDown radix 4 55 -> 49 us, radix 8
+// 53 -> 57 us).
+template <int LOGN, int RL>
+constexpr bool ROW_PIPE = geo_loga(LOGN) != 0 && RL == 2;
+
+// The key multiply of keymult_body for N >= 2^13, software-pipelined over the digits:
+// while digit j's ext tile is transformed and multiplied, the copies of digit j+1's
+// tile (the ModUp intermediate, or d_t on the digit's own limbs) and of its two key
+// tiles are in flight (cp.async into the other half of double buffers). Same
+// arithmetic, same bounds and the same result as keymult_body.
+template <int LOGN, int RL>
+__device__ __forceinline__ void keymult_pipe_body(const KArgs &a, const JobPtr &jp,
+                                                  const WsOff &wo, const Tasks &tk, int bx,
+                                                  int by, unsigned char *raw) {
+  using GT = GeoT<LOGN, RL, 1>;
+  using SM = KmSmem<GT>;
+  constexpr int EPT = GT::EPT, TILE = GT::TILE, NT = GT::NT;
+  constexpr bool WIDE = EPT <= 4;
+  ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
+  u64 *tiles = reinterpret_cast<u64 *>(raw + SM::TW);
+  u64 *keys = tiles + 2 * SM::TILEW;
+  const u64 *tmp = jp.ws + wo.tmp;
+  u64 *acc = jp.ws + wo.acc;
+  const int t = task_limb(decode(a, tk, by));
+  const ModInfo mi = a.tab.mod[t];
+  const int blk = bx, r0 = blk * GT::GR;
+  const size_t N = a.N;
+  const size_t off0 = (size_t)r0 << GT::LOGB;  // the tile is contiguous from here
+  auto own = [&](int j) {
+    const int lo = j * a.alpha;
+    return t >= lo && t < min(lo + a.alpha, a.nq);
+  };
+  auto issue_keys = [&](int j, int b) {
+    const u64 *e0 = jp.evk + evk_off(a, j, 0, t) + off0;
+    const u64 *e1 = jp.evk + evk_off(a, j, 1, t) + off0;
+    u64 *k0 = keys + b * SM::KEYW;
+#pragma unroll
+    for (int it = 0; it < (TILE / 2 + NT - 1) / NT; ++it) {
+      const int q = threadIdx.x + it * NT;
+      if ((TILE / 2) % NT != 0 && q >= TILE / 2) break;
+      cp_async16(k0 + 2 * q, e0 + 2 * q);
+      cp_async16(k0 + TILE + 2 * q, e1 + 2 * q);
+    }
+  };
+  auto issue_tile = [&](int j, int b) {
+    const u64 *src = own(j) ? jp.d + (size_t)t * N + off0
+                            : tmp + (size_t)(j * tk.sm.sj + t * tk.sm.st + tk.sm.base) * N + off0;
+    u64 *st = tiles + b * SM::TILEW;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int w = threadIdx.x + k * NT;
+      if (TILE % NT != 0 && w >= TILE) break;
+      cp_async8(st + (w & (GT::N2 - 1)) * GT::PR + (w >> GT::LOGB), src + w);
+    }
+  };
+  // the key tiles are inputs of the operation (no kernel of the chain writes them):
+  // their first copies start before the wait for the previous kernel
+  issue_keys(tk.j0, 0);
+  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  pdl_wait();
+  issue_tile(tk.j0, 0);
+  cp_async_commit();
+  const bool fast = mi.m < kFastModulus;
+  const int nd = tk.j1 - tk.j0;
+  const bool lazy = fast && (unsigned __int128)(kFwdLazy * (WIDE ? nd : 1)) * mi.m <
+                                (unsigned __int128)1 << 64;
+  const u64 m2 = 2 * mi.m;
+  U128 w0[WIDE ? EPT : 1], w1[WIDE ? EPT : 1];  // exact digit sums (WIDE)
+  u64 s0[WIDE ? 1 : EPT], s1[WIDE ? 1 : EPT];    // lazy residue sums in [0, 2m)
+#pragma unroll
+  for (int k = 0; k < (WIDE ? EPT : 1); ++k) w0[k] = w1[k] = U128{0, 0};
+#pragma unroll
+  for (int k = 0; k < (WIDE ? 1 : EPT); ++k) s0[k] = s1[k] = 0;
+  for (int j = tk.j0; j < tk.j1; ++j) {
+    const int b = (j - tk.j0) & 1;
+    if (j + 1 < tk.j1) {
+      issue_keys(j + 1, b ^ 1);
+      issue_tile(j + 1, b ^ 1);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // digit j's copies are done (this thread's)
+    __syncthreads();     // ... and every thread's
+    u64 *sm = tiles + b * SM::TILEW;
+    const u64 *k0 = keys + b * SM::KEYW;
+    const bool ow = own(j);
+    if (!ow) tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, mi.m);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (TILE % NT != 0 && e >= TILE) break;
+      const u64 x = sm[(e & (GT::N2 - 1)) * GT::PR + (e >> GT::LOGB)];
+      u64 y;
+      if (ow) {
+        y = shoup(x, mi.r1, mi.r1s, mi.m);  // d_t in Montgomery form, [0, 2m)
+        if (!lazy) y = csub(y, mi.m);
+      } else if (lazy) {
+        y = x;
+      } else {
+        y = fast ? reduce_full(x, mi.m, mi.mu) : csub(csub(x, m2), mi.m);
+      }
+      const u64 ka = k0[e], kb = k0[TILE + e];
+      if (WIDE) {
+        mac128(w0[k], y, ka);
+        mac128(w1[k], y, kb);
+      } else {
+        U128 p0 = {0, 0}, p1 = {0, 0};
+        mac128(p0, y, ka);
+        mac128(p1, y, kb);
+        const u64 a0v = s0[k] + redc(p0, mi.m, mi.minv), a1v = s1[k] + redc(p1, mi.m, mi.minv);
+        s0[k] = a0v >= m2 ? a0v - m2 : a0v;
+        s1[k] = a1v >= m2 ? a1v - m2 : a1v;
+      }
+    }
+    __syncthreads();  // buffers b are free for digit j + 2
+  }
+  u64 *a0 = acc + (size_t)t * N + off0;
+  u64 *a1 = acc + ((size_t)a.qp + t) * N + off0;
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int e = threadIdx.x + k * NT;
+    if (TILE % NT != 0 && e >= TILE) break;
+    u64 r0v, r1v;
+    if (WIDE) {
+      r0v = csub(redc(w0[k], mi.m, mi.minv), mi.m);
+      r1v = csub(redc(w1[k], mi.m, mi.minv), mi.m);
+    } else {
+      r0v = csub(s0[k], mi.m);
+      r1v = csub(s1[k], mi.m);
+    }
+    if (!tk.first) {
+      r0v = addmod(r0v, a0[e], mi.m);
+      r1v = addmod(r1v, a1[e], mi.m);
+    }
+    a0[e] = r0v;
+    a1[e] = r1v;
+  }
+}
+
 template <int LOGN, int RL, int PRO>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
                                   min_blocks(GeoT<LOGN, RL, 1>::NT,
                                              RL == 4 ? 384 : RL == 2 ? 1024 : 768))
     k_fwd_row_keymult(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
-  __shared__ u64 cst[kMaxLimbs];
   // Targets in reverse: the P-limb targets, listed last, have no digit of their own (one
   // more NTT per CTA), so starting them first shortens the tail of multi-wave launches
   // (measured on GB300 at (4, 2^16, 35): 125 -> 121 us for this launch).
-  keymult_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x,
-                              gridDim.y - 1 - blockIdx.y, raw, cst);
+  const int by = gridDim.y - 1 - blockIdx.y;
+  if constexpr (ROW_PIPE<LOGN, RL>) {
+    keymult_pipe_body<LOGN, RL>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, by, raw);
+  } else {
+    __shared__ u64 cst[GeoT<LOGN, RL, 1>::LOGA == 0 ? kMaxLimbs : 1];
+    keymult_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, by, raw, cst);
+  }
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
@@ -777,17 +932,101 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
   }
 }
 
+// Shared memory of the pipelined ModDown row pass: the row twiddles, the two
+// polynomials' NTT tiles (odd pitch) and their accumulator tiles (contiguous).
+template <class GT>
+struct MdSmem {
+  static constexpr int TW = GT::TWR * 16;
+  static constexpr int TILEW = GT::N2 * GT::PR;
+  static constexpr int BYTES = TW + 2 * TILEW * 8 + 2 * GT::TILE * 8;
+};
+
+// moddown_body for N >= 2^13 with both polynomials' input tiles and accumulator tiles
+// copied into shared memory at the start (cp.async): the copies of c = 1 and of the
+// accumulators are in flight while c = 0 is transformed. Same arithmetic and result.
+template <int LOGN, int RL>
+__device__ __forceinline__ void moddown_pipe_body(const KArgs &a, const JobPtr &jp,
+                                                  const WsOff &wo, const Tasks &tk, int bx,
+                                                  int by, unsigned char *raw) {
+  using GT = GeoT<LOGN, RL, 1>;
+  using SM = MdSmem<GT>;
+  constexpr int EPT = GT::EPT, TILE = GT::TILE, NT = GT::NT;
+  ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
+  u64 *tiles = reinterpret_cast<u64 *>(raw + SM::TW);
+  u64 *accs = tiles + 2 * SM::TILEW;
+  const u64 *tmp2 = jp.ws + wo.tmp2, *acc = jp.ws + wo.acc;
+  const uint32_t w = decode(a, tk, by);
+  const int i = task_limb(w), blk = bx, r0 = blk * GT::GR;
+  const u64 m = a.tab.mod[i].m;
+  const ulonglong2 pv = a.tab.pinv[i];
+  const size_t N = a.N;
+  const size_t off0 = (size_t)r0 << GT::LOGB;
+  // the NTT output enters the scaling lazy, as in moddown_body
+  const bool fast = m < kFastModulus;
+  const u64 m2 = 2 * m, zb = fast ? kFwdLazy * m : m2;
+  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
+  pdl_wait();
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const u64 *src = tmp2 + (size_t)(task_slot(w) + c * tk.span) * N + off0;
+    const u64 *ac = acc + ((size_t)c * a.qp + i) * N + off0;
+    u64 *st = tiles + c * SM::TILEW, *sa = accs + c * TILE;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (TILE % NT != 0 && e >= TILE) break;
+      cp_async8(st + (e & (GT::N2 - 1)) * GT::PR + (e >> GT::LOGB), src + e);
+    }
+#pragma unroll
+    for (int it = 0; it < (TILE / 2 + NT - 1) / NT; ++it) {
+      const int q = threadIdx.x + it * NT;
+      if ((TILE / 2) % NT != 0 && q >= TILE / 2) break;
+      cp_async16(sa + 2 * q, ac + 2 * q);
+    }
+    cp_async_commit();
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (c == 0)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
+    __syncthreads();
+    u64 *sm = tiles + c * SM::TILEW;
+    const u64 *sa = accs + c * TILE;
+    tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
+    const size_t ob = ((size_t)c * a.nq + i) * N + off0;
+    u64 *o = jp.out + ob;
+    const bool add = (jp.addmask >> c) & 1;
+    const u64 *ad = jp.add + ob;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (TILE % NT != 0 && e >= TILE) break;
+      const u64 zr = sm[(e & (GT::N2 - 1)) * GT::PR + (e >> GT::LOGB)];
+      const u64 z = fast ? zr : csub(zr, m2);
+      u64 r = csub(shoup(sa[e] + zb - z, pv.x, pv.y, m), m);
+      if (add) r = addmod(r, ad[e], m);
+      o[e] = r;
+    }
+  }
+}
+
 template <int LOGN, int RL, int PRO>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
                                   min_blocks(GeoT<LOGN, RL, 1>::NT, RL == 4 ? 0 : 1024))
     k_fwd_row_moddown(KArgs a, JobSet js, WsOff wo, Tasks tk) {
   extern __shared__ __align__(16) unsigned char raw[];
-  __shared__ u64 cst[kMaxLimbs];
   // host-buffer operation: let the next one's input pass (which reads host memory and
   // does not wait for this kernel before it ends) start while this one writes its result
   // to host memory
   if (js.j[blockIdx.z].dsrc) pdl_trigger();
-  moddown_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
+  if constexpr (ROW_PIPE<LOGN, RL>) {
+    moddown_pipe_body<LOGN, RL>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw);
+  } else {
+    __shared__ u64 cst[GeoT<LOGN, RL, 1>::LOGA == 0 ? kMaxLimbs : 1];
+    moddown_body<LOGN, RL, PRO>(a, js.j[blockIdx.z], wo, tk, blockIdx.x, blockIdx.y, raw, cst);
+  }
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
@@ -816,13 +1055,16 @@ struct Launch {
   static constexpr int GRID_ROW = GTR::N1 / GTR::GR;
   static constexpr int PRO_ROW_UP = GTR::LOGA == 0 ? PRO_UP : PRO_LOAD;
   static constexpr int PRO_ROW_DOWN = GTR::LOGA == 0 ? PRO_DOWN : PRO_LOAD;
+  // the pipelined row kernels reserve their double buffers
+  static constexpr int SMEM_KM = ROW_PIPE<LOGN, RL> ? KmSmem<GTR>::BYTES : GTR::SMEM_ROW;
+  static constexpr int SMEM_MD = ROW_PIPE<LOGN, RL> ? MdSmem<GTR>::BYTES : GTR::SMEM_ROW;
 
   static cudaError_t prepare() {
     cudaError_t e;
     if ((e = smem_attr(k_inv_row<LOGN, RL>, GTR::SMEM_ROW))) return e;
     if ((e = smem_attr(k_fwd_row_store<LOGN, RL>, GTR::SMEM_ROW))) return e;
-    if ((e = smem_attr(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, GTR::SMEM_ROW))) return e;
-    if ((e = smem_attr(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, GTR::SMEM_ROW))) return e;
+    if ((e = smem_attr(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, SMEM_KM))) return e;
+    if ((e = smem_attr(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, SMEM_MD))) return e;
     if (GTC::LOGA > 0) {
       if ((e = smem_attr(k_inv_col<LOGN, RL, CA>, GTC::SMEM_COL))) return e;
       if ((e = smem_attr(k_fwd_col<LOGN, RL, PRO_LOAD, CA>, GTC::SMEM_COL))) return e;
@@ -882,7 +1124,7 @@ struct Launch {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
     return launch_pdl(k_fwd_row_keymult<LOGN, RL, PRO_ROW_UP>, dim3(GRID_ROW, n, js.n),
-                      dim3(GTR::NT), GTR::SMEM_ROW, s, args_of(c), js, wo, tk);
+                      dim3(GTR::NT), SMEM_KM, s, args_of(c), js, wo, tk);
   }
 
   static cudaError_t moddown_row(const ks_context *c, const JobSet &js, const WsOff &wo,
@@ -890,7 +1132,7 @@ struct Launch {
     const int n = count_tasks(c, tk);
     if (n == 0 || js.n == 0) return cudaSuccess;
     return launch_pdl(k_fwd_row_moddown<LOGN, RL, PRO_ROW_DOWN>, dim3(GRID_ROW, n, js.n),
-                      dim3(GTR::NT), GTR::SMEM_ROW, s, args_of(c), js, wo, tk);
+                      dim3(GTR::NT), SMEM_MD, s, args_of(c), js, wo, tk);
   }
 
   static cudaError_t ntt_col(const ks_context *c, const JobSet &js, const WsOff &wo,

@@ -21,7 +21,8 @@ KS_RADIX16 = 0x400
 KS_STAGE_SHIFT = 16
 KS_ST_INV, KS_ST_UPC, KS_ST_KM, KS_ST_DNC, KS_ST_DNR = 0, 1, 2, 3, 4
 KS_R4, KS_R8, KS_R16 = 1, 2, 3
-KS_COLTILE_ALT = 0x4000000
+KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC = 0x4000000, 0x8000000, 0x10000000
+KS_COLTILE_ALT = KS_COLALT_INV | KS_COLALT_UPC | KS_COLALT_DNC
 STAGE_NAMES = ("inv", "upc", "km", "dnc", "dnr")
 
 
@@ -428,8 +429,10 @@ def variant_name(v: int, chunks: int = 0) -> str:
              if (code := (v >> (KS_STAGE_SHIFT + 2 * st)) & 3)]
     if sched:
         s += "[" + ",".join(sched) + "]"
-    if v & KS_COLTILE_ALT:
-        s += "-colalt"
+    alt = [n for n, b in (("inv", KS_COLALT_INV), ("upc", KS_COLALT_UPC), ("dnc", KS_COLALT_DNC))
+           if v & b]
+    if alt:
+        s += "-colalt" if len(alt) == 3 else "-colalt(" + ",".join(alt) + ")"
     return s
 
 

@@ -28,7 +28,7 @@ def main(argv=None):
     ap.add_argument("--unfused", action="store_true")
     ap.add_argument("--radix", type=int, default=8, choices=[4, 8, 16])
     ap.add_argument("--sched", default="",
-                    help="per-stage radix and column tile, e.g. km4,dnr16,colalt "
+                    help="per-stage radix and column tile, e.g. km4,dnr16,colalt-inv "
                          "(stages inv, upc, km, dnc, dnr); 'tuned' = ks_tune's choice")
     ap.add_argument("--op", default="switch", choices=["switch", "hmul", "hrot"])
     ap.add_argument("--level", type=int, default=-1, help="run on a level view (default: top)")
@@ -81,6 +81,9 @@ def parse_sched(text: str) -> int:
     for item in filter(None, text.split(",")):
         if item == "colalt":
             v |= ks.KS_COLTILE_ALT
+        elif item.startswith("colalt-"):
+            v |= {"inv": ks.KS_COLALT_INV, "upc": ks.KS_COLALT_UPC,
+                  "dnc": ks.KS_COLALT_DNC}[item[len("colalt-"):]]
         elif item == "tuned":
             continue
         else:

@@ -101,6 +101,9 @@ SCHEDULES = [
     | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R16),
     ks.KS_DPOC | ks.KS_COLTILE_ALT | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R16),
     ks.KS_DPOB | ks.KS_UNFUSED | ks.KS_STAGE_RADIX(ks.KS_ST_UPC, ks.KS_R4) | ks.KS_COLTILE_ALT,
+    ks.KS_DPOB | ks.KS_COLALT_INV | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4),
+    ks.KS_DSOC | ks.KS_COLALT_UPC | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R4),
+    ks.KS_DPOB | ks.KS_UNFUSED | ks.KS_COLALT_DNC,
 ]
 
 

@@ -58,8 +58,8 @@ def test_random_workload_and_plan(k):
 
 def draw_schedule(k: int):
     """Case k of the schedule sweep: a workload with N in 2^5..2^17 and a plan whose
-    stages each take a random radix (or the plan's), with the default or the
-    alternative column tile."""
+    stages each take a random radix (or the plan's), each column pass the default or
+    the alternative column tile."""
     g = W.rng(11000 + k, 19)
     logn = int(g.integers(5, 18))
     L = int(g.integers(0, 40 if logn <= 13 else (16 if logn <= 16 else 6)))
@@ -68,8 +68,9 @@ def draw_schedule(k: int):
     v = base | int(RADIX[g.integers(0, 3)]) | (ks.KS_UNFUSED if g.random() < 0.25 else 0)
     for st in range(5):
         v |= ks.KS_STAGE_RADIX(st, int(g.integers(0, 4)))
-    if g.random() < 0.5:
-        v |= ks.KS_COLTILE_ALT
+    for bit in (ks.KS_COLALT_INV, ks.KS_COLALT_UPC, ks.KS_COLALT_DNC):
+        if g.random() < 0.4:
+            v |= bit
     chunks = int(g.integers(1, 8)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0
     return (dnum, logn, L), v, chunks
 
