@@ -87,6 +87,12 @@ extern "C" {
 #define KS_COLALT_UPC 0x8000000
 #define KS_COLALT_DNC 0x10000000
 #define KS_COLTILE_ALT (KS_COLALT_INV | KS_COLALT_UPC | KS_COLALT_DNC)
+/* OR-ed into a fused DPOB variant at N >= 2^13 (other plans ignore it): the key multiply
+ * of the Q-limb targets runs on a second stream of the context while, on `stream`, the
+ * P-limb targets' key multiply is followed by the iNTT of the accumulators' P-limbs and
+ * the ModDown BConv pass (they need only the P-limb accumulators); the two join before
+ * the last ModDown pass. Same result bits; calls on one context serialize this fork. */
+#define KS_SPLIT_DOWN 0x20000000
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -172,7 +178,7 @@ int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *by
  *   evk_dev [beta][2][QP][N]    keys from ks_keygen (or any canonical keys)
  *   out_dev [2][L+1][N]         output pair, NTT form; must not alias the inputs
  *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | a radix schedule
- *           KS_STAGE_RADIX(..) | KS_COLTILE_ALT), or KS_AUTO (the
+ *           KS_STAGE_RADIX(..) | KS_COLALT_* | KS_SPLIT_DOWN), or KS_AUTO (the
  *           plan ks_tune chose for this context, else the one ks_select chose, else
  *           DPOB fused radix 8)
  *   chunks  1..64 output groups for the OC variants (0 = 2; the paper searches 2..10);
@@ -316,8 +322,9 @@ int ks_batch_status(void *stream);
 /* Autotuner: times the dataflows {DPOB, DSOB, DPOC c=2, DPOC c=4, DSOC c=2} x
  * {radix 8, radix 4, radix 16} on this job (replicated `batch` times, 1..16, in one
  * launch set); then, for N >= 2^13, refines the winner's schedule one coordinate at a
- * time: each stage's radix (KS_STAGE_RADIX) and each column pass's tile (KS_COLALT_*),
- * a change kept when the KeySwitch gets more than 1% faster. Stores the result as the
+ * time: each stage's radix (KS_STAGE_RADIX), each column pass's tile (KS_COLALT_*) and,
+ * for DPOB, the split ModDown (KS_SPLIT_DOWN), a change kept when the KeySwitch gets
+ * more than 1% faster. Stores the result as the
  * context's KS_AUTO plan and writes it to *variant / *chunks. Writes the switched
  * result to out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
 int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,

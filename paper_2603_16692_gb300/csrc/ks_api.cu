@@ -35,6 +35,7 @@ struct Plan {
   int srl[ST_COUNT];  // per stage (the plan's unless the variant's schedule sets one)
   int ca[ST_COUNT];   // per stage: 1 = alternative column tile (stages with column passes)
   int code;      // every variant bit that changes the launches (graph-cache key)
+  bool split;    // KS_SPLIT_DOWN in effect (fused DPOB, two-pass N)
   int chunks;    // phase-1 and phase-2 group counts (1 for OB)
   int clen;      // max QP-limbs per phase-1 group
   int clq;       // max Q-limbs per phase-2 group
@@ -47,7 +48,8 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 constexpr int kSchedMask = 0x3ff << KS_STAGE_SHIFT;
 
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
-  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT))
+  if (variant &
+      ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT | KS_SPLIT_DOWN))
     return KS_EINVAL;
   if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
@@ -83,6 +85,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   pl->ca[ST_UPC] = (variant & KS_COLALT_UPC) ? 1 : 0;
   pl->ca[ST_DNC] = (variant & KS_COLALT_DNC) ? 1 : 0;
   pl->code = variant & ~0xff;
+  pl->split = (variant & KS_SPLIT_DOWN) && base == KS_DPOB && !pl->unfused && c->loga > 0;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
   pl->clq = (c->nq + chunks - 1) / chunks;
@@ -167,8 +170,13 @@ cudaError_t timed(const char *name, double bytes, double ops, double macs, cudaS
   return e;
 }
 
-int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
+int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
+             bool allow_split = true) {
   if (js.n == 0) return KS_OK;
+  // KS_SPLIT_DOWN: the fork / join below must not interleave with another call's
+  const bool split = pl.split && allow_split && c->side;
+  std::unique_lock<std::mutex> side_lock(c->side_mu, std::defer_lock);
+  if (split) side_lock.lock();
   const size_t N = c->N;
   const double J = js.n;                                 // jobs per launch
   const double W = (double)N * 8 * J;                    // bytes per limb, all jobs
@@ -249,7 +257,22 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
       // acc written (and read when accumulating over digit launches)
       const double km_bytes = (2 * nd * nt + nconv + own + (up.first ? 2 : 4) * nt) * W;
       const double km_ops = 2 * nd * nt * NJ + own * NJ;
-      if (!pl.unfused) {
+      if (!pl.unfused && split) {
+        // P-limb targets here; Q-limb targets on the side stream, forked after ModUp and
+        // joined before the last ModDown pass (the P-limb chain needs no Q-limb acc)
+        const double fq = (double)c->nq / c->qp, fp = 1.0 - fq;
+        const double b = km_bytes, o = km_ops + nconv * BF_B, m = km_ops;
+        KS_TRY(cudaEventRecord(c->ev_fork, s));
+        KS_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        Tasks tp = tg, tq = tg;
+        tp.t0 = c->nq;
+        tq.t1 = c->nq;
+        KS_TRY(timed("modup_row_keymult", fp * b, fp * o, fp * m, s,
+                     [&] { return LK.modup_row(c, js, wo, tp, s); }));
+        KS_TRY(timed("modup_row_keymult", fq * b, fq * o, fq * m, c->side,
+                     [&] { return LK.modup_row(c, js, wo, tq, c->side); }));
+        KS_TRY(cudaEventRecord(c->ev_join, c->side));
+      } else if (!pl.unfused) {
         const double b = km_bytes + (single ? src_b - nconv * W : 0);
         const double o = km_ops + nconv * BF_B + (single ? conv_ops : 0);
         const double m = km_ops + (single ? conv_ops : 0);
@@ -291,6 +314,7 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s) {
                      [&] { return LDC.moddown_col(c, js, wo, dn, s); }));
       const double b = 3 * n * W + (single ? vp_b - n * W : 0);
       const double o = n * (BF_B + NJ) + (single ? conv : 0);
+      if (split) KS_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
       KS_TRY(timed("moddown_row", b, o, single ? conv : 0, s,
                    [&] { return LDR.moddown_row(c, js, wo, d1, s); }));
     } else {
@@ -449,6 +473,15 @@ int create_context(int dnum, int logn, int L, const u64 *q, const u64 *p, int al
       c->ltab[r][ca] = t;
     }
   c->lt = c->ltab[1][0];
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    delete c;
+    return KS_ECUDA;
+  }
   c->mods = mods;
   // basis-conversion sums: run * max_source * m < m 2^64
   c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
@@ -800,6 +833,12 @@ void ks_context_destroy(ks_context *c) {
   forget_graphs(c);
   drop_graph_cache(c);
   if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->table_mem) cudaFree(c->table_mem);
   if (c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
@@ -882,7 +921,7 @@ int switch_launch_only(ks_context *c, const uint64_t *d, const uint64_t *evk, ui
   js.j[0].evk = (const u64 *)evk;
   js.j[0].out = (u64 *)out;
   js.j[0].ws = (u64 *)ws;
-  return run_plan(c, pl, js, (cudaStream_t)stream);
+  return run_plan(c, pl, js, (cudaStream_t)stream, false);
 }
 
 }  // namespace ks
@@ -1334,8 +1373,9 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
           best_v = v;
         }
       }
-    for (int bit : {KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC}) {
+    for (int bit : {KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC, KS_SPLIT_DOWN}) {
       if (rc != KS_OK) break;
+      if (bit == KS_SPLIT_DOWN && ((best_v & 0xff) != KS_DPOB || (best_v & KS_UNFUSED))) continue;
       const float ms = time_plan(best_v ^ bit, best_c);
       if (ms < 0.99f * best) {
         best = ms;

@@ -146,6 +146,12 @@ struct ks_context {
   std::map<std::array<uintptr_t, 10>, CachedGraph> gcache;
   unsigned long long gclock = 0;
   cudaStream_t gstream = nullptr;  // capture stream
+  // second stream of plans with KS_SPLIT_DOWN (the Q-limb key multiply runs there while
+  // the P-limb ModDown chain runs on the caller's stream), its fork / join events, and
+  // the lock that keeps one call's record / wait pairs together
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::mutex side_mu;
 };
 
 namespace ks {
@@ -208,7 +214,8 @@ struct LaunchTable {
                          int buf, cudaStream_t);
 };
 // ks_switch on the caller's workspace `ws` (ws_bytes >= ks_workspace_size) that only
-// launches kernels on `stream`: no graph cache, no arena (ks_api.cu).
+// launches kernels, all on `stream` (a KS_SPLIT_DOWN plan runs unsplit): no graph
+// cache, no arena (ks_api.cu).
 int switch_launch_only(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out,
                        int variant, int chunks, void *ws, size_t ws_bytes, void *stream);
 // True when ctx's selected plan came from the selector installed now (ks_select.cu).

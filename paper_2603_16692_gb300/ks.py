@@ -23,6 +23,7 @@ KS_ST_INV, KS_ST_UPC, KS_ST_KM, KS_ST_DNC, KS_ST_DNR = 0, 1, 2, 3, 4
 KS_R4, KS_R8, KS_R16 = 1, 2, 3
 KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC = 0x4000000, 0x8000000, 0x10000000
 KS_COLTILE_ALT = KS_COLALT_INV | KS_COLALT_UPC | KS_COLALT_DNC
+KS_SPLIT_DOWN = 0x20000000
 STAGE_NAMES = ("inv", "upc", "km", "dnc", "dnr")
 
 
@@ -433,6 +434,8 @@ def variant_name(v: int, chunks: int = 0) -> str:
            if v & b]
     if alt:
         s += "-colalt" if len(alt) == 3 else "-colalt(" + ",".join(alt) + ")"
+    if v & KS_SPLIT_DOWN:
+        s += "-split"
     return s
 
 

@@ -79,7 +79,9 @@ def parse_sched(text: str) -> int:
     """'km4,dnr16,colalt' -> KS_STAGE_RADIX(KS_ST_KM, KS_R4) | ... | KS_COLTILE_ALT."""
     v = 0
     for item in filter(None, text.split(",")):
-        if item == "colalt":
+        if item == "split":
+            v |= ks.KS_SPLIT_DOWN
+        elif item == "colalt":
             v |= ks.KS_COLTILE_ALT
         elif item.startswith("colalt-"):
             v |= {"inv": ks.KS_COLALT_INV, "upc": ks.KS_COLALT_UPC,

@@ -110,3 +110,60 @@ def test_tuner_picks_a_valid_plan_and_writes_result():
         assert np.array_equal(host(out2), out_o)
     finally:
         ctx.close()
+
+
+SPLIT = ks.KS_DPOB | ks.KS_SPLIT_DOWN
+
+
+@pytest.mark.parametrize("flags", [0, ks.KS_BATCH_GRAPH])
+def test_batch_split_moddown_plans(flags):
+    """Jobs naming the split-ModDown plan (second stream per context) in a batch, plain
+    and captured into a graph (two groups of one context fork onto the same side
+    stream), replayed twice, bit for bit against the oracle."""
+    import torch
+    cfgs = [(2, 13, 7), (4, 16, 9), (2, 13, 7), (3, 15, 6), (4, 16, 9)]
+    seeds = [0, 1, 2, 3, 4]
+    plans = [SPLIT, SPLIT | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4), ks.KS_DPOB, SPLIT,
+             SPLIT | ks.KS_RADIX4]
+    ctxs, jobs = _jobs(cfgs, seeds)
+    try:
+        arg = [(c.h, d, evk, out, v, 0) for (c, d, evk, out, _), v in zip(jobs, plans)]
+        for rep in range(2):
+            for _, _, _, out, _ in jobs:
+                out.fill_(3)
+            ks.ks_switch_batch(arg, flags)
+            torch.cuda.synchronize()
+            for k, (_, _, _, out, want) in enumerate(jobs):
+                got = host(out)
+                assert np.array_equal(got, want), f"rep {rep} job {k} {cfgs[k]}: " + \
+                    first_mismatch(got, want)
+    finally:
+        for c in ctxs.values():
+            c.close()
+
+
+def test_split_moddown_from_two_streams_on_one_context():
+    """Two caller streams (own workspaces) switching on one context with the split plan:
+    the context's fork / join is serialized per call, every result exact."""
+    import torch
+    cfg = (4, 16, 11)
+    cases = [oracle_case(cfg, s) for s in (0, 1)]
+    prm = cases[0][0]
+    ctx = ks.Context(prm)
+    try:
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        n = ks.ks_workspace_size(ctx.h, SPLIT, 0) // 8 + 1
+        wss = [torch.empty(n, dtype=torch.uint64, device="cuda") for _ in streams]
+        ins = [(dev(c[5]), dev(c[6])) for c in cases]
+        outs = [torch.full((2, prm.L + 1, prm.N), 3, dtype=torch.uint64, device="cuda")
+                for _ in streams]
+        torch.cuda.synchronize()
+        for rep in range(6):
+            q = rep % 2
+            with torch.cuda.stream(streams[q]):
+                ctx.switch(ins[q][0], ins[q][1], outs[q], SPLIT, 0, wss[q], streams[q])
+        torch.cuda.synchronize()
+        for q in range(2):
+            assert np.array_equal(host(outs[q]), cases[q][7]), f"stream {q}"
+    finally:
+        ctx.close()

@@ -104,6 +104,9 @@ SCHEDULES = [
     ks.KS_DPOB | ks.KS_COLALT_INV | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4),
     ks.KS_DSOC | ks.KS_COLALT_UPC | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R4),
     ks.KS_DPOB | ks.KS_UNFUSED | ks.KS_COLALT_DNC,
+    ks.KS_DPOB | ks.KS_SPLIT_DOWN | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4),
+    ks.KS_DPOB | ks.KS_RADIX4 | ks.KS_SPLIT_DOWN | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R8),
+    ks.KS_DPOC | ks.KS_SPLIT_DOWN,  # ignored by other plans
 ]
 
 

@@ -71,6 +71,8 @@ def draw_schedule(k: int):
     for bit in (ks.KS_COLALT_INV, ks.KS_COLALT_UPC, ks.KS_COLALT_DNC):
         if g.random() < 0.4:
             v |= bit
+    if g.random() < 0.4:
+        v |= ks.KS_SPLIT_DOWN
     chunks = int(g.integers(1, 8)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0
     return (dnum, logn, L), v, chunks
 
