@@ -131,8 +131,8 @@ int build_tables(ks_context *c) {
   const size_t twr_tile = (N2 - 1) * GR;  // entries per row tile
 
   std::vector<ModInfo> mod(QP);
-  std::vector<ulonglong2> twc_f(QP * N1), twc_i(QP * N1), twr_f(QP * rowlen),
-      twr_i(QP * rowlen);
+  // (the inverse row pass reads the forward row table, mirrored: see ks_ntt.cuh)
+  std::vector<ulonglong2> twc_f(QP * N1), twc_i(QP * N1), twr_f(QP * rowlen);
   std::vector<ulonglong2> iscale_q(nq), iscale_p(np), pinv(nq), pmod(nq);
   std::vector<u64> cup((size_t)beta * QP * alpha, 0), cdown((size_t)nq * alpha, 0);
 
@@ -172,7 +172,6 @@ int build_tables(ks_context *c) {
             const size_t idx =
                 t * rowlen + b * twr_tile + ((((size_t)1 << ls) - 1 + cc) << loggr) + g;
             twr_f[idx] = shoup_pair(pw[e], m);
-            twr_i[idx] = shoup_pair(pwi[e], m);
           }
   });
 
@@ -234,7 +233,6 @@ int build_tables(ks_context *c) {
       {twc_f.data(), twc_f.size() * 16, (void **)&T.twc_f},
       {twc_i.data(), twc_i.size() * 16, (void **)&T.twc_i},
       {twr_f.data(), twr_f.size() * 16, (void **)&T.twr_f},
-      {twr_i.data(), twr_i.size() * 16, (void **)&T.twr_i},
       {iscale_q.data(), iscale_q.size() * 16, (void **)&T.iscale_q},
       {iscale_p.data(), iscale_p.size() * 16, (void **)&T.iscale_p},
       {cup.data(), cup.size() * 8, (void **)&T.cup},

@@ -86,8 +86,8 @@ struct Tables {
   ModInfo *mod;          // [QP]
   ulonglong2 *twc_f;     // [QP][N1]  column-pass forward twiddles (w, w')
   ulonglong2 *twc_i;     // [QP][N1]  column-pass inverse twiddles
-  ulonglong2 *twr_f;     // [QP][N1/GR][N2-1][GR] row-pass forward twiddles by row tile
-  ulonglong2 *twr_i;     // [QP][N1/GR][N2-1][GR]
+  ulonglong2 *twr_f;     // [QP][N1/GR][N2-1][GR] row-pass twiddles by row tile (the
+                         // inverse row pass reads them mirrored)
   ulonglong2 *iscale_q;  // [nq]  N^-1 * Qhat_{j,i}^-1 mod q_i   (Shoup pair)
   ulonglong2 *iscale_p;  // [np]  N^-1 * Phat_k^-1 mod p_k
   u64 *cup;              // [beta][QP][alpha] (Qhat_{j,i} mod m_t) 2^128 mod m_t

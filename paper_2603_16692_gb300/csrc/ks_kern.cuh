@@ -382,7 +382,8 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   const int r0 = blk * GT::GR;
   const u64 m = a.tab.mod[prime].m, mu = a.tab.mod[prime].mu;
   const size_t N = a.N;
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_i, prime, blk), GT::TWR);
+  // inverse twiddles: the forward slab of the mirrored row tile (see ks_ntt.cuh)
+  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, prime, GT::N1 / GT::GR - 1 - blk), GT::TWR);
   // Reading the input from host memory (`dsrc`), this pass writes only v and the device
   // copy of d, which no kernel of the previous operation on the stream reads once its
   // last kernel runs: it starts without waiting, so its host reads overlap that kernel's

@@ -6,6 +6,12 @@
 // k = a(psi^(2 brv(k)+1)) (bit-reversed evaluation order). The inverse runs the
 // Gentleman-Sande stages in reverse with psi^-brv(m+i), then scales by N^-1.
 //
+// The inverse twiddle of block i at stage s is psi^-brv(2^s + i) = -psi^brv(2^s + i'),
+// with i' = i XOR (2^s - 1) (psi^N = -1, and brv maps the complement of i to N minus
+// the exponent). The inverse row pass therefore reads the forward row table: the slab
+// of the mirrored row tile, mirrored inside (row g -> G-1-g, block c -> 2^ls-1-c),
+// and its Gentleman-Sande butterflies take (Y - X) w instead of (X - Y)(-w).
+//
 // N = N1 * N2. The column pass runs stages 0..log N1-1 on the N2 columns (each an
 // N1-point transform with twiddle index 2^ls + c for local stage ls, block c);
 // the row pass runs the remaining stages on the N1 rows of N2 contiguous points
@@ -109,6 +115,20 @@ __device__ __forceinline__ void bfly_inv_fast(u64 &a, u64 &b, const ulonglong2 w
   a = X + Y;
   b = shoup4(X - Y + bias, w.x, w.y, m);
 }
+// The same two butterflies with the negated twiddle -w given as w (mirrored tables).
+__device__ __forceinline__ void bfly_inv_neg(u64 &a, u64 &b, const ulonglong2 w, u64 m,
+                                             u64 m2) {
+  const u64 X = a, Y = b;
+  u64 S = X + Y;
+  a = S >= m2 ? S - m2 : S;
+  b = shoup(Y - X + m2, w.x, w.y, m);
+}
+__device__ __forceinline__ void bfly_inv_fast_neg(u64 &a, u64 &b, const ulonglong2 w, u64 m,
+                                                  u64 bias) {
+  const u64 X = a, Y = b;
+  a = X + Y;
+  b = shoup4(Y - X + bias, w.x, w.y, m);
+}
 
 template <int LOGM, int LOGG, int P, int NT, bool ROW, bool INV, int LS0, int R, bool FAST>
 __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
@@ -149,19 +169,29 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
 #pragma unroll
       for (int q = R - 1; q >= 0; --q) {
         const int half = 1 << (R - 1 - q);
+        // row pass: the forward slab of the mirrored tile, entry (2^ls - 1 + c') G + g'
+        // with c' = 2^ls - 1 - c, g' = G - 1 - g (negated twiddles)
         const ulonglong2 *twq =
-            ROW ? tw + ((((1 << (LS0 + q)) - 1 + (hi << q)) << LOGG) + g)
+            ROW ? tw + ((((2 << (LS0 + q)) - 2 - (hi << q)) << LOGG) + ((1 << LOGG) - 1 - g))
                 : tw + (1 << (LS0 + q)) + (hi << q);
         // processed-stage index k = LOGM-1-ls, bias m 2^(k+1)
         const u64 bias = m << (LOGM - (LS0 + q));
 #pragma unroll
         for (int u = 0; u < (1 << R); ++u) {
           if (u & half) continue;
-          const ulonglong2 w = twq[ROW ? ((u >> (R - q)) << LOGG) : (u >> (R - q))];
-          if (FAST)
-            bfly_inv_fast(v[u], v[u + half], w, m, bias);
-          else
-            bfly_inv(v[u], v[u + half], w, m, m2);
+          if (ROW) {
+            const ulonglong2 w = twq[-((u >> (R - q)) << LOGG)];
+            if (FAST)
+              bfly_inv_fast_neg(v[u], v[u + half], w, m, bias);
+            else
+              bfly_inv_neg(v[u], v[u + half], w, m, m2);
+          } else {
+            const ulonglong2 w = twq[u >> (R - q)];
+            if (FAST)
+              bfly_inv_fast(v[u], v[u + half], w, m, bias);
+            else
+              bfly_inv(v[u], v[u + half], w, m, m2);
+          }
         }
       }
     }
