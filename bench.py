@@ -40,19 +40,22 @@ MAX_STREAMS = 3
 UNIT = "KeySwitch/s"
 WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 
-# Per-kernel DRAM bytes (read + write) per launch and the busiest integer pipe, from one
-# cold-cache ncu capture of every kernel of one KeySwitch of the workload (profile_case,
-# `--metrics dram__bytes_read.sum,dram__bytes_write.sum,...`); keyed by (workload,
-# kernel), with the plan the capture ran. Missing = not captured for the current kernels.
-NCU = {("c3", k): {"traffic": t, "plan": "DPOB", **pipes} for k, t, pipes in (
-    ("intt_row(d)", 57072640, {"issue_pct": 39.6, "alu_pct": 33.0, "fma_cycles_pct": 22.2}),
-    ("intt_col(d)", 19061760, {"issue_pct": 39.6, "alu_pct": 32.0, "fma_cycles_pct": 24.1}),
-    ("modup_col", 38981888, {"issue_pct": 59.5, "alu_pct": 47.8, "fma_cycles_pct": 36.2}),
-    ("modup_row_keymult", 360252416, {"issue_pct": 53.3, "alu_pct": 44.3, "fma_cycles_pct": 35.3}),
-    ("intt_row(accP)", 18875648, {"issue_pct": 41.0, "alu_pct": 36.4, "fma_cycles_pct": 22.2}),
-    ("intt_col(accP)", 9512192, {"issue_pct": 40.2, "alu_pct": 35.7, "fma_cycles_pct": 23.6}),
-    ("moddown_col", 9656064, {"issue_pct": 57.2, "alu_pct": 45.1, "fma_cycles_pct": 35.3}),
-    ("moddown_row", 129248512, {"issue_pct": 42.8, "alu_pct": 33.9, "fma_cycles_pct": 27.2}))}
+# Per-kernel DRAM bytes (read + write) per launch and pipe use, from the cold-cache ncu
+# launch list and the per-kernel --set full captures of one KeySwitch of the workload
+# (profile_case with the tuned plan DPOB[km4,dnr4]-split; summaries and commands in
+# profiles/keyswitch_4_2e16_35_launches.md and keyswitch_4_2e16_35_kernels_ncu.md);
+# keyed by (workload, kernel name of the library's profiler), so a change of the
+# dominant kernel still finds its row. The split key multiply's two launches (P-limb
+# and Q-limb targets) are averaged, as the profiler averages them.
+NCU = {("c3", k): {"traffic": t, "plan": "DPOB[km4,dnr4]-split", **pipes} for k, t, pipes in (
+    ("intt_row(d)", 57200000, {"issue_pct": 40.4, "fmaheavy_pct": 37.4, "alu_pct": 33.4}),
+    ("intt_col(d)", 19100000, {"issue_pct": 39.9, "fmaheavy_pct": 40.9, "alu_pct": 32.5}),
+    ("modup_col", 41200000, {"issue_pct": 55.7, "fmaheavy_pct": 65.1, "alu_pct": 46.5}),
+    ("modup_row_keymult", 176350000, {"issue_pct": 53.4, "fmaheavy_pct": 54.5, "alu_pct": 36.9}),
+    ("intt_row(accP)", 18900000, {"issue_pct": 41.4, "fmaheavy_pct": 33.6, "alu_pct": 36.7}),
+    ("intt_col(accP)", 9500000, {"issue_pct": 40.3, "fmaheavy_pct": 35.7, "alu_pct": 35.7}),
+    ("moddown_col", 9600000, {"issue_pct": 57.7, "fmaheavy_pct": 65.4, "alu_pct": 45.0}),
+    ("moddown_row", 124300000, {"issue_pct": 49.7, "fmaheavy_pct": 49.0, "alu_pct": 44.2}))}
 
 
 def measured_alu(ks, stream):
