@@ -249,6 +249,21 @@ int ks_switch_host(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_
 int ks_switch_host_async(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
                          uint64_t *out_host, int variant, int chunks, void *stream);
 
+/* Host-buffer KeySwitch on a caller scratch, for host-buffer KeySwitches of one context
+ * in flight on several streams at once (each stream with its own scratch): the input is
+ * copied to the device and the result back by the copy engines (cudaMemcpyAsync on
+ * `stream`), around kernels on device buffers, so one call's transfers overlap another
+ * call's kernels. d_host ([L+1][N]) and out_host ([2][L+1][N]) must be pinned,
+ * device-mapped host memory (else KS_EINVAL); the result is in out_host once `stream`
+ * has passed this call, and d_host must stay unmodified until then. ws: device scratch
+ * of ks_host_workspace_size bytes (the workspace, then device copies of the input and
+ * of the result), 16-byte aligned, not used by another call in flight; smaller scratch
+ * returns KS_EINVAL and queues nothing. No synchronization, no graph cache. */
+int ks_host_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *bytes);
+int ks_switch_host_async_ws(ks_context *ctx, const uint64_t *d_host, const uint64_t *evk_dev,
+                            uint64_t *out_host, int variant, int chunks, void *ws_dev,
+                            size_t ws_bytes, void *stream);
+
 /* ks_switch without any device allocation, for callers that cannot allocate device
  * memory when they switch keys: callers held to a fixed allocator or memory-pool
  * budget that forbids new device allocations, and real-time or embedded integrations

@@ -928,6 +928,37 @@ int switch_launch_only(ks_context *c, const uint64_t *d, const uint64_t *evk, ui
 
 namespace {
 
+// ks_switch_host_async_ws: host-buffer KeySwitch on the caller's scratch (workspace,
+// device input, device output), with the transfers on the copy engines: the input is
+// copied in, the kernels run on device buffers, the result is copied out, all queued on
+// s. With calls on several streams the copies of one overlap the kernels of another
+// (GPU-side accesses to mapped host memory, as ks_switch_host_async does, would instead
+// occupy the first and last kernels for the whole transfer).
+int switch_host_ws(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
+                   int variant, int chunks, void *ws, size_t ws_bytes, cudaStream_t s) {
+  if (!c || !d_host || !evk || !out_host || !ws) return KS_EINVAL;
+  if (!aligned16(evk) || !aligned16(ws)) return KS_EALIGN;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
+  if (rc) return rc;
+  const size_t in_w = (size_t)c->nq * c->N;
+  if (ws_bytes < (pl.total + 3 * in_w) * 8) return KS_EINVAL;
+  // pinned host memory only: pageable copies would not be asynchronous
+  if (!host_mapped(d_host) || !host_mapped(out_host)) return KS_EINVAL;
+  u64 *din = (u64 *)ws + pl.total, *dout = din + in_w;
+  KS_TRY(cudaMemcpyAsync(din, d_host, in_w * 8, cudaMemcpyHostToDevice, s));
+  JobSet js = {};
+  js.n = 1;
+  js.j[0].ws = (u64 *)ws;
+  js.j[0].d = din;
+  js.j[0].evk = (const u64 *)evk;
+  js.j[0].out = dout;
+  rc = run_plan(c, pl, js, s);
+  if (rc) return rc;
+  KS_TRY(cudaMemcpyAsync(out_host, dout, 2 * in_w * 8, cudaMemcpyDeviceToHost, s));
+  return KS_OK;
+}
+
 // ks_switch_host / ks_switch_host_async. `async`: pinned buffers only, no final
 // synchronization, and direct (chained) launches where ks_switch uses them.
 int switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, uint64_t *out_host,
@@ -1004,6 +1035,22 @@ int ks_switch_host(ks_context *c, const uint64_t *d_host, const uint64_t *evk, u
 int ks_switch_host_async(ks_context *c, const uint64_t *d_host, const uint64_t *evk,
                          uint64_t *out_host, int variant, int chunks, void *stream) {
   return switch_host(c, d_host, evk, out_host, variant, chunks, (cudaStream_t)stream, true);
+}
+
+int ks_host_workspace_size(const ks_context *c, int variant, int chunks, size_t *bytes) {
+  if (!c || !bytes) return KS_EINVAL;
+  Plan pl;
+  int rc = make_plan(c, variant, chunks, &pl);
+  if (rc) return rc;
+  *bytes = (pl.total + 3 * (size_t)c->nq * c->N) * 8;
+  return KS_OK;
+}
+
+int ks_switch_host_async_ws(ks_context *c, const uint64_t *d_host, const uint64_t *evk,
+                            uint64_t *out_host, int variant, int chunks, void *ws,
+                            size_t ws_bytes, void *stream) {
+  return switch_host_ws(c, d_host, evk, out_host, variant, chunks, ws, ws_bytes,
+                        (cudaStream_t)stream);
 }
 
 int ks_keygen(ks_context *c, const int8_t *s_from, const int8_t *s_to, const uint64_t *a,

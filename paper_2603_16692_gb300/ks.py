@@ -92,7 +92,8 @@ SYMBOLS = ("ks_context_create", "ks_context_destroy", "ks_context_info", "ks_key
            "ks_mlp_forward", "ks_mlp_grad", "ks_mlp_train", "ks_batch_status",
            "ks_context_at_level", "ks_keygen_relin", "ks_keygen_galois",
            "ks_eval_workspace_size", "ks_hmul", "ks_hrot", "ks_calibrate",
-           "ks_switch_host_async", "ks_selector_load", "ks_select")
+           "ks_switch_host_async", "ks_selector_load", "ks_select", "ks_host_workspace_size",
+           "ks_switch_host_async_ws")
 
 
 def lib_path() -> str:
@@ -119,6 +120,8 @@ def load(build: bool = True):
         l.ks_switch.argtypes = [vp, vp, vp, vp, i, i, vp, sz, vp]
         l.ks_switch_host.argtypes = [vp, vp, vp, vp, i, i, vp]
         l.ks_switch_host_async.argtypes = [vp, vp, vp, vp, i, i, vp]
+        l.ks_host_workspace_size.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_size_t)]
+        l.ks_switch_host_async_ws.argtypes = [vp, vp, vp, vp, i, i, vp, ctypes.c_size_t, vp]
         l.ks_switch_batch.argtypes = [ctypes.POINTER(ks_job), i, i, vp]
         l.ks_tune.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp]
         l.ks_mlp_forward.argtypes = [vp, vp, i, vp, vp]
@@ -326,6 +329,39 @@ def ks_switch_host_async(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO
     tensors. The result is in out_host once the stream has passed the call."""
     _check(load().ks_switch_host_async(ctx, _host_ptr(d_host), _ptr(evk), _host_ptr(out_host),
                                        variant, chunks, _stream(stream)), "ks_switch_host_async")
+
+
+def ks_host_workspace_size(ctx: int, variant: int = KS_AUTO, chunks: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(load().ks_host_workspace_size(ctx, variant, chunks, ctypes.byref(n)),
+           "ks_host_workspace_size")
+    return n.value
+
+
+def ks_switch_host_async_ws(ctx: int, d_host, evk, out_host, workspace, variant: int = KS_AUTO,
+                            chunks: int = 0, stream=None):
+    """Host-buffer KeySwitch on a caller scratch (ks_host_workspace_size bytes), the
+    transfers on the copy engines; pinned host buffers."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().ks_switch_host_async_ws(ctx, _host_ptr(d_host), _ptr(evk), _host_ptr(out_host),
+                                          variant, chunks, _ptr(workspace), nbytes,
+                                          _stream(stream)), "ks_switch_host_async_ws")
+
+
+def prepare_switch_host_async_ws(ctx: int, d_host, evk, out_host, workspace,
+                                 variant: int = KS_AUTO, chunks: int = 0, stream=None):
+    """ks_switch_host_async_ws on fixed buffers as a zero-argument callable."""
+    f = load().ks_switch_host_async_ws
+    vp = ctypes.c_void_p
+    args = (vp(ctx), vp(_host_ptr(d_host)), vp(_ptr(evk)), vp(_host_ptr(out_host)),
+            ctypes.c_int(variant), ctypes.c_int(chunks), vp(_ptr(workspace)),
+            ctypes.c_size_t(workspace.numel() * workspace.element_size()), vp(_stream(stream)))
+
+    def call():
+        rc = f(*args)
+        if rc != KS_OK:
+            raise KSError(rc, "ks_switch_host_async_ws")
+    return call
 
 
 def prepare_switch_host_async(ctx: int, d_host, evk, out_host, variant: int = KS_AUTO,

@@ -84,6 +84,10 @@ def test_new_entry_points_reject_bad_arguments_on_host():
     assert lib.ks_selector_load(None) == ks.KS_EINVAL
     assert lib.ks_select(None, None, None, None) == ks.KS_EINVAL
     assert lib.ks_switch_host_async(None, None, None, None, 0, 0, None) == ks.KS_EINVAL
+    assert lib.ks_switch_host_async_ws(None, None, None, None, 0, 0, None, 0, None) == \
+        ks.KS_EINVAL
+    n = ctypes.c_size_t()
+    assert lib.ks_host_workspace_size(None, 0, 0, ctypes.byref(n)) == ks.KS_EINVAL
     sel = ks.ks_selector()
     for k in range(6):
         sel.x_std[k] = 1.0

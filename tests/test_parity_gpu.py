@@ -151,6 +151,50 @@ def test_host_entry_points_with_each_radix(cfg, radix):
         ctx.close()
 
 
+@pytest.mark.parametrize("plan", [ks.KS_DPOB | ks.KS_RADIX4,
+                                  ks.KS_DPOB | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4)
+                                  | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R4) | ks.KS_SPLIT_DOWN])
+@pytest.mark.parametrize("cfg", [W.C2, W.C3, (2, 12, 5)])
+def test_host_async_with_caller_scratch_on_three_streams(cfg, plan):
+    """ks_switch_host_async_ws: host-buffer KeySwitches in flight on three streams, each
+    with its own scratch (workspace + device copies of the input and result, moved by
+    the copy engines), nine calls over a ring of three pinned inputs and nine pinned
+    outputs; every result exact, and short scratch or pageable buffers refused."""
+    import torch
+    prm = W.make_params(*cfg)
+    cases = [oracle_case(cfg, seed) for seed in (0, 1, 2)]
+    evk_o = cases[0][6]
+    from oracle import oracle as O
+    want = [cases[0][7]] + [O.keyswitch(prm, c[5], evk_o) for c in cases[1:]]
+    ctx = ks.Context(prm)
+    try:
+        evk = dev(evk_o)
+        nbytes = ks.ks_host_workspace_size(ctx.h, plan, 0)
+        assert nbytes == ks.ks_workspace_size(ctx.h, plan, 0) + 3 * (prm.L + 1) * prm.N * 8
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        wss = [torch.empty(nbytes // 8, dtype=torch.uint64, device="cuda") for _ in streams]
+        d_hs = [torch.from_numpy(c[5].copy()).pin_memory() for c in cases]
+        outs = [torch.full((2, prm.L + 1, prm.N), 3, dtype=torch.uint64).pin_memory()
+                for _ in range(9)]
+        torch.cuda.synchronize()
+        for k in range(9):
+            ks.ks_switch_host_async_ws(ctx.h, d_hs[k % 3], evk, outs[k], wss[k % 3], plan, 0,
+                                       streams[k % 3])
+        torch.cuda.synchronize()
+        for k in range(9):
+            assert np.array_equal(outs[k].numpy(), want[k % 3]), f"call {k}"
+        small = torch.empty(nbytes // 8 - 2, dtype=torch.uint64, device="cuda")
+        with pytest.raises(ks.KSError) as ei:
+            ks.ks_switch_host_async_ws(ctx.h, d_hs[0], evk, outs[0], small, plan, 0)
+        assert ei.value.code == ks.KS_EINVAL
+        with pytest.raises(ks.KSError) as ei:  # pageable host memory is refused
+            ks.ks_switch_host_async_ws(ctx.h, torch.from_numpy(cases[0][5].copy()), evk,
+                                       outs[0], wss[0], plan, 0)
+        assert ei.value.code == ks.KS_EINVAL
+    finally:
+        ctx.close()
+
+
 def test_host_entry_point_and_workspace():
     import torch
     prm, s_from, s_to, a, e, d, evk_o, out_o = oracle_case(W.C2, 0)
