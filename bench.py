@@ -699,13 +699,30 @@ def main():
     host_us = min(host_us)
 
     # per-kernel event timing over a second pass of the same steps on one stream (kept out
-    # of `value`)
+    # of `value`). A split-ModDown plan runs its key multiply beside the P-limb ModDown
+    # chain, so its launch times overlap and do not add up to a step: the profiling
+    # pass runs the same plan unsplit (the same kernels, the key multiply in one
+    # launch), beside that plan's own one-stream step time, the reference of the scaling
+    # below.
     kprof = min(args.steps, 500)
+    pvar = variant & ~ks.KS_SPLIT_DOWN
+    pcalls = calls if pvar == variant else \
+        [ks.prepare_switch(ctx.h, d, evk, out, pvar, args.chunks, ws, stream) for d, evk, out in sets]
+    for k in range(10):
+        pcalls[k % ring]()
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for k in range(k1):
+        pcalls[k % ring]()
+    p1.record(stream)
+    barrier()
+    prof_step_ms = p0.elapsed_time(p1) / k1
     ks.ks_profile_begin()
     for k in range(kprof):
-        calls[k % ring]()
+        pcalls[k % ring]()
     stats = ks.ks_profile_end()
-    launches_per_step = sum(s["launches"] for s in stats) / kprof
+    launches_per_step = sum(s["launches"] for s in stats) / kprof + (pvar != variant)
 
     # end to end through the host-buffer entry points: a ring of pinned host inputs and
     # outputs; every step's input is read from and its result written to host memory
@@ -789,16 +806,18 @@ def main():
     sms = props.multi_processor_count
     # Per-kernel durations: the profiling pass brackets every launch with events, which
     # breaks the programmatic-dependent-launch overlap of consecutive kernels, so their
-    # sum exceeds the timed step; each kernel's event time is scaled by step / sum.
+    # sum exceeds the one-stream step of the profiled plan; each kernel's event time is
+    # scaled by (that step / the sum), so the kernels add up to the step.
     step_ms = el_ms / args.steps
     ev_sum = sum(s["ms"] for s in stats) / kprof
-    scale = one_stream_ms / ev_sum
+    scale = prof_step_ms / ev_sum
     dom = max(stats, key=lambda s: s["ms"])
     per_launch_ms = dom["ms"] / dom["launches"] * scale
     bytes_l = dom["bytes"] / dom["launches"]
     hbm_ach = bytes_l / (per_launch_ms / 1e3) / 1e9
     bf, mac = measured_alu(ks, stream)
     alu = alu_roofline(dom, per_launch_ms, bf, mac)
+    alu_ev = alu_roofline(dom, dom["ms"] / dom["launches"], bf, mac)
     # the recipe's unit counts for context: SMs x 64 IMAD lanes x max clock / 10 IMAD per
     # 64-bit Shoup product
     derived = sms * 64 * sm_mhz * 1e6 / 10 / 1e9
@@ -810,8 +829,12 @@ def main():
                                f"({bf / 1e12:.3f} T/s) and 128-bit MAC ({mac / 1e12:.3f} T "
                                f"terms/s) on all {sms} SMs; MAC terms counted at the ratio",
                 "t_ceil_ms": alu["t_ceil_ms"], "duration_ms": per_launch_ms,
-                "duration_source": f"event time x {scale:.3f} (one-stream step / sum of "
-                                   "event-bracketed launches)",
+                "duration_source": f"event time x {scale:.3f} (one-stream step of the "
+                                   f"profiled plan {ks.variant_name(pvar, args.chunks)}, "
+                                   f"{prof_step_ms:.4f} ms, / sum of its event-bracketed "
+                                   "launches)",
+                "event_ms": dom["ms"] / dom["launches"],
+                "event_frac": alu_ev["frac"],
                 "share": dom["ms"] / sum(s["ms"] for s in stats),
                 "macs_per_launch": alu["macs_per_launch"],
                 "shoup_per_launch": alu["shoup_per_launch"],

@@ -339,7 +339,7 @@ int ks_batch_status(void *stream);
  * launch set); then, for N >= 2^13, refines the winner's schedule one coordinate at a
  * time: each stage's radix (KS_STAGE_RADIX), each column pass's tile (KS_COLALT_*) and,
  * for DPOB, the split ModDown (KS_SPLIT_DOWN), a change kept when the KeySwitch gets
- * more than 1% faster. Stores the result as the
+ * more than 1.5% faster (best of six timings each). Stores the result as the
  * context's KS_AUTO plan and writes it to *variant / *chunks. Writes the switched
  * result to out_dev. Synchronizes `stream`; allocates and frees its own scratch. */
 int ks_tune(ks_context *ctx, const uint64_t *d_dev, const uint64_t *evk_dev, uint64_t *out_dev,

@@ -1365,8 +1365,8 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
   const bool prof = g_prof.on;
   g_prof.on = false;
   int rc = KS_OK;
-  // best of three timed launch sets (after one untimed) of plan (v, ch), ms
-  auto time_plan = [&](int v, int ch) -> float {
+  // best of `reps` timed launch sets (after one untimed) of plan (v, ch), ms
+  auto time_plan = [&](int v, int ch, int reps) -> float {
     Plan pl;
     if (make_plan(c, v, ch, &pl) != KS_OK) return 1e30f;
     JobSet js = {};
@@ -1379,7 +1379,7 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
       js.j[q].ws = (u64 *)base;
     }
     float ms_min = 1e30f;
-    for (int rep = 0; rep < 4 && rc == KS_OK; ++rep) {
+    for (int rep = 0; rep <= reps && rc == KS_OK; ++rep) {
       cudaEventRecord(e0, s);
       rc = run_plan(c, pl, js, s);
       cudaEventRecord(e1, s);
@@ -1396,7 +1396,7 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
   for (auto &b : bases)
     for (int ri = 0; ri < 3 && rc == KS_OK; ++ri) {
       const int v = b[0] | radix[ri];
-      const float ms = time_plan(v, b[1]);
+      const float ms = time_plan(v, b[1], 3);
       if (ms < best) {
         best = ms;
         best_v = v;
@@ -1404,9 +1404,11 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
       }
     }
   // 2) the schedule of the winner, one coordinate at a time: each stage's radix, then
-  // the column tile (a change is kept only if the whole KeySwitch gets faster by more
-  // than the timing noise, 1%)
+  // each column pass's tile, then the split ModDown; the winner is re-timed with the
+  // same number of repetitions, and a change is kept only if the whole KeySwitch gets
+  // faster by more than the timing noise (1.5%)
   if (rc == KS_OK && c->loga > 0) {
+    best = time_plan(best_v, best_c, 6);
     const int plan_code3 = (best_v & KS_RADIX4) ? KS_R4 : (best_v & KS_RADIX16) ? KS_R16 : KS_R8;
     for (int st = 0; st < ST_COUNT && rc == KS_OK; ++st)
       for (int code = KS_R4; code <= KS_R16 && rc == KS_OK; ++code) {
@@ -1414,8 +1416,8 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
         const int cur = (best_v >> (KS_STAGE_SHIFT + 2 * st)) & 3;
         if (cur == code) continue;
         const int v = (best_v & ~KS_STAGE_RADIX(st, 3)) | KS_STAGE_RADIX(st, code);
-        const float ms = time_plan(v, best_c);
-        if (ms < 0.99f * best) {
+        const float ms = time_plan(v, best_c, 6);
+        if (ms < 0.985f * best) {
           best = ms;
           best_v = v;
         }
@@ -1423,8 +1425,8 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
     for (int bit : {KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC, KS_SPLIT_DOWN}) {
       if (rc != KS_OK) break;
       if (bit == KS_SPLIT_DOWN && ((best_v & 0xff) != KS_DPOB || (best_v & KS_UNFUSED))) continue;
-      const float ms = time_plan(best_v ^ bit, best_c);
-      if (ms < 0.99f * best) {
+      const float ms = time_plan(best_v ^ bit, best_c, 6);
+      if (ms < 0.985f * best) {
         best = ms;
         best_v ^= bit;
       }
