@@ -118,6 +118,59 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Bulk copies by the TMA unit (cp.async.bulk, global -> shared, one instruction for a
+// whole contiguous tile) completing on a shared-memory mbarrier: one thread arms the
+// barrier with the byte count and issues the copy; every thread then waits on the
+// barrier's phase. Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void mbar_init(u64 *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64 *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// The slow path of mbar_wait, kept out of line (it holds the kernel's registers only
+// while it runs): polls at most ~1 s of %globaltimer and 2^24 times.
+static __device__ __noinline__ bool mbar_wait_slow(u64 *bar, unsigned phase) {
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if (global_ns() - t0 > 1000000000ull) break;
+  }
+  return false;
+}
+// Waits for phase `phase` of the barrier; false if it gave up (the caller records the
+// error and carries on without the data).
+__device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned phase) {
+  return mbar_try_wait(bar, phase) || mbar_wait_slow(bar, phase);
+}
+
 // Programmatic dependent launch. Every KeySwitch kernel lets the next kernel of its
 // stream launch once all its CTAs reach their end (pdl_trigger), and waits for the
 // previous kernel to complete, with its memory visible, before it reads or writes any

@@ -189,12 +189,33 @@ __device__ __forceinline__ void store_cols(u64 *dst, const u64 *s, int c0) {
   }
 }
 
-// Stage n twiddle pairs into shared memory.
-template <class GT>
+// Stage n twiddle pairs (a contiguous slab of the table) into shared memory with one
+// TMA bulk copy: thread 0 arms the CTA's barrier `bar` and issues the copy, which then
+// lands while the kernel waits for its predecessor and loads its data tile. Every thread
+// calls tw_ready before the first round that reads the twiddles, after a barrier that
+// follows stage_tw (so the barrier's initialisation is visible).
+// TMA = false (the persistent kernel, whose CTAs run many tiles): every thread copies
+// its share with ordinary loads instead, and tw_ready is a no-op (the barrier before
+// the first round orders the stores).
+template <class GT, bool TMA = true>
 __device__ __forceinline__ void stage_tw(ulonglong2 *tws, const ulonglong2 *__restrict__ src,
-                                         int n) {
-  const u64 pol = l2_keep();
-  for (int k = threadIdx.x; k < n; k += GT::NT) tws[k] = ldg_pol(src + k, pol);
+                                         int n, u64 *bar) {
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_expect_tx(bar, (unsigned)n * 16);
+      bulk_g2s(tws, src, (unsigned)n * 16, bar);
+    }
+  } else {
+    const u64 pol = l2_keep();
+    for (int k = threadIdx.x; k < n; k += GT::NT) tws[k] = ldg_pol(src + k, pol);
+  }
+}
+// Wait for the twiddle slab; a wait that gives up records it in the context's error
+// word (ks_sync_status then returns KS_ETIMEOUT) and carries on.
+template <bool TMA = true>
+__device__ __forceinline__ void tw_ready(u64 *bar, int *err) {
+  if (TMA && !mbar_wait(bar, 0)) atomicExch(err, 1);
 }
 
 // Column-pass twiddles of a prime: the first N1 entries of its column table.
@@ -370,7 +391,7 @@ __device__ __forceinline__ InttSet intt_set(const KArgs &a, const JobPtr &jp, co
 // polynomials in one CTA (shared twiddles), or only polynomial `only_o` when it is
 // >= 0. With a single pass (N1 == 1) it also applies the per-limb scale (canonical
 // output).
-template <int LOGN, int RL>
+template <int LOGN, int RL, bool TMA = true>
 __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              int which, int bx, int by, unsigned char *raw,
                                              int only_o = -1) {
@@ -383,7 +404,9 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
   const u64 m = a.tab.mod[prime].m, mu = a.tab.mod[prime].mu;
   const size_t N = a.N;
   // inverse twiddles: the forward slab of the mirrored row tile (see ks_ntt.cuh)
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, prime, GT::N1 / GT::GR - 1 - blk), GT::TWR);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, row_table<GT>(a.tab.twr_f, prime, GT::N1 / GT::GR - 1 - blk), GT::TWR,
+               &twbar);
   // Reading the input from host memory (`dsrc`), this pass writes only v and the device
   // copy of d, which no kernel of the previous operation on the stream reads once its
   // last kernel runs: it starts without waiting, so its host reads overlap that kernel's
@@ -399,6 +422,7 @@ __device__ __forceinline__ void inv_row_body(const KArgs &a, const JobPtr &jp, c
     else
       load_rows<GT>(sm, is.src + ((size_t)o * is.src_outer + ii) * N, r0);
     __syncthreads();
+    tw_ready<TMA>(&twbar, a.tab.err);
     tile_inv<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
     u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * N;
     if (GT::LOGA == 0) {
@@ -442,7 +466,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
 
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
 // per-limb scale; `only_o` as in the row pass.
-template <int LOGN, int RL, int CA>
+template <int LOGN, int RL, int CA, bool TMA = true>
 __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              int which, int bx, int by, unsigned char *raw,
                                              int only_o = -1) {
@@ -453,7 +477,8 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
   const int ii = by, prime = is.prime_base + ii;
   const int c0 = bx * GT::GC;
   const u64 m = a.tab.mod[prime].m;
-  stage_tw<GT>(tws, col_table<GT>(a.tab.twc_i, prime), GT::TWC);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, col_table<GT>(a.tab.twc_i, prime), GT::TWC, &twbar);
   pdl_wait();
   const ulonglong2 sc = is.scale[ii];
   const int o0 = only_o < 0 ? 0 : only_o, o1 = only_o < 0 ? is.outer : only_o + 1;
@@ -461,6 +486,7 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
     u64 *d = is.dst + ((size_t)o * is.dst_outer + ii) * (size_t)a.N;
     load_cols<GT>(sm, d, c0);
     __syncthreads();
+    tw_ready<TMA>(&twbar, a.tab.err);
     tile_inv<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false, RL>(sm, tws, m);
     constexpr int TILE = GT::N1 * GT::GC;
 #pragma unroll
@@ -505,7 +531,7 @@ __device__ __forceinline__ void fwd_bufs(const JobPtr &jp, const WsOff &wo, int 
 
 // Forward NTT, column pass (global stages 0 .. logN1-1) with a tile producer; the
 // lazy ([0, 4m)) result goes to the output buffer's slot.
-template <int LOGN, int RL, int PRO, int CA>
+template <int LOGN, int RL, int PRO, int CA, bool TMA = true>
 __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int buf, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
@@ -518,10 +544,12 @@ __device__ __forceinline__ void fwd_col_body(const KArgs &a, const JobPtr &jp, c
   const uint32_t w = decode(a, tk, by);
   const int t = task_limb(w);
   const int c0 = bx * GT::GC;
-  stage_tw<GT>(tws, col_table<GT>(a.tab.twc_f, t), GT::TWC);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, col_table<GT>(a.tab.twc_f, t), GT::TWC, &twbar);
   pdl_wait();
   produce<GT, PRO, true>(a, sm, cst, w, src, dst, c0);
   __syncthreads();
+  tw_ready<TMA>(&twbar, a.tab.err);
   tile_fwd<GT::LOGA, GT::LOGGC, GT::PC, GT::NT, false, RL>(sm, tws, a.tab.mod[t].m);
   store_cols<GT>(dst + (size_t)task_slot(w) * a.N, sm, c0);
 }
@@ -546,6 +574,7 @@ template <int LOGN, int RL>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
     k_fwd_row_store(KArgs a, JobSet js, WsOff wo, Tasks tk, int buf) {
   using GT = GeoT<LOGN, RL, 1>;
+  constexpr bool TMA = true;
   extern __shared__ __align__(16) unsigned char raw[];
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, false>(raw);
@@ -555,11 +584,13 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
   const uint32_t w = decode(a, tk, blockIdx.y);
   const int t = task_limb(w), blk = blockIdx.x, r0 = blk * GT::GR;
   const u64 m = a.tab.mod[t].m;
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR, &twbar);
   pdl_wait();
   u64 *b = dst + (size_t)task_slot(w) * a.N;
   load_rows<GT>(sm, b, r0);
   __syncthreads();
+  tw_ready<TMA>(&twbar, a.tab.err);
   tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
   store_rows<GT>(b, sm, r0, m, a.tab.mod[t].mu);
   pdl_trigger();  // the next kernel may launch once every CTA is here
@@ -580,7 +611,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
 // per output word (needs (bound of ext) * (digits) * m < 2^64, checked per CTA; the
 // context guarantees digits * m < 2^64 for canonical ext); with more elements per
 // thread (register budget) each product is reduced and the residues summed lazily.
-template <int LOGN, int RL, int PRO>
+template <int LOGN, int RL, int PRO, bool TMA = true>
 __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
@@ -610,7 +641,8 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
       prefetch_l2(tmp + (size_t)(j * tk.sm.sj + t * tk.sm.st + tk.sm.base) * N + off0, TB);
   };
   prefetch_digit(tk.j0);
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR, &twbar);
   pdl_wait();
   const u64 pol = l2_stream();
   const bool fast = mi.m < kFastModulus;
@@ -667,6 +699,7 @@ __device__ __forceinline__ void keymult_body(const KArgs &a, const JobPtr &jp, c
       else
         produce<GT, PRO_LOAD, false>(a, sm, cst, pack_task(t, j, slot), v, tmp, r0);
       __syncthreads();
+      tw_ready<TMA>(&twbar, a.tab.err);
       tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, mi.m);
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
@@ -722,15 +755,17 @@ constexpr bool ROW_PIPE = geo_loga(LOGN) != 0 && RL == 2;
 
 // The key multiply of keymult_body for N >= 2^13, software-pipelined over the digits:
 // while digit j's ext tile is transformed and multiplied, the copies of digit j+1's
-// tile (the ModUp intermediate, or d_t on the digit's own limbs) and of its two key
-// tiles are in flight (cp.async into the other half of double buffers). Same
-// arithmetic, same bounds and the same result as keymult_body.
+// tile (the ModUp intermediate, or d_t on the digit's own limbs: cp.async into the odd
+// pitch) and of its two key tiles (TMA bulk copies on a barrier) are in flight into the
+// other half of double buffers. Same arithmetic, same bounds and the same result as
+// keymult_body.
 template <int LOGN, int RL>
 __device__ __forceinline__ void keymult_pipe_body(const KArgs &a, const JobPtr &jp,
                                                   const WsOff &wo, const Tasks &tk, int bx,
                                                   int by, unsigned char *raw) {
   using GT = GeoT<LOGN, RL, 1>;
   using SM = KmSmem<GT>;
+  constexpr bool TMA = true;
   constexpr int EPT = GT::EPT, TILE = GT::TILE, NT = GT::NT;
   constexpr bool WIDE = EPT <= 4;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
@@ -747,17 +782,17 @@ __device__ __forceinline__ void keymult_pipe_body(const KArgs &a, const JobPtr &
     const int lo = j * a.alpha;
     return t >= lo && t < min(lo + a.alpha, a.nq);
   };
+  // key tiles: two contiguous TILE-word tiles per digit, one TMA bulk copy each, on the
+  // buffer's barrier (use k of buffer b completes phase k & 1)
+  __shared__ u64 keybar[2];
   auto issue_keys = [&](int j, int b) {
+    if (threadIdx.x != 0) return;
     const u64 *e0 = jp.evk + evk_off(a, j, 0, t) + off0;
     const u64 *e1 = jp.evk + evk_off(a, j, 1, t) + off0;
     u64 *k0 = keys + b * SM::KEYW;
-#pragma unroll
-    for (int it = 0; it < (TILE / 2 + NT - 1) / NT; ++it) {
-      const int q = threadIdx.x + it * NT;
-      if ((TILE / 2) % NT != 0 && q >= TILE / 2) break;
-      cp_async16(k0 + 2 * q, e0 + 2 * q);
-      cp_async16(k0 + TILE + 2 * q, e1 + 2 * q);
-    }
+    mbar_expect_tx(&keybar[b], 2 * TILE * 8);
+    bulk_g2s(k0, e0, TILE * 8, &keybar[b]);
+    bulk_g2s(k0 + TILE, e1, TILE * 8, &keybar[b]);
   };
   auto issue_tile = [&](int j, int b) {
     const u64 *src = own(j) ? jp.d + (size_t)t * N + off0
@@ -772,8 +807,13 @@ __device__ __forceinline__ void keymult_pipe_body(const KArgs &a, const JobPtr &
   };
   // the key tiles are inputs of the operation (no kernel of the chain writes them):
   // their first copies start before the wait for the previous kernel
+  if (threadIdx.x == 0) {
+    mbar_init(&keybar[0], 1);
+    mbar_init(&keybar[1], 1);
+  }
   issue_keys(tk.j0, 0);
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, row_table<GT>(a.tab.twr_f, t, blk), GT::TWR, &twbar);
   pdl_wait();
   issue_tile(tk.j0, 0);
   cp_async_commit();
@@ -800,7 +840,11 @@ __device__ __forceinline__ void keymult_pipe_body(const KArgs &a, const JobPtr &
     u64 *sm = tiles + b * SM::TILEW;
     const u64 *k0 = keys + b * SM::KEYW;
     const bool ow = own(j);
-    if (!ow) tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, mi.m);
+    if (!ow) {
+      tw_ready<TMA>(&twbar, a.tab.err);
+      tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, mi.m);
+    }
+    if (!mbar_wait(&keybar[b], ((j - tk.j0) >> 1) & 1)) atomicExch(a.tab.err, 1);
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int e = threadIdx.x + k * NT;
@@ -875,7 +919,7 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT,
 // ModDown row pass fused with the final scaling, both polynomials c = 0, 1 of
 // limb i (TASK_DOWN1) in one CTA (shared twiddles):
 //   out_c[i] = (acc_c[i] - NTT(BConv_{P->Q}(c))[i]) * P^-1 mod q_i.
-template <int LOGN, int RL, int PRO>
+template <int LOGN, int RL, int PRO, bool TMA = true>
 __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              const Tasks &tk, int bx, int by,
                                              unsigned char *raw, u64 *cst) {
@@ -896,7 +940,8 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
   const u64 m2 = 2 * m, zb = fast ? kFwdLazy * m : m2;
   if (threadIdx.x == 0)
     for (int c = 0; c < 2; ++c) prefetch_l2(acc + ((size_t)c * a.qp + i) * N + off0, GT::TILE * 8);
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR, &twbar);
   pdl_wait();
   for (int c = 0; c < 2; ++c) {
     const uint32_t wc = pack_task(i, c, task_slot(w) + c * tk.span);
@@ -905,6 +950,7 @@ __device__ __forceinline__ void moddown_body(const KArgs &a, const JobPtr &jp, c
     else
       produce<GT, PRO_LOAD, false>(a, sm, cst, wc, vp, tmp2, r0);
     __syncthreads();
+    tw_ready<TMA>(&twbar, a.tab.err);
     tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
     const u64 *ac = acc + ((size_t)c * a.qp + i) * N + off0;
     const size_t ob = ((size_t)c * a.nq + i) * N + off0;
@@ -942,15 +988,17 @@ struct MdSmem {
   static constexpr int BYTES = TW + 2 * TILEW * 8 + 2 * GT::TILE * 8;
 };
 
-// moddown_body for N >= 2^13 with both polynomials' input tiles and accumulator tiles
-// copied into shared memory at the start (cp.async): the copies of c = 1 and of the
-// accumulators are in flight while c = 0 is transformed. Same arithmetic and result.
+// moddown_body for N >= 2^13 with both polynomials' input tiles (cp.async into the odd
+// pitch) and accumulator tiles (TMA bulk copies on a barrier) copied into shared memory
+// at the start: the copies of c = 1 and of the accumulators are in flight while c = 0
+// is transformed. Same arithmetic and result.
 template <int LOGN, int RL>
 __device__ __forceinline__ void moddown_pipe_body(const KArgs &a, const JobPtr &jp,
                                                   const WsOff &wo, const Tasks &tk, int bx,
                                                   int by, unsigned char *raw) {
   using GT = GeoT<LOGN, RL, 1>;
   using SM = MdSmem<GT>;
+  constexpr bool TMA = true;
   constexpr int EPT = GT::EPT, TILE = GT::TILE, NT = GT::NT;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *tiles = reinterpret_cast<u64 *>(raw + SM::TW);
@@ -965,24 +1013,26 @@ __device__ __forceinline__ void moddown_pipe_body(const KArgs &a, const JobPtr &
   // the NTT output enters the scaling lazy, as in moddown_body
   const bool fast = m < kFastModulus;
   const u64 m2 = 2 * m, zb = fast ? kFwdLazy * m : m2;
-  stage_tw<GT>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR);
+  __shared__ u64 twbar;
+  stage_tw<GT, TMA>(tws, row_table<GT>(a.tab.twr_f, i, blk), GT::TWR, &twbar);
   pdl_wait();
+  // the accumulator tiles (contiguous): one TMA bulk copy each, on one barrier
+  __shared__ u64 accbar;
+  if (threadIdx.x == 0) {
+    mbar_init(&accbar, 1);
+    mbar_expect_tx(&accbar, 2 * TILE * 8);
+    for (int c = 0; c < 2; ++c)
+      bulk_g2s(accs + c * TILE, acc + ((size_t)c * a.qp + i) * N + off0, TILE * 8, &accbar);
+  }
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const u64 *src = tmp2 + (size_t)(task_slot(w) + c * tk.span) * N + off0;
-    const u64 *ac = acc + ((size_t)c * a.qp + i) * N + off0;
-    u64 *st = tiles + c * SM::TILEW, *sa = accs + c * TILE;
+    u64 *st = tiles + c * SM::TILEW;
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int e = threadIdx.x + k * NT;
       if (TILE % NT != 0 && e >= TILE) break;
       cp_async8(st + (e & (GT::N2 - 1)) * GT::PR + (e >> GT::LOGB), src + e);
-    }
-#pragma unroll
-    for (int it = 0; it < (TILE / 2 + NT - 1) / NT; ++it) {
-      const int q = threadIdx.x + it * NT;
-      if ((TILE / 2) % NT != 0 && q >= TILE / 2) break;
-      cp_async16(sa + 2 * q, ac + 2 * q);
     }
     cp_async_commit();
   }
@@ -995,7 +1045,9 @@ __device__ __forceinline__ void moddown_pipe_body(const KArgs &a, const JobPtr &
     __syncthreads();
     u64 *sm = tiles + c * SM::TILEW;
     const u64 *sa = accs + c * TILE;
+    tw_ready<TMA>(&twbar, a.tab.err);
     tile_fwd<GT::LOGB, GT::LOGGR, GT::PR, GT::NT, true, RL>(sm, tws, m);
+    if (c == 0 && !mbar_wait(&accbar, 0)) atomicExch(a.tab.err, 1);
     const size_t ob = ((size_t)c * a.nq + i) * N + off0;
     u64 *o = jp.out + ob;
     const bool add = (jp.addmask >> c) & 1;

@@ -124,17 +124,17 @@ template <int LOGN, int STAGE>
 __device__ __forceinline__ void stage_fn(const PJob &J, int which, int bx, int by,
                                       unsigned char *raw, u64 *cst) {
   constexpr int RC = prl_col(LOGN), RR = prl_row(LOGN);
-  if constexpr (STAGE == 0) kern::inv_row_body<LOGN, RR>(J.a, J.jp, J.wo, which, bx, by, raw);
-  if constexpr (STAGE == 1) kern::inv_col_body<LOGN, RC, 0>(J.a, J.jp, J.wo, which, bx, by, raw);
+  if constexpr (STAGE == 0) kern::inv_row_body<LOGN, RR, false>(J.a, J.jp, J.wo, which, bx, by, raw);
+  if constexpr (STAGE == 1) kern::inv_col_body<LOGN, RC, 0, false>(J.a, J.jp, J.wo, which, bx, by, raw);
   if constexpr (STAGE == 2)
-    kern::fwd_col_body<LOGN, RC, kern::PRO_UP, 0>(J.a, J.jp, J.wo, J.up, BUF_TMP, bx, by, raw, cst);
+    kern::fwd_col_body<LOGN, RC, kern::PRO_UP, 0, false>(J.a, J.jp, J.wo, J.up, BUF_TMP, bx, by, raw, cst);
   if constexpr (STAGE == 3)
-    kern::keymult_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.tg, bx, by, raw, cst);
+    kern::keymult_body<LOGN, RR, kern::PRO_LOAD, false>(J.a, J.jp, J.wo, J.tg, bx, by, raw, cst);
   if constexpr (STAGE == 6)
-    kern::fwd_col_body<LOGN, RC, kern::PRO_DOWN, 0>(J.a, J.jp, J.wo, J.dn, BUF_TMP2, bx, by, raw,
+    kern::fwd_col_body<LOGN, RC, kern::PRO_DOWN, 0, false>(J.a, J.jp, J.wo, J.dn, BUF_TMP2, bx, by, raw,
                                                 cst);
   if constexpr (STAGE == 7)
-    kern::moddown_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.d1, bx, by, raw, cst);
+    kern::moddown_body<LOGN, RR, kern::PRO_LOAD, false>(J.a, J.jp, J.wo, J.d1, bx, by, raw, cst);
 }
 
 template <int LOGN>
