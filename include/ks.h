@@ -93,6 +93,14 @@ extern "C" {
  * the ModDown BConv pass (they need only the P-limb accumulators); the two join before
  * the last ModDown pass. Same result bits; calls on one context serialize this fork. */
 #define KS_SPLIT_DOWN 0x20000000
+/* OR-ed into a fused variant: the ModUp and ModDown basis conversions (Sec. II-A) run on
+ * the tensor cores (tcgen05): both operands split into bytes, exact bf16 x bf16 -> fp32
+ * products summed below 2^23, recombined into the exact 128-bit sum and reduced once,
+ * fused with the first forward NTT pass (the inverse column passes write the bytes of
+ * their output instead of the output). Same result bits as the integer path. Effective
+ * on contexts with ks_info.tc = 1 (2^13 <= N <= 2^17, 2 <= alpha <= 15); ignored
+ * otherwise and by unfused plans. */
+#define KS_BCONV_TC 0x800
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -119,6 +127,7 @@ typedef struct {
   int top_L;          /* level of the context whose keys it reads (= L unless a level view) */
   int selected_variant; /* plan picked by ks_select (0 = none) */
   int selected_chunks;
+  int tc;               /* 1: KS_BCONV_TC is effective on this context */
 } ks_info;
 
 typedef struct ks_context ks_context;

@@ -36,10 +36,11 @@ struct Plan {
   int ca[ST_COUNT];   // per stage: 1 = alternative column tile (stages with column passes)
   int code;      // every variant bit that changes the launches (graph-cache key)
   bool split;    // KS_SPLIT_DOWN in effect (fused DPOB, two-pass N)
+  bool tc;       // KS_BCONV_TC in effect (fused, context with a tensor-core path)
   int chunks;    // phase-1 and phase-2 group counts (1 for OB)
   int clen;      // max QP-limbs per phase-1 group
   int clq;       // max Q-limbs per phase-2 group
-  size_t off_v, off_tmp, off_acc, off_vp, off_tmp2, total;  // in u64 words
+  size_t off_v, off_tmp, off_acc, off_vp, off_tmp2, off_pv, off_ppv, total;  // u64 words
   size_t tmp_slots, tmp2_slots;
 };
 
@@ -48,8 +49,8 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 constexpr int kSchedMask = 0x3ff << KS_STAGE_SHIFT;
 
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
-  if (variant &
-      ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT | KS_SPLIT_DOWN))
+  if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT |
+                  KS_SPLIT_DOWN | KS_BCONV_TC))
     return KS_EINVAL;
   if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
@@ -86,6 +87,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   pl->ca[ST_DNC] = (variant & KS_COLALT_DNC) ? 1 : 0;
   pl->code = variant & ~0xff;
   pl->split = (variant & KS_SPLIT_DOWN) && base == KS_DPOB && !pl->unfused && c->loga > 0;
+  pl->tc = (variant & KS_BCONV_TC) && !pl->unfused && c->tc_ap > 0;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
   pl->clq = (c->nq + chunks - 1) / chunks;
@@ -111,6 +113,9 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   pl->off_acc = take((size_t)2 * c->qp * N);
   pl->off_vp = take((size_t)2 * c->np * N);
   pl->off_tmp2 = take(pl->tmp2_slots * N);
+  // the bf16 bytes of v and vp (16 bytes per residue) for the tensor-core conversions
+  pl->off_pv = pl->tc ? take((size_t)2 * c->nq * N) : 0;
+  pl->off_ppv = pl->tc ? take((size_t)4 * c->np * N) : 0;
   pl->total = off;
   return KS_OK;
 }
@@ -195,6 +200,8 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
   wo.acc = (long long)pl.off_acc;
   wo.vp = (long long)pl.off_vp;
   wo.tmp2 = (long long)pl.off_tmp2;
+  wo.pv = (long long)pl.off_pv;
+  wo.ppv = (long long)pl.off_ppv;
   const bool dp = pl.base == KS_DPOB || pl.base == KS_DPOC;
   const bool oc = pl.base == KS_DSOC || pl.base == KS_DPOC;
   auto dsize = [&](int j) { return std::min(c->nq, (j + 1) * c->alpha) - j * c->alpha; };
@@ -205,8 +212,9 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
     KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), 0, s,
                  [&] { return L.intt_row(c, js, wo, 0, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(d)", 2 * nl * W, nl * (BF_A + NJ), 0, s,
-                   [&] { return L.intt_col(c, js, wo, 0, s); }));
+      KS_TRY(timed("intt_col(d)", (pl.tc ? 3 : 2) * nl * W, nl * (BF_A + NJ), 0, s, [&] {
+        return pl.tc ? L.intt_col_tc(c, js, wo, 0, s) : L.intt_col(c, js, wo, 0, s);
+      }));
   }
 
   // Phase 1: ModUp (BConv + NTT) and key multiply, per output group.
@@ -243,7 +251,10 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
       if (!pl.unfused) {
         if (!single)
           KS_TRY(timed("modup_col", nconv * W + src_b, conv_ops + nconv * BF_A, conv_ops, s,
-                       [&] { return LU.modup_col(c, js, wo, up, s); }));
+                       [&] {
+                         return pl.tc ? launch_bconv_tc(c, js, wo, up, true, s)
+                                      : LU.modup_col(c, js, wo, up, s);
+                       }));
       } else {
         KS_TRY(timed("bconv_up", nconv * W + src_b, conv_ops, conv_ops, s,
                      [&] { return launch_bconv_up(c, js, wo, up, nconv, s); }));
@@ -291,8 +302,9 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
     KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), 0, s,
                  [&] { return L.intt_row(c, js, wo, 1, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(accP)", 2 * nl * W, nl * (BF_A + NJ), 0, s,
-                   [&] { return L.intt_col(c, js, wo, 1, s); }));
+      KS_TRY(timed("intt_col(accP)", (pl.tc ? 3 : 2) * nl * W, nl * (BF_A + NJ), 0, s, [&] {
+        return pl.tc ? L.intt_col_tc(c, js, wo, 1, s) : L.intt_col(c, js, wo, 1, s);
+      }));
   }
 
   // Phase 2: ModDown (BConv P->Q + NTT) and (acc - .) * P^-1, per output group.
@@ -310,8 +322,10 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
     const double n = 2.0 * (i1 - i0), vp_b = 2.0 * c->np * W, conv = n * NJ * (c->np + 1.0);
     if (!pl.unfused) {
       if (!single)
-        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s,
-                     [&] { return LDC.moddown_col(c, js, wo, dn, s); }));
+        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s, [&] {
+          return pl.tc ? launch_bconv_tc(c, js, wo, dn, false, s)
+                       : LDC.moddown_col(c, js, wo, dn, s);
+        }));
       const double b = 3 * n * W + (single ? vp_b - n * W : 0);
       const double o = n * (BF_B + NJ) + (single ? conv : 0);
       if (split) KS_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -486,6 +500,18 @@ int create_context(int dnum, int logn, int L, const u64 *q, const u64 *p, int al
   // basis-conversion sums: run * max_source * m < m 2^64
   c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
   c->run_down = (int)std::min<u64>(1 << 20, (~(u64)0) / maxp);
+  // Tensor-core basis conversions (ks_tc.cu): two-pass N, 2..15 sources per set (the
+  // fp32 sums of byte products stay exact below 2^23), one REDC per sum, at most
+  // kTcMaxSets digits.
+  if (c->loga > 0 && logn <= 17 && alpha >= 2 && alpha <= 15 && beta <= ks::kTcMaxSets &&
+      c->run_up >= alpha && c->run_down >= alpha) {
+    c->tc_ap = (alpha + 2) & ~1;  // alpha + 1 slots (the last adds 2^23), rounded to even
+    c->tc_tplog = c->tc_ap <= 10 ? 10 : 9;
+    if (ks::tc_prepare(logn) != cudaSuccess) {
+      cudaGetLastError();
+      c->tc_ap = c->tc_tplog = 0;
+    }
+  }
   cudaGetDevice(&c->device);
   int rc = ks::build_tables(c);
   if (rc) {
@@ -865,6 +891,7 @@ int ks_context_info(const ks_context *c, ks_info *info) {
   info->tuned_ms = c->tuned_ms;
   info->selected_variant = c->sel_variant;
   info->selected_chunks = c->sel_chunks;
+  info->tc = c->tc_ap > 0 ? 1 : 0;
   return KS_OK;
 }
 
@@ -1351,7 +1378,8 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
   for (auto &b : bases)
     for (int r : radix) {
       Plan pl;
-      if (make_plan(c, b[0] | r, b[1], &pl) == KS_OK) ws_max = std::max(ws_max, pl.total * 8);
+      if (make_plan(c, b[0] | r | KS_BCONV_TC, b[1], &pl) == KS_OK)
+        ws_max = std::max(ws_max, pl.total * 8);
     }
   const size_t out_b = (size_t)2 * c->nq * c->N * 8;
   void *mem = nullptr;
@@ -1403,15 +1431,26 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
         best_c = b[1];
       }
     }
-  // 2) the schedule of the winner, one coordinate at a time: each stage's radix, then
-  // each column pass's tile, then the split ModDown; the winner is re-timed with the
-  // same number of repetitions, and a change is kept only if the whole KeySwitch gets
-  // faster by more than the timing noise (1.5%)
+  // 2) the schedule of the winner, one coordinate at a time: the tensor-core basis
+  // conversions, each stage's radix, then each column pass's tile, then the split
+  // ModDown; the winner is re-timed with the same number of repetitions, and a change is
+  // kept only if the whole KeySwitch gets faster by more than the timing noise (1.5%).
+  // With the tensor-core conversions the ModUp / ModDown column passes have no radix or
+  // tile of their own to tune.
   if (rc == KS_OK && c->loga > 0) {
     best = time_plan(best_v, best_c, 6);
+    if (c->tc_ap > 0 && !(best_v & KS_UNFUSED)) {
+      const float ms = time_plan(best_v | KS_BCONV_TC, best_c, 6);
+      if (ms < 0.985f * best) {
+        best = ms;
+        best_v |= KS_BCONV_TC;
+      }
+    }
+    const bool tc = (best_v & KS_BCONV_TC) != 0;
     const int plan_code3 = (best_v & KS_RADIX4) ? KS_R4 : (best_v & KS_RADIX16) ? KS_R16 : KS_R8;
     for (int st = 0; st < ST_COUNT && rc == KS_OK; ++st)
       for (int code = KS_R4; code <= KS_R16 && rc == KS_OK; ++code) {
+        if (tc && (st == ST_UPC || st == ST_DNC)) continue;
         if (code == plan_code3) continue;
         const int cur = (best_v >> (KS_STAGE_SHIFT + 2 * st)) & 3;
         if (cur == code) continue;
@@ -1424,6 +1463,7 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
       }
     for (int bit : {KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC, KS_SPLIT_DOWN}) {
       if (rc != KS_OK) break;
+      if (tc && (bit == KS_COLALT_UPC || bit == KS_COLALT_DNC)) continue;
       if (bit == KS_SPLIT_DOWN && ((best_v & 0xff) != KS_DPOB || (best_v & KS_UNFUSED))) continue;
       const float ms = time_plan(best_v ^ bit, best_c, 6);
       if (ms < 0.985f * best) {

@@ -171,6 +171,23 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned phase) {
   return mbar_try_wait(bar, phase) || mbar_wait_slow(bar, phase);
 }
 
+// The eight bytes of x (least significant first) as bf16 values, two per word: the
+// A operand of the tensor-core basis conversion. A byte b < 256 has at most 8
+// significant bits, so bf16(b) is exact: the float 2^23 + b (bits 0x4B000000 | b)
+// minus 2^23 is b exactly, and its upper 16 bits are bf16(b).
+__device__ __forceinline__ uint32_t bf16_of_byte(uint32_t b) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | b) - 8388608.0f) >> 16;
+}
+__device__ __forceinline__ uint4 bf16_bytes(u64 x) {
+  const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+  uint4 r;
+  r.x = bf16_of_byte(lo & 0xffu) | (bf16_of_byte((lo >> 8) & 0xffu) << 16);
+  r.y = bf16_of_byte((lo >> 16) & 0xffu) | (bf16_of_byte(lo >> 24) << 16);
+  r.z = bf16_of_byte(hi & 0xffu) | (bf16_of_byte((hi >> 8) & 0xffu) << 16);
+  r.w = bf16_of_byte((hi >> 16) & 0xffu) | (bf16_of_byte(hi >> 24) << 16);
+  return r;
+}
+
 // Programmatic dependent launch. Every KeySwitch kernel lets the next kernel of its
 // stream launch once all its CTAs reach their end (pdl_trigger), and waits for the
 // previous kernel to complete, with its memory visible, before it reads or writes any

@@ -221,6 +221,46 @@ int build_tables(ks_context *c) {
     pmod[i] = shoup_pair(P, q);
   }
 
+  // Tensor-core basis conversion constants (ks_tc.cu): per (digit, target) / target, a
+  // block [g < 2][k < ap][r < 8][a < 8] of bf16 values, the Toeplitz-shaped B operand:
+  // entry (s = 8g + r, limb k, byte a) = byte s - a of the constant of source k (zero
+  // outside bytes 0..7 and for missing sources), and in slot k = alpha the value 2^23
+  // at a = 0 (it meets the 1.0 the A operand holds there, adding 2^23 to every sum).
+  std::vector<u64> bup, bdown;
+  if (c->tc_ap > 0) {
+    const int ap = c->tc_ap;
+    const size_t blk = 32 * (size_t)ap;  // words per block (256 ap bytes)
+    auto bf16_byte = [](unsigned b) {
+      const float f = (float)b;
+      uint32_t bits;
+      std::memcpy(&bits, &f, 4);
+      return (uint16_t)(bits >> 16);
+    };
+    auto fill = [&](u64 *dst, const u64 *cst, int ns) {
+      uint16_t *h = reinterpret_cast<uint16_t *>(dst);
+      for (int g = 0; g < 2; ++g)
+        for (int k = 0; k < ap; ++k)
+          for (int r = 0; r < 8; ++r)
+            for (int a = 0; a < 8; ++a) {
+              const int sl = 8 * g + r, b = sl - a;
+              uint16_t val = 0;
+              if (k < ns && b >= 0 && b <= 7)
+                val = bf16_byte((unsigned)(cst[k] >> (8 * b)) & 0xffu);
+              else if (k == alpha && a == 0)
+                val = 0x4B00;  // 2^23
+              h[((g * ap + k) * 8 + r) * 8 + a] = val;
+            }
+    };
+    bup.assign((size_t)beta * QP * blk, 0);
+    bdown.assign((size_t)nq * blk, 0);
+    for (int j = 0; j < beta; ++j) {
+      const int lo = j * alpha, ns = std::min(nq, lo + alpha) - lo;
+      for (int t = 0; t < QP; ++t)
+        fill(&bup[((size_t)j * QP + t) * blk], &cup[((size_t)j * QP + t) * alpha], ns);
+    }
+    for (int i = 0; i < nq; ++i) fill(&bdown[(size_t)i * blk], &cdown[(size_t)i * alpha], np);
+  }
+
   // One device allocation for everything (256-byte aligned pieces).
   struct Piece {
     const void *src;
@@ -239,6 +279,8 @@ int build_tables(ks_context *c) {
       {cdown.data(), cdown.size() * 8, (void **)&T.cdown},
       {pinv.data(), pinv.size() * 16, (void **)&T.pinv},
       {pmod.data(), pmod.size() * 16, (void **)&T.pmod},
+      {bup.data(), bup.size() * 8, (void **)&T.bup},
+      {bdown.data(), bdown.size() * 8, (void **)&T.bdown},
       {nullptr, 256, (void **)&T.err},
   };
   size_t total = 0;

@@ -78,6 +78,8 @@ struct JobSet {
 // Word offsets of the workspace pieces.
 struct WsOff {
   long long v, tmp, acc, vp, tmp2;
+  // tensor-core basis conversions: the bf16 bytes of v and of vp (see ks_tc.cu)
+  long long pv, ppv;
 };
 // Which workspace piece a plain NTT pass works on.
 enum { BUF_TMP = 0, BUF_TMP2 = 1 };
@@ -94,7 +96,23 @@ struct Tables {
   u64 *cdown;            // [nq][alpha]       (Phat_k mod q_i) 2^64 mod q_i
   ulonglong2 *pinv;      // [nq] P^-1 mod q_i (Shoup pair)
   ulonglong2 *pmod;      // [nq] P mod q_i (Shoup pair), keygen only
+  // Tensor-core basis conversions (ks_tc.cu): the constants of cup / cdown as bf16
+  // bytes in the MMA's B layout, 32 * tc_ap words per (digit, target) / target.
+  u64 *bup;              // [beta][QP][32 tc_ap] (empty when the context has no TC path)
+  u64 *bdown;            // [nq][32 tc_ap]
   int *err;              // sticky device error word
+};
+
+// Tensor-core basis conversion: at most this many source sets (digits) per context.
+constexpr int kTcMaxSets = 64;
+// Work of one tensor-core BConv launch: the target pairs of every source set, over all
+// column tiles; item = (tile, pair), tile-major (see ks_tc.cu).
+struct TcItems {
+  int nsets, pairs, tiles, items, per_cta;
+  int set_id[kTcMaxSets];       // digit j (ModUp) or polynomial c (ModDown)
+  int set_y0[kTcMaxSets];       // first work item (Tasks index) of the set
+  int set_cnt[kTcMaxSets];      // work items of the set
+  int set_p0[kTcMaxSets + 1];   // pairs before the set
 };
 
 struct LaunchTable;
@@ -116,6 +134,9 @@ struct ks_context {
   const ks::LaunchTable *ltab[3][2] = {};
   const ks::LaunchTable *lt = nullptr;
   int run_up = 1, run_down = 1;  // max terms per exact 128-bit BConv sum
+  // Tensor-core basis conversions: K slots per source set (alpha + 1 rounded up to
+  // even; 0 = not available for this context) and log2 of the points per column tile.
+  int tc_ap = 0, tc_tplog = 0;
   std::vector<u64> mods;  // host copy, Q then P
   void *table_mem = nullptr;
   size_t table_bytes = 0;
@@ -193,6 +214,10 @@ struct LaunchTable {
                           cudaStream_t);
   cudaError_t (*intt_col)(const ks_context *, const JobSet &, const WsOff &, int which,
                           cudaStream_t);
+  // The same column pass writing the bf16 bytes of its output (pv / ppv) for the
+  // tensor-core basis conversion instead of v / vp.
+  cudaError_t (*intt_col_tc)(const ks_context *, const JobSet &, const WsOff &, int which,
+                             cudaStream_t);
   // ModUp column pass (TASK_UP): BConv of digit j onto limb t + first NTT pass -> tmp.
   cudaError_t (*modup_col)(const ks_context *, const JobSet &, const WsOff &, const Tasks &,
                            cudaStream_t);
@@ -225,6 +250,14 @@ bool selected_current(const ks_context *c);
 // per thread, twice the threads per tile; 4: 16 points); ca = 1: the alternative
 // column tile (geo_tile_log_col_alt).
 const LaunchTable *launch_table(int logn, int rl, int ca);
+
+// Tensor-core basis conversion + first forward NTT pass (ks_tc.cu), in place of the
+// fused column passes modup_col (up = true, TASK_UP -> tmp) and moddown_col (TASK_DOWN ->
+// tmp2); reads the bytes the intt_col_tc pass wrote. Needs ctx->tc_ap > 0.
+cudaError_t launch_bconv_tc(const ks_context *c, const JobSet &js, const WsOff &o,
+                            const Tasks &tk, bool up, cudaStream_t s);
+// Opt in to the shared memory of the tensor-core kernels of this N (once per context).
+cudaError_t tc_prepare(int logn);
 
 // Element-wise kernels (ks_elem.cu): the unfused building blocks and keygen.
 cudaError_t launch_bconv_up(const ks_context *c, const JobSet &js, const WsOff &o,

@@ -25,6 +25,7 @@ struct KArgs {
   int N, nq, np, qp, alpha, beta;
   int run_up, run_down;
   int eqp, epb;  // key layout (see ks_context)
+  int tc_ap, tc_tplog;  // tensor-core basis conversion (see ks_context)
 };
 
 // Word offset of evk[j][c][limb t] (t in the context's Q u P numbering).
@@ -52,6 +53,8 @@ inline KArgs make_args(const ks_context *c) {
   a.run_down = c->run_down;
   a.eqp = c->eqp;
   a.epb = c->epb;
+  a.tc_ap = c->tc_ap;
+  a.tc_tplog = c->tc_tplog;
   return a;
 }
 
@@ -464,12 +467,32 @@ __global__ void __launch_bounds__(GeoT<LOGN, RL, 1>::NT)
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
+// The bf16 bytes of a scaled column tile, in the layout of the tensor-core basis
+// conversion (ks_tc.cu): the limb's columns in blocks of 2^tplog / N1 columns, block
+// after block; inside a block, point (y, g) at y * (columns per block) + g, 16 bytes
+// (eight bf16) per point.
+template <class GT>
+__device__ __forceinline__ void store_pieces(u64 *pb, const u64 *s, int c0, int tplog) {
+  constexpr int TILE = GT::N1 * GT::GC;
+  const int lgc = tplog - GT::LOGA;
+#pragma unroll
+  for (int k = 0; k < (TILE + GT::NT - 1) / GT::NT; ++k) {
+    const int e = threadIdx.x + k * GT::NT;
+    if (TILE % GT::NT != 0 && e >= TILE) break;
+    const int y = e >> GT::LOGGC, g = e & (GT::GC - 1), col = c0 + g;
+    const size_t p =
+        ((size_t)(col >> lgc) << tplog) + ((size_t)y << lgc) + (col & ((1 << lgc) - 1));
+    *reinterpret_cast<uint4 *>(pb + 2 * p) = bf16_bytes(s[y * GT::PC + g]);
+  }
+}
+
 // Inverse NTT, column pass (global stages logN1-1 .. 0), in place, then the
-// per-limb scale; `only_o` as in the row pass.
+// per-limb scale; `only_o` as in the row pass. pieces: write the bf16 bytes of the
+// result to pv / ppv (tensor-core basis conversion) instead of the result to v / vp.
 template <int LOGN, int RL, int CA, bool TMA = true>
 __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, const WsOff &wo,
                                              int which, int bx, int by, unsigned char *raw,
-                                             int only_o = -1) {
+                                             int only_o = -1, bool pieces = false) {
   using GT = GeoT<LOGN, RL, 0, CA>;
   ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(raw);
   u64 *sm = tile_ptr<GT, true>(raw);
@@ -497,7 +520,14 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
       sm[y * GT::PC + g] = csub(shoup(sm[y * GT::PC + g], sc.x, sc.y, m), m);
     }
     __syncthreads();
-    store_cols<GT>(d, sm, c0);
+    if (pieces) {
+      // limb ii of v, or P-limb ii of polynomial o of vp: 2N words of bytes per limb
+      const size_t limb = which == 0 ? (size_t)ii : (size_t)o * a.np + ii;
+      store_pieces<GT>(jp.ws + (which == 0 ? wo.pv : wo.ppv) + limb * 2 * a.N, sm, c0,
+                       a.tc_tplog);
+    } else {
+      store_cols<GT>(d, sm, c0);
+    }
     __syncthreads();
   }
 }
@@ -505,11 +535,12 @@ __device__ __forceinline__ void inv_col_body(const KArgs &a, const JobPtr &jp, c
 template <int LOGN, int RL, int CA>
 __global__ void __launch_bounds__(GeoT<LOGN, RL, 0, CA>::NT,
                                   min_blocks(GeoT<LOGN, RL, 0, CA>::NT, RL == 4 ? 512 : 768))
-    k_inv_col(KArgs a, JobSet js, WsOff wo, int which, int split) {
+    k_inv_col(KArgs a, JobSet js, WsOff wo, int which, int split, int pieces) {
   extern __shared__ __align__(16) unsigned char raw[];
   int only_o;
   const int by = inv_grid_row(a, which, split, only_o);
-  inv_col_body<LOGN, RL, CA>(a, js.j[blockIdx.z], wo, which, blockIdx.x, by, raw, only_o);
+  inv_col_body<LOGN, RL, CA>(a, js.j[blockIdx.z], wo, which, blockIdx.x, by, raw, only_o,
+                             pieces != 0);
   pdl_trigger();  // the next kernel may launch once every CTA is here
 }
 
@@ -1144,13 +1175,21 @@ struct Launch {
                       GTR::SMEM_ROW, s, args_of(c), js, wo, which, split);
   }
 
-  static cudaError_t intt_col(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
-                              cudaStream_t s) {
+  static cudaError_t intt_col_p(const ks_context *c, const JobSet &js, const WsOff &wo,
+                                int which, int pieces, cudaStream_t s) {
     const int inner = which == 0 ? c->nq : c->np;
     if (GTC::LOGA == 0 || inner == 0 || js.n == 0) return cudaSuccess;
     const int split = inv_split(GRID_COL, inner, which, js.n);
     return launch_pdl(k_inv_col<LOGN, RL, CA>, dim3(GRID_COL, inner << split, js.n), dim3(GTC::NT),
-                      GTC::SMEM_COL, s, args_of(c), js, wo, which, split);
+                      GTC::SMEM_COL, s, args_of(c), js, wo, which, split, pieces);
+  }
+  static cudaError_t intt_col(const ks_context *c, const JobSet &js, const WsOff &wo, int which,
+                              cudaStream_t s) {
+    return intt_col_p(c, js, wo, which, 0, s);
+  }
+  static cudaError_t intt_col_tc(const ks_context *c, const JobSet &js, const WsOff &wo,
+                                 int which, cudaStream_t s) {
+    return intt_col_p(c, js, wo, which, 1, s);
   }
 
   template <int PRO>
@@ -1202,8 +1241,9 @@ struct Launch {
   }
 
   static const LaunchTable &table() {
-    static const LaunchTable t = {&prepare, &count,       &intt_row,    &intt_col, &modup_col,
-                                  &modup_row, &moddown_col, &moddown_row, &ntt_col,  &ntt_row};
+    static const LaunchTable t = {&prepare,     &count,       &intt_row,  &intt_col,
+                                  &intt_col_tc, &modup_col,   &modup_row, &moddown_col,
+                                  &moddown_row, &ntt_col,     &ntt_row};
     return t;
   }
 };

@@ -130,14 +130,18 @@ __device__ __forceinline__ void bfly_inv_fast_neg(u64 &a, u64 &b, const ulonglon
   b = shoup4(Y - X + bias, w.x, w.y, m);
 }
 
-template <int LOGM, int LOGG, int P, int NT, bool ROW, bool INV, int LS0, int R, bool FAST>
+// SPLIT: the block runs several tiles side by side, NT threads each (NT a power of
+// two); a thread works on the tile of its group of NT (the caller picks s, tw, m).
+template <int LOGM, int LOGG, int P, int NT, bool ROW, bool INV, int LS0, int R, bool FAST,
+          bool SPLIT = false>
 __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
   constexpr int SUB = LOGM - LS0 - R;
   constexpr int NG = 1 << (LOGM - R + LOGG);
   const u64 m2 = 2 * m, m4 = 4 * m;
+  const int tid = SPLIT ? (int)(threadIdx.x & (NT - 1)) : (int)threadIdx.x;
 #pragma unroll
   for (int it = 0; it < (NG + NT - 1) / NT; ++it) {
-    const int grp = threadIdx.x + it * NT;
+    const int grp = tid + it * NT;
     if (NG % NT != 0 && grp >= NG) break;
     const int g = grp & ((1 << LOGG) - 1);
     const int rest = grp >> LOGG;
@@ -203,13 +207,14 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
 // Forward stages 0..LOGM-1 of every sub-transform in the tile, in rounds of at
 // most RM stages. Inputs in [0, 4m), outputs in [0, 4m). Caller syncs before;
 // each round syncs after.
-template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM, bool FAST, int LS0 = 0>
+template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM, bool FAST, int LS0 = 0,
+          bool SPLIT = false>
 __device__ __forceinline__ void tile_fwd_t(u64 *s, const ulonglong2 *tw, u64 m) {
   if constexpr (LS0 < LOGM) {
     constexpr int R = (LOGM - LS0) >= RM ? RM : (LOGM - LS0);
-    ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R, FAST>(s, tw, m);
+    ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R, FAST, SPLIT>(s, tw, m);
     __syncthreads();
-    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, FAST, LS0 + R>(s, tw, m);
+    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, FAST, LS0 + R, SPLIT>(s, tw, m);
   }
 }
 

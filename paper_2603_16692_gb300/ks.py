@@ -24,6 +24,7 @@ KS_R4, KS_R8, KS_R16 = 1, 2, 3
 KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC = 0x4000000, 0x8000000, 0x10000000
 KS_COLTILE_ALT = KS_COLALT_INV | KS_COLALT_UPC | KS_COLALT_DNC
 KS_SPLIT_DOWN = 0x20000000
+KS_BCONV_TC = 0x800
 STAGE_NAMES = ("inv", "upc", "km", "dnc", "dnr")
 
 
@@ -57,7 +58,8 @@ class ks_info(ctypes.Structure):
                 ("tuned_variant", ctypes.c_int), ("tuned_chunks", ctypes.c_int),
                 ("tuned_batch", ctypes.c_int), ("tuned_ms", ctypes.c_float),
                 ("L", ctypes.c_int), ("top_L", ctypes.c_int),
-                ("selected_variant", ctypes.c_int), ("selected_chunks", ctypes.c_int)]
+                ("selected_variant", ctypes.c_int), ("selected_chunks", ctypes.c_int),
+                ("tc", ctypes.c_int)]
 
 
 class ks_kernel_stat(ctypes.Structure):
@@ -472,6 +474,8 @@ def variant_name(v: int, chunks: int = 0) -> str:
         s += "-colalt" if len(alt) == 3 else "-colalt(" + ",".join(alt) + ")"
     if v & KS_SPLIT_DOWN:
         s += "-split"
+    if v & KS_BCONV_TC:
+        s += "-tc"
     return s
 
 

@@ -29,7 +29,8 @@ def main(argv=None):
     ap.add_argument("--radix", type=int, default=8, choices=[4, 8, 16])
     ap.add_argument("--sched", default="",
                     help="per-stage radix and column tile, e.g. km4,dnr16,colalt-inv "
-                         "(stages inv, upc, km, dnc, dnr); 'tuned' = ks_tune's choice")
+                         "(stages inv, upc, km, dnc, dnr), split, tc; 'tuned' = ks_tune's "
+                         "choice")
     ap.add_argument("--op", default="switch", choices=["switch", "hmul", "hrot"])
     ap.add_argument("--level", type=int, default=-1, help="run on a level view (default: top)")
     ap.add_argument("--reps", type=int, default=1)
@@ -81,6 +82,8 @@ def parse_sched(text: str) -> int:
     for item in filter(None, text.split(",")):
         if item == "split":
             v |= ks.KS_SPLIT_DOWN
+        elif item == "tc":
+            v |= ks.KS_BCONV_TC
         elif item == "colalt":
             v |= ks.KS_COLTILE_ALT
         elif item.startswith("colalt-"):
