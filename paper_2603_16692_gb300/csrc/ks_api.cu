@@ -500,13 +500,14 @@ int create_context(int dnum, int logn, int L, const u64 *q, const u64 *p, int al
   // basis-conversion sums: run * max_source * m < m 2^64
   c->run_up = (int)std::min<u64>(1 << 20, (~(u64)0) / maxq);
   c->run_down = (int)std::min<u64>(1 << 20, (~(u64)0) / maxp);
-  // Tensor-core basis conversions (ks_tc.cu): two-pass N, 2..15 sources per set (the
-  // fp32 sums of byte products stay exact below 2^23), one REDC per sum, at most
+  // Tensor-core basis conversions (ks_tc.cu): two-pass N, 2..9 sources per set (the
+  // fp32 sums of byte products stay exact below 2^23 up to 16 sources; the source bytes
+  // of a 1024-point tile fill the shared memory at 9), one REDC per sum, at most
   // kTcMaxSets digits.
-  if (c->loga > 0 && logn <= 17 && alpha >= 2 && alpha <= 15 && beta <= ks::kTcMaxSets &&
+  if (c->loga > 0 && logn <= 17 && alpha >= 2 && alpha <= 9 && beta <= ks::kTcMaxSets &&
       c->run_up >= alpha && c->run_down >= alpha) {
     c->tc_ap = (alpha + 2) & ~1;  // alpha + 1 slots (the last adds 2^23), rounded to even
-    c->tc_tplog = c->tc_ap <= 10 ? 10 : 9;
+    c->tc_tplog = 10;             // 1024-point column tiles
     if (ks::tc_prepare(logn) != cudaSuccess) {
       cudaGetLastError();
       c->tc_ap = c->tc_tplog = 0;

@@ -132,6 +132,10 @@ __device__ __forceinline__ void mbar_expect_tx(u64 *bar, unsigned bytes) {
                "r"(bytes)
                : "memory");
 }
+// One arrival on the barrier (no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(u64 *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::

@@ -207,14 +207,24 @@ __device__ __forceinline__ void ntt_round(u64 *s, const ulonglong2 *tw, u64 m) {
 // Forward stages 0..LOGM-1 of every sub-transform in the tile, in rounds of at
 // most RM stages. Inputs in [0, 4m), outputs in [0, 4m). Caller syncs before;
 // each round syncs after.
+// Barrier after a round: the whole block (BARN = 0), or named barrier `id` over BARN
+// threads (a group of the block; the others run another role or another group).
+template <int BARN>
+__device__ __forceinline__ void round_sync(int id = 1) {
+  if constexpr (BARN == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(BARN) : "memory");
+}
+
 template <int LOGM, int LOGG, int P, int NT, bool ROW, int RM, bool FAST, int LS0 = 0,
-          bool SPLIT = false>
-__device__ __forceinline__ void tile_fwd_t(u64 *s, const ulonglong2 *tw, u64 m) {
+          bool SPLIT = false, int BARN = 0>
+__device__ __forceinline__ void tile_fwd_t(u64 *s, const ulonglong2 *tw, u64 m, int bar_id = 1) {
   if constexpr (LS0 < LOGM) {
     constexpr int R = (LOGM - LS0) >= RM ? RM : (LOGM - LS0);
     ntt_round<LOGM, LOGG, P, NT, ROW, false, LS0, R, FAST, SPLIT>(s, tw, m);
-    __syncthreads();
-    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, FAST, LS0 + R, SPLIT>(s, tw, m);
+    round_sync<BARN>(bar_id);
+    tile_fwd_t<LOGM, LOGG, P, NT, ROW, RM, FAST, LS0 + R, SPLIT, BARN>(s, tw, m, bar_id);
   }
 }
 

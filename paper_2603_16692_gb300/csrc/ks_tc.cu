@@ -23,17 +23,18 @@
 //  B  [u < 2][g < 2][k < ap][r < 8][8 bf16] per target pair: target u, output slots
 //     s = 8g + r, limb k; K stride 128 bytes (LBO), N stride ap*128 bytes (SBO). A
 //     constant table per (digit, target) / target, built with the context.
-//  D  TMEM lane p (of a 128-point M block), column (u, s): two buffers of
-//     (TP / 128) x 32 columns, so the MMAs of the next pair run while this pair's sums
-//     are recombined.
+//  D  TMEM lane p (of a 128-point M block), column (u, s): one accumulator of
+//     (TP / 128) x 32 columns per consumer group, so the MMAs of one group's next pair
+//     run while the other group recombines and transforms its own.
 //
 // One CTA per SM walks a contiguous range of (column tile, target pair) items; the
 // bytes of a tile's sources stay in shared memory while the CTA converts them onto
-// successive pairs of targets. Per item: thread 0 issues the MMAs (one elected thread,
-// completion on an mbarrier through tcgen05.commit); every thread reads its lane's 16
-// sums per target from TMEM, recombines them into the exact 128-bit S, applies REDC,
-// and writes the tile; then the two halves of the block run the column NTT of the two
-// targets side by side and store them.
+// successive pairs of targets. Roles: one producer thread (its own warp) issues the
+// bulk copies and the MMAs (completion on mbarriers through tcgen05.commit); two
+// consumer groups take the items in turn: each reads its lanes' 16 sums per target from
+// TMEM, recombines them into the exact 128-bit S, applies REDC and writes the tiles,
+// then its two halves run the column NTT of the pair's two targets side by side and
+// store them. Full / empty mbarriers hand the buffers over between the roles.
 #include <algorithm>
 
 #include "ks_internal.h"
@@ -128,25 +129,39 @@ __device__ __forceinline__ U128 tc_sum(const uint32_t (&r)[16]) {
   return s;
 }
 
-// Geometry: column tiles of TP = 2^TPLOG points (N1 rows x GC columns).
-template <int LOGN, int TPLOG>
+// Column tiles of TP = 2^10 points (N1 rows x GC columns); the inverse column passes
+// write the source bytes in blocks of this size (tc_tplog).
+constexpr int kTcTpLog = 10;
+// Consumer groups per CTA.
+constexpr int kTcGroups = 2;
+
+// Geometry. Consumers: GRP groups of 256 threads taking items round-robin (so that one
+// group's waits and barriers overlap the other's arithmetic); a group is two halves of
+// 128 threads, one per target of the pair, 8 points per thread (radix-8 NTT rounds).
+// Per group: a TMEM accumulator (8 M blocks x 32 columns), a constant buffer and two
+// NTT tiles. The column twiddles are read from the table (L1).
+template <int LOGN, int GRP>
 struct TcGeo {
   static constexpr int LOGA = geo_loga(LOGN), LOGB = LOGN - LOGA;
   static constexpr int N1 = 1 << LOGA;
-  static constexpr int TP = 1 << TPLOG;
+  static constexpr int TPLOG = kTcTpLog, TP = 1 << TPLOG;
   static constexpr int LOGGC = TPLOG - LOGA, GC = 1 << LOGGC, PC = GC + 1;
   static constexpr int MB = TP / 128;  // M blocks of 128 points
-  static constexpr int HT = TP / 4;    // threads per target of a pair (4 points each)
-  static constexpr int NT = 2 * HT;
+  static constexpr int PTS = 8, RM = 3;  // points per consumer thread, NTT stages per round
+  static constexpr int HT = TP / PTS;    // consumer threads per target
+  static constexpr int GT = 2 * HT;      // threads per group
+  static constexpr int NT = GRP * GT;    // consumer threads
   static constexpr int TILES = (1 << LOGN) / TP;
-  static constexpr int COLS = 2 * MB * 32;  // TMEM columns: two buffers
-  static constexpr int TILE_W = N1 * PC;    // words of one target's NTT tile
-  static constexpr int APMAX = TPLOG >= 10 ? 10 : 16;
-  // shared memory for ap K slots per source set
+  static constexpr int DCOLS = MB * 32;  // TMEM columns per group
+  static constexpr int COLS = GRP * DCOLS <= 256 ? 256 : 512;
+  static constexpr int TILE_W = N1 * PC;  // words of one target's NTT tile
+  static constexpr int APMAX = 10;        // K slots (alpha <= 9)
   __host__ __device__ static constexpr int smem(int ap) {
-    return ap * TP * 16 + 4 * 256 * ap + 4 * N1 * 16 + 2 * TILE_W * 8;
+    return ap * TP * 16 + GRP * 512 * ap + GRP * 2 * TILE_W * 8;
   }
-  static_assert(LOGGC >= 1 && MB % 4 == 0, "tile shape");
+  static_assert(LOGGC >= 1 && MB % 4 == 0 && (HT / 32) % 4 == 0 && GRP * DCOLS <= 512 &&
+                    smem(APMAX) <= 227 * 1024 - 256 && NT + 32 <= 1024,
+                "tile shape");
 };
 
 struct TcItem {
@@ -165,36 +180,45 @@ __device__ __forceinline__ TcItem tc_item(const TcItems &ti, int it) {
   return r;
 }
 
-template <int LOGN, int PRO, int TPLOG>
-__global__ void __launch_bounds__(TcGeo<LOGN, TPLOG>::NT, 1)
+template <int LOGN, int PRO, int GRP>
+__global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
     k_bconv_tc(KArgs a, JobSet js, WsOff wo, Tasks tk, TcItems ti) {
-  using G = TcGeo<LOGN, TPLOG>;
-  extern __shared__ __align__(1024) unsigned char raw[];
-  __shared__ u64 bar_a, bar_b[2], bar_m[2];
+  using G = TcGeo<LOGN, GRP>;
+  extern __shared__ __align__(16) unsigned char raw[];
+  // Per group g: bar_b[g] (the pair's constants landed; releases the pair's info),
+  // bar_m[g] (the MMAs into the group's accumulator completed), bar_tm[g] (every warp
+  // of the group has read the accumulator and the info: both, and the constant buffer,
+  // may be refilled). bar_a: a tile's source bytes landed.
+  __shared__ u64 bar_a, bar_b[GRP], bar_m[GRP], bar_tm[GRP];
   __shared__ uint32_t tm_slot;
+  // per group, written by the producer before it arms bar_b: the pair's decoded work
+  // items, how many are real, the tile, and whether both moduli take the fast
+  // butterflies
+  __shared__ uint32_t info_w[GRP][2];
+  __shared__ int info_cnt[GRP], info_tile[GRP], info_fast[GRP];
   const JobPtr &jp = js.j[blockIdx.z];
   const int AP = a.tc_ap;
   const int it0 = blockIdx.x * ti.per_cta, it1 = min(ti.items, it0 + ti.per_cta);
   unsigned char *sA = raw;
-  unsigned char *sB = raw + (size_t)AP * G::TP * 16;
-  ulonglong2 *sTW = reinterpret_cast<ulonglong2 *>(sB + 4 * 256 * AP);
-  u64 *sT = reinterpret_cast<u64 *>(sTW + 4 * G::N1);
+  unsigned char *sB = raw + (size_t)AP * G::TP * 16;       // [GRP][2][256 ap]
+  u64 *sT = reinterpret_cast<u64 *>(sB + (size_t)GRP * 512 * AP);  // [GRP][2][TILE_W]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int half = threadIdx.x / G::HT;  // the target of the pair this thread works on
+  constexpr int CW = G::NT / 32;  // consumer warps; warp CW is the producer
 
   if (warp == 0) tmem_alloc(&tm_slot, G::COLS);
   if (threadIdx.x == 0) {
     mbar_init(&bar_a, 1);
-    mbar_init(&bar_b[0], 1);
-    mbar_init(&bar_b[1], 1);
-    mbar_init(&bar_m[0], 1);
-    mbar_init(&bar_m[1], 1);
+    for (int g = 0; g < GRP; ++g) {
+      mbar_init(&bar_b[g], 1);
+      mbar_init(&bar_m[g], 1);
+      mbar_init(&bar_tm[g], G::GT / 32);
+    }
   }
   // A: zero (finite values in the slots a short digit leaves unused; their B rows are
   // zero), with bf16 1.0 in the first K element of slot alpha (the 2^23 row); B: zero.
-  for (int k = threadIdx.x; k < AP * G::TP; k += G::NT)
+  for (int k = threadIdx.x; k < AP * G::TP; k += blockDim.x)
     reinterpret_cast<uint4 *>(sA)[k] = make_uint4(k / G::TP == a.alpha ? 0x3F80u : 0u, 0, 0, 0);
-  for (int k = threadIdx.x; k < 4 * 16 * AP; k += G::NT)
+  for (int k = threadIdx.x; k < GRP * 32 * AP; k += blockDim.x)
     reinterpret_cast<uint4 *>(sB)[k] = make_uint4(0, 0, 0, 0);
   proxy_fence();
   tc_fence_before();
@@ -203,120 +227,129 @@ __global__ void __launch_bounds__(TcGeo<LOGN, TPLOG>::NT, 1)
   const uint32_t tmem = tm_slot;
   pdl_wait();
 
-  const u64 *pbase = jp.ws + (PRO == PRO_UP ? wo.pv : wo.ppv);
-  u64 *dst = jp.ws + (PRO == PRO_UP ? wo.tmp : wo.tmp2);
-  auto nsrc = [&](int set) {
-    const int j = ti.set_id[set];
-    return PRO == PRO_UP ? min(a.nq, (j + 1) * a.alpha) - j * a.alpha : a.np;
-  };
   auto target = [&](const TcItem &x, int u) { return decode(a, tk, x.y0 + min(u, x.cnt - 1)); };
-  // thread 0: bulk copies of a tile's source bytes (bar_a) / of a pair's constants and
-  // twiddles (bar_b[buf])
-  auto load_a = [&](const TcItem &x) {
-    const int ns = nsrc(x.set);
-    const size_t l0 = (size_t)ti.set_id[x.set] * (PRO == PRO_UP ? a.alpha : a.np);
-    mbar_expect_tx(&bar_a, (unsigned)ns * G::TP * 16);
-    for (int k = 0; k < ns; ++k)
-      bulk_g2s(sA + (size_t)k * G::TP * 16,
-               pbase + (((l0 + k) * G::TILES + x.tile) << TPLOG) * 2, G::TP * 16, &bar_a);
-  };
-  auto load_b = [&](const TcItem &x, int buf) {
-    mbar_expect_tx(&bar_b[buf], 2u * (256 * AP + G::N1 * 16));
-    for (int u = 0; u < 2; ++u) {
-      const uint32_t w = target(x, u);
-      const int t = task_limb(w);
-      const u64 *b = PRO == PRO_UP ? a.tab.bup + ((size_t)task_dig(w) * a.qp + t) * 32 * AP
-                                   : a.tab.bdown + (size_t)t * 32 * AP;
-      bulk_g2s(sB + (size_t)(buf * 2 + u) * 256 * AP, b, 256 * AP, &bar_b[buf]);
-      bulk_g2s(sTW + (buf * 2 + u) * G::N1, a.tab.twc_f + ((size_t)t << G::LOGA), G::N1 * 16,
-               &bar_b[buf]);
-    }
-  };
-  // barrier phases: bit buf of phb / phm is the next phase of bar_b[buf] / bar_m[buf]
-  unsigned pha = 0, phb = 0, phm = 0;
-  auto issue_mma = [&](int buf, bool wait_a) {
-    if (wait_a) {
-      if (!mbar_wait(&bar_a, pha)) atomicExch(a.tab.err, 1);
-      pha ^= 1;
-    }
-    if (!mbar_wait(&bar_b[buf], (phb >> buf) & 1)) atomicExch(a.tab.err, 1);
-    phb ^= 1u << buf;
-    tc_fence_after();
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + (size_t)buf * 2 * 256 * AP);
-    for (int b = 0; b < G::MB; ++b)
-      for (int k = 0; k < AP / 2; ++k)
-        tc_mma(tmem + buf * (G::MB * 32) + b * 32,
-               smem_desc(a0 + 2 * k * G::TP * 16 + b * 2048, G::TP * 16, 128),
-               smem_desc(b0 + 2 * k * 128, 128, AP * 128), tc_idesc(32), k > 0);
-    tc_commit(&bar_m[buf]);
-  };
-
-  if (it0 < it1 && threadIdx.x == 0) {
-    const TcItem x = tc_item(ti, it0);
-    load_a(x);
-    load_b(x, it0 & 1);
-    issue_mma(it0 & 1, true);
-  }
-  const int q = warp & 3, r4 = ((warp % (G::HT / 32)) >> 2) * 4;  // TMEM quadrant, M blocks
-  for (int it = it0; it < it1; ++it) {
-    const int buf = it & 1;
-    const TcItem x = tc_item(ti, it);
-    const bool more = it + 1 < it1;
-    TcItem nx = x;
-    bool nx_unit = false;
-    if (more) {
-      nx = tc_item(ti, it + 1);
-      nx_unit = nx.tile != x.tile || nx.set != x.set;
-    }
-    if (threadIdx.x == 0 && more) load_b(nx, buf ^ 1);
-    if (!mbar_wait(&bar_m[buf], (phm >> buf) & 1)) atomicExch(a.tab.err, 1);
-    phm ^= 1u << buf;
-    tc_fence_after();
-    // the MMAs of item `it` were the last to read A: a new tile's bytes may land now
-    if (threadIdx.x == 0 && nx_unit) load_a(nx);
-    const uint32_t w = target(x, half);
-    const int t = task_limb(w);
-    const ModInfo mi = a.tab.mod[t];
-    u64 *tile = sT + half * G::TILE_W;
-    {
-      uint32_t v[4][16];
+  if (warp == CW) {
+    // Producer (one thread): constants, source bytes and MMAs, each group's next item as
+    // soon as the group has read its previous one.
+    if (lane == 0) {
+      const u64 *pbase = jp.ws + (PRO == PRO_UP ? wo.pv : wo.ppv);
+      const u64 ad0 = smem_desc(smem_u32(sA), G::TP * 16, 128);
+      unsigned pha = 0;
+      int cur_tile = -1, cur_set = -1;
+      for (int it = it0; it < it1; ++it) {
+        const int g = (it - it0) % GRP;
+        const unsigned k = (unsigned)(it - it0) / GRP;  // the group's k-th item
+        const TcItem x = tc_item(ti, it);
+        if (k > 0 && !mbar_wait(&bar_tm[g], (k - 1) & 1)) atomicExch(a.tab.err, 1);
+        const uint32_t wp[2] = {target(x, 0), target(x, 1)};
+        info_w[g][0] = wp[0];
+        info_w[g][1] = wp[1];
+        info_cnt[g] = x.cnt;
+        info_tile[g] = x.tile;
+        info_fast[g] = a.tab.mod[task_limb(wp[0])].m < kFastModulus &&
+                       a.tab.mod[task_limb(wp[1])].m < kFastModulus;
+        mbar_expect_tx(&bar_b[g], 2u * 256 * AP);  // releases the info
+        for (int v = 0; v < 2; ++v) {
+          const int t = task_limb(wp[v]);
+          const u64 *b = PRO == PRO_UP
+                             ? a.tab.bup + ((size_t)task_dig(wp[v]) * a.qp + t) * 32 * AP
+                             : a.tab.bdown + (size_t)t * 32 * AP;
+          bulk_g2s(sB + (size_t)(g * 2 + v) * 256 * AP, b, 256 * AP, &bar_b[g]);
+        }
+        if (x.tile != cur_tile || x.set != cur_set) {
+          // a new tile's source bytes, once the MMAs of the previous item no longer read A
+          if (it > it0) {
+            const int gp = (it - 1 - it0) % GRP;
+            if (!mbar_wait(&bar_m[gp], ((unsigned)(it - 1 - it0) / GRP) & 1))
+              atomicExch(a.tab.err, 1);
+          }
+          const int j = ti.set_id[x.set];
+          const int ns = PRO == PRO_UP ? min(a.nq, (j + 1) * a.alpha) - j * a.alpha : a.np;
+          const size_t l0 = (size_t)j * (PRO == PRO_UP ? a.alpha : a.np);
+          mbar_expect_tx(&bar_a, (unsigned)ns * G::TP * 16);
+          for (int s = 0; s < ns; ++s)
+            bulk_g2s(sA + (size_t)s * G::TP * 16,
+                     pbase + (((l0 + s) * G::TILES + x.tile) << G::TPLOG) * 2, G::TP * 16,
+                     &bar_a);
+          if (!mbar_wait(&bar_a, pha)) atomicExch(a.tab.err, 1);
+          pha ^= 1;
+          cur_tile = x.tile;
+          cur_set = x.set;
+        }
+        if (!mbar_wait(&bar_b[g], k & 1)) atomicExch(a.tab.err, 1);
+        tc_fence_after();
+        const u64 bd0 = smem_desc(smem_u32(sB + (size_t)g * 512 * AP), 128, AP * 128);
+        const uint32_t d0 = tmem + g * G::DCOLS;
+        // descriptors advance by (byte offset >> 4) in their start-address field
 #pragma unroll
-      for (int bb = 0; bb < 4; ++bb)
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * (G::MB * 32) + (r4 + bb) * 32 +
-                      half * 16,
-                  v[bb]);
-      tmem_wait_ld();
-#pragma unroll
-      for (int bb = 0; bb < 4; ++bb) {
-        const u64 z = redc(tc_sum(v[bb]), mi.m, mi.minv);
-        const int p = (r4 + bb) * 128 + 32 * q + lane;
-        tile[(p >> G::LOGGC) * G::PC + (p & (G::GC - 1))] = z;
+        for (int b = 0; b < G::MB; ++b)
+          for (int s = 0; s < AP / 2; ++s)
+            tc_mma(d0 + b * 32, ad0 + (u64)(2 * s * G::TP + b * 128), bd0 + (u64)(16 * s),
+                   tc_idesc(32), s > 0);
+        tc_commit(&bar_m[g]);
       }
     }
-    if (threadIdx.x == 0 && more) issue_mma(buf ^ 1, nx_unit);
-    tc_fence_before();
-    __syncthreads();
-    // both halves take the same butterflies (their rounds share the block's barriers):
-    // the fast ones only when both moduli allow them
-    const ulonglong2 *tw = sTW + (buf * 2 + half) * G::N1;
-    if (mi.m < kFastModulus && a.tab.mod[task_limb(target(x, half ^ 1))].m < kFastModulus)
-      tile_fwd_t<G::LOGA, G::LOGGC, G::PC, G::HT, false, 2, true, 0, true>(tile, tw, mi.m);
-    else
-      tile_fwd_t<G::LOGA, G::LOGGC, G::PC, G::HT, false, 2, false, 0, true>(tile, tw, mi.m);
-    if (half < x.cnt) {
-      u64 *d = dst + (size_t)task_slot(w) * a.N;
-      const int c0 = x.tile * G::GC, lt = threadIdx.x & (G::HT - 1);
+  } else {
+    // Consumers: recombine the sums of each item, then the two targets' column NTTs.
+    const int group = threadIdx.x / G::GT, bar_id = 1 + group;
+    const int half = (threadIdx.x % G::GT) / G::HT;  // the target of the pair
+    const int q = warp & 3;  // TMEM lane quadrant of the warp (its 32 points of each M block)
+    u64 *dst = jp.ws + (PRO == PRO_UP ? wo.tmp : wo.tmp2);
+    u64 *tile = sT + (group * 2 + half) * G::TILE_W;
+    for (int it = it0 + group, k = 0; it < it1; it += GRP, ++k) {
+      // the pair's decoded items (the producer's info, released with its constants)
+      if (!mbar_wait(&bar_b[group], k & 1)) atomicExch(a.tab.err, 1);
+      const uint32_t w = info_w[group][half];
+      const int cnt = info_cnt[group], xtile = info_tile[group];
+      const bool fast = info_fast[group] != 0;
+      const ModInfo mi = a.tab.mod[task_limb(w)];
+      if (!mbar_wait(&bar_m[group], k & 1)) atomicExch(a.tab.err, 1);
+      tc_fence_after();
 #pragma unroll
-      for (int k = 0; k < G::TP / 2 / G::HT; ++k) {
-        const int e = 2 * (lt + k * G::HT), y = e >> G::LOGGC, g = e & (G::GC - 1);
-        ulonglong2 val;
-        val.x = tile[y * G::PC + g];
-        val.y = tile[y * G::PC + g + 1];
-        *reinterpret_cast<ulonglong2 *>(d + ((size_t)y << G::LOGB) + c0 + g) = val;
+      for (int b0 = 0; b0 < G::MB; b0 += 4) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb)
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + group * G::DCOLS + (b0 + bb) * 32 +
+                        half * 16,
+                    v[bb]);
+        tmem_wait_ld();
+        if (b0 + 4 == G::MB) {  // the warp's last reads of the accumulator
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_tm[group]);
+        }
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+          const u64 z = redc(tc_sum(v[bb]), mi.m, mi.minv);
+          const int p = (b0 + bb) * 128 + 32 * q + lane;
+          tile[(p >> G::LOGGC) * G::PC + (p & (G::GC - 1))] = z;
+        }
       }
+      round_sync<G::GT>(bar_id);
+      // both halves take the same butterflies (their rounds share the barrier): the fast
+      // ones only when both moduli allow them; twiddles from the column table
+      const ulonglong2 *tw = a.tab.twc_f + ((size_t)task_limb(w) << G::LOGA);
+      if (fast)
+        tile_fwd_t<G::LOGA, G::LOGGC, G::PC, G::HT, false, G::RM, true, 0, true, G::GT>(
+            tile, tw, mi.m, bar_id);
+      else
+        tile_fwd_t<G::LOGA, G::LOGGC, G::PC, G::HT, false, G::RM, false, 0, true, G::GT>(
+            tile, tw, mi.m, bar_id);
+      if (half < cnt) {
+        u64 *d = dst + (size_t)task_slot(w) * a.N;
+        const int c0 = xtile * G::GC, lt = threadIdx.x & (G::HT - 1);
+#pragma unroll
+        for (int r = 0; r < G::TP / 2 / G::HT; ++r) {
+          const int e = 2 * (lt + r * G::HT), y = e >> G::LOGGC, c = e & (G::GC - 1);
+          ulonglong2 val;
+          val.x = tile[y * G::PC + c];
+          val.y = tile[y * G::PC + c + 1];
+          *reinterpret_cast<ulonglong2 *>(d + ((size_t)y << G::LOGB) + c0 + c) = val;
+        }
+      }
+      round_sync<G::GT>(bar_id);  // the group's tiles are free for its next item
     }
-    proxy_fence();
-    __syncthreads();
   }
   tc_fence_before();
   __syncthreads();
@@ -325,24 +358,25 @@ __global__ void __launch_bounds__(TcGeo<LOGN, TPLOG>::NT, 1)
   pdl_trigger();
 }
 
-template <int LOGN, int TPLOG>
+template <int LOGN>
 cudaError_t prepare_one() {
-  using G = TcGeo<LOGN, TPLOG>;
+  using G = TcGeo<LOGN, kTcGroups>;
   cudaError_t e;
-  if ((e = smem_attr(k_bconv_tc<LOGN, PRO_UP, TPLOG>, G::smem(G::APMAX)))) return e;
-  return smem_attr(k_bconv_tc<LOGN, PRO_DOWN, TPLOG>, G::smem(G::APMAX));
+  if ((e = smem_attr(k_bconv_tc<LOGN, PRO_UP, kTcGroups>, G::smem(G::APMAX)))) return e;
+  return smem_attr(k_bconv_tc<LOGN, PRO_DOWN, kTcGroups>, G::smem(G::APMAX));
 }
 
-template <int LOGN, int TPLOG>
+template <int LOGN>
 cudaError_t launch_one(const ks_context *c, const JobSet &js, const WsOff &wo, const Tasks &tk,
                        const TcItems &ti, int grid, bool up, cudaStream_t s) {
-  using G = TcGeo<LOGN, TPLOG>;
+  constexpr int GRP = kTcGroups;
+  using G = TcGeo<LOGN, GRP>;
   const int smem = G::smem(c->tc_ap);
   if (up)
-    return launch_pdl(k_bconv_tc<LOGN, PRO_UP, TPLOG>, dim3(grid, 1, js.n), dim3(G::NT), smem, s,
-                      args_of(c), js, wo, tk, ti);
-  return launch_pdl(k_bconv_tc<LOGN, PRO_DOWN, TPLOG>, dim3(grid, 1, js.n), dim3(G::NT), smem, s,
-                    args_of(c), js, wo, tk, ti);
+    return launch_pdl(k_bconv_tc<LOGN, PRO_UP, GRP>, dim3(grid, 1, js.n), dim3(G::NT + 32), smem,
+                      s, args_of(c), js, wo, tk, ti);
+  return launch_pdl(k_bconv_tc<LOGN, PRO_DOWN, GRP>, dim3(grid, 1, js.n), dim3(G::NT + 32), smem,
+                    s, args_of(c), js, wo, tk, ti);
 }
 
 }  // namespace kern
@@ -402,11 +436,9 @@ cudaError_t launch_bconv_tc(const ks_context *c, const JobSet &js, const WsOff &
   const int per_job = std::max(1, sm_count(c->device) / js.n);
   ti.per_cta = (ti.items + per_job - 1) / per_job;
   const int grid = (ti.items + ti.per_cta - 1) / ti.per_cta;
-  const bool big = c->tc_tplog >= 10;
-#define KS_TC_CASE(LN)                                                     \
-  case LN:                                                                \
-    return big ? kern::launch_one<LN, 10>(c, js, wo, tk, ti, grid, up, s) \
-               : kern::launch_one<LN, 9>(c, js, wo, tk, ti, grid, up, s);
+#define KS_TC_CASE(LN) \
+  case LN:              \
+    return kern::launch_one<LN>(c, js, wo, tk, ti, grid, up, s);
   switch (c->logn) {
     KS_TC_CASE(13)
     KS_TC_CASE(14)
@@ -420,27 +452,14 @@ cudaError_t launch_bconv_tc(const ks_context *c, const JobSet &js, const WsOff &
 }
 
 cudaError_t tc_prepare(int logn) {
-  cudaError_t e = cudaSuccess;
   switch (logn) {
-    case 13:
-      if (!(e = kern::prepare_one<13, 10>())) e = kern::prepare_one<13, 9>();
-      break;
-    case 14:
-      if (!(e = kern::prepare_one<14, 10>())) e = kern::prepare_one<14, 9>();
-      break;
-    case 15:
-      if (!(e = kern::prepare_one<15, 10>())) e = kern::prepare_one<15, 9>();
-      break;
-    case 16:
-      if (!(e = kern::prepare_one<16, 10>())) e = kern::prepare_one<16, 9>();
-      break;
-    case 17:
-      if (!(e = kern::prepare_one<17, 10>())) e = kern::prepare_one<17, 9>();
-      break;
-    default:
-      break;
+    case 13: return kern::prepare_one<13>();
+    case 14: return kern::prepare_one<14>();
+    case 15: return kern::prepare_one<15>();
+    case 16: return kern::prepare_one<16>();
+    case 17: return kern::prepare_one<17>();
+    default: return cudaSuccess;
   }
-  return e;
 }
 
 }  // namespace ks

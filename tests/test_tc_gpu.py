@@ -2,11 +2,11 @@
 
 The ModUp / ModDown BConv on tcgen05 (byte-split bf16 operands, fp32 sums, exact
 128-bit recombination, one REDC) must give the same words as the integer path and the
-oracle: every dataflow and chunk count, both column-tile sizes (2^10 points for
-alpha <= 9, 2^9 for 10 <= alpha <= 15), ragged last digits, dnum = 1, the three plain
-workloads at full size with seeds 0-2, with the split ModDown and radix schedules, in
-batches and on the host-buffer and allocation-free entry points. Contexts outside the
-path's range (alpha = 1, single-pass N) ignore the flag.
+oracle: every dataflow and chunk count, ragged last digits, dnum = 1, the three plain
+workloads at full size with seeds 0-2, alpha up to 9 (the path's limit), with the split
+ModDown and radix schedules, in batches and on the host-buffer and allocation-free
+entry points. Contexts outside the path's range (alpha = 1 or > 9, single-pass N)
+ignore the flag.
 """
 import numpy as np
 import pytest
@@ -37,10 +37,10 @@ def test_tc_plain_workloads(cfg, seed):
     check(cfg, seed, [v | TC for v in BASES], chunk_list=chunks)
 
 
-@pytest.mark.parametrize("cfg", [(2, 14, 20), (2, 16, 27), (3, 15, 44), (5, 16, 47)])
-def test_tc_large_alpha_tiles(cfg):
-    """alpha = 11, 14, 15 (2^9-point tiles, 12 and 16 K slots) and alpha = 10 with a
-    ragged last digit."""
+@pytest.mark.parametrize("cfg", [(2, 14, 17), (4, 16, 33), (7, 17, 60), (2, 14, 20)])
+def test_tc_alpha_limits(cfg):
+    """alpha = 9 (the most K slots, 10) with two full digits, with a ragged last digit,
+    at 2^17 with seven digits, and alpha = 11 (beyond the path: the flag is ignored)."""
     check(cfg, 1, [ks.KS_DPOB | TC, ks.KS_DSOC | TC], chunk_list=(3,))
 
 
@@ -61,7 +61,7 @@ def test_tc_with_schedules(cfg):
 
 def test_tc_flag_reported_by_context_info():
     for cfg, want in [(W.C3, 1), (W.C2, 1), ((6, 17, 5), 0), ((3, 12, 8), 0),
-                      ((2, 16, 27), 1), ((2, 16, 31), 0)]:
+                      ((2, 16, 17), 1), ((2, 16, 19), 0)]:
         ctx = ks.Context(W.make_params(*cfg))
         try:
             assert ks.ks_context_info(ctx.h)["tc"] == want, cfg
