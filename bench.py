@@ -42,20 +42,34 @@ WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 
 # Per-kernel DRAM bytes (read + write) per launch and pipe use, from the cold-cache ncu
 # launch list and the per-kernel --set full captures of one KeySwitch of the workload
-# (profile_case with the tuned plan DPOB[km4,dnr4]-split; summaries and commands in
+# (profile_case with the plan DPOB[km4,dnr4]-split; summaries and commands in
 # profiles/keyswitch_4_2e16_35_launches.md and keyswitch_4_2e16_35_kernels_ncu.md);
 # keyed by (workload, kernel name of the library's profiler), so a change of the
 # dominant kernel still finds its row. The split key multiply's two launches (P-limb
-# and Q-limb targets) are averaged, as the profiler averages them.
+# and Q-limb targets) are averaged, as the profiler averages them. Plans with the
+# tensor-core basis conversions (KS_BCONV_TC) run other column kernels: NCU_TC holds
+# their rows (profiles/bconv_tc_4_2e16_35_ncu.md); the inverse column passes that write
+# the source bytes for them were not captured (None).
 NCU = {("c3", k): {"traffic": t, "plan": "DPOB[km4,dnr4]-split", **pipes} for k, t, pipes in (
-    ("intt_row(d)", 57200000, {"issue_pct": 40.4, "fmaheavy_pct": 37.4, "alu_pct": 33.4}),
-    ("intt_col(d)", 19100000, {"issue_pct": 39.9, "fmaheavy_pct": 40.9, "alu_pct": 32.5}),
-    ("modup_col", 41200000, {"issue_pct": 55.7, "fmaheavy_pct": 65.1, "alu_pct": 46.5}),
-    ("modup_row_keymult", 176350000, {"issue_pct": 53.4, "fmaheavy_pct": 54.5, "alu_pct": 36.9}),
-    ("intt_row(accP)", 18900000, {"issue_pct": 41.4, "fmaheavy_pct": 33.6, "alu_pct": 36.7}),
-    ("intt_col(accP)", 9500000, {"issue_pct": 40.3, "fmaheavy_pct": 35.7, "alu_pct": 35.7}),
-    ("moddown_col", 9600000, {"issue_pct": 57.7, "fmaheavy_pct": 65.4, "alu_pct": 45.0}),
-    ("moddown_row", 124300000, {"issue_pct": 49.7, "fmaheavy_pct": 49.0, "alu_pct": 44.2}))}
+    ("intt_row(d)", 57100000, {"issue_pct": 47.3, "fmaheavy_pct": 45.0, "alu_pct": 37.3}),
+    ("intt_col(d)", 19100000, {"issue_pct": 45.8, "fmaheavy_pct": 47.0, "alu_pct": 35.0}),
+    ("modup_col", 38400000, {"issue_pct": 59.8, "fmaheavy_pct": 69.0, "alu_pct": 48.3}),
+    ("modup_row_keymult", 176050000, {"issue_pct": 54.1, "fmaheavy_pct": 55.0, "alu_pct": 37.2}),
+    ("intt_row(accP)", 18900000, {"issue_pct": 45.2, "fmaheavy_pct": 38.0, "alu_pct": 38.6}),
+    ("intt_col(accP)", 9500000, {"issue_pct": 45.0, "fmaheavy_pct": 41.0, "alu_pct": 37.1}),
+    ("moddown_col", 9600000, {"issue_pct": 58.2, "fmaheavy_pct": 66.0, "alu_pct": 46.0}),
+    ("moddown_row", 123700000, {"issue_pct": 51.7, "fmaheavy_pct": 52.0, "alu_pct": 44.7}))}
+NCU_TC = {("c3", "modup_col"): {"traffic": 111940000, "plan": "DPOB[km4,dnr4]-tc",
+                                "issue_pct": 29.9, "tensor_pct": 6.4, "alu_pct": 21.7},
+          ("c3", "moddown_col"): {"traffic": 19640000, "plan": "DPOB[km4,dnr4]-tc",
+                                  "issue_pct": 31.0, "tensor_pct": 6.9, "alu_pct": 22.4},
+          ("c3", "intt_col(d)"): None, ("c3", "intt_col(accP)"): None}
+
+
+def ncu_row(workload, name, tc):
+    if tc and (workload, name) in NCU_TC:
+        return NCU_TC[(workload, name)]
+    return NCU.get((workload, name))
 
 
 def measured_alu(ks, stream):
@@ -821,7 +835,7 @@ def main():
     # the recipe's unit counts for context: SMs x 64 IMAD lanes x max clock / 10 IMAD per
     # 64-bit Shoup product
     derived = sms * 64 * sm_mhz * 1e6 / 10 / 1e9
-    ncu = NCU.get((args.workload, dom["name"]))
+    ncu = ncu_row(args.workload, dom["name"], bool(pvar & ks.KS_BCONV_TC))
     roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu["achieved"],
                 "peak": alu["peak"], "unit": "Gop/s (butterfly-equivalent)",
                 "frac": alu["frac"], "traffic": ncu["traffic"] if ncu else None,
@@ -856,7 +870,7 @@ def main():
         k = {"name": s_["name"], "launches_per_step": n / kprof, "ms_per_launch": round(t, 5),
              "event_ms_per_launch": round(s_["ms"] / n, 5), "alu_frac": round(tc / t, 4),
              "share": round(s_["ms"] / sum(x["ms"] for x in stats), 4)}
-        nc = NCU.get((args.workload, s_["name"]))
+        nc = ncu_row(args.workload, s_["name"], bool(pvar & ks.KS_BCONV_TC))
         if nc:
             k["dram_bytes"] = nc["traffic"]
             k["algo_bytes"] = s_["bytes"] / n
