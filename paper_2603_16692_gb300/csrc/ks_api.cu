@@ -751,6 +751,8 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   const size_t bytes = persist_bytes(*pb), soff = persist_state_offset(*pb);
   int nj = 0, nw = 0, nc = 0;
   persist_counts(*pb, &nj, &nw, &nc);
+  int stage_off[kPersistStages + 1];
+  persist_stage_offsets(*pb, stage_off);
   int rc = KS_OK;
   void *buf = nullptr;
   if (graph && !stall) {
@@ -779,8 +781,14 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   rc = persist_upload(*pb, buf, s);
   persist_free(pb);
   if (rc) return rc;
+  // the stage-major kernels; the one-launch dataflow kernel (tile-level dependency
+  // counters, bounded waits) for the failure-detection test
+  auto launch = [&](cudaStream_t q) {
+    return stall ? persist_launch(buf, nj, nw, nc, soff, kPersistWaitNs, true, q)
+                 : persist_launch_staged(buf, nj, stage_off, nc, soff, q);
+  };
   if (!(graph && !stall)) {
-    rc = persist_launch(buf, nj, nw, nc, soff, kPersistWaitNs, stall, s);
+    rc = launch(s);
     if (rc == KS_OK) {
       g_batch.last_state_buf = buf;
       g_batch.last_state_off = soff;
@@ -789,7 +797,7 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   }
   cudaStream_t cs = g_batch.capture_stream();
   KS_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  rc = persist_launch(buf, nj, nw, nc, soff, kPersistWaitNs, false, cs);
+  rc = launch(cs);
   cudaGraph_t gr = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &gr);
   if (rc == KS_OK && e != cudaSuccess) rc = cuda_rc(e);

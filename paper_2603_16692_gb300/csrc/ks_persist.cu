@@ -79,7 +79,8 @@ struct PState {
   int abort;
   int err;
   int pad;
-  int cnt[1];  // dependency counters
+  int snext[kStages];  // next item of each stage (stage-major launches)
+  int cnt[1];          // dependency counters
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -204,6 +205,101 @@ __global__ void __launch_bounds__(kPNT, 3) k_persist(const PJob *__restrict__ jo
   }
 }
 
+constexpr int cmax_(int a, int b) { return a > b ? a : b; }
+
+// Stage-major form: one persistent kernel per stage over every job's tiles of that
+// stage, the kernels chained by programmatic dependent launch (each tile body waits for
+// the previous stage's kernel before it reads a buffer another stage wrote). A stage
+// has no dependencies inside itself, so its CTAs only claim items: no waits. Each
+// stage kernel holds one stage body per N (its own register budget) and its own block
+// size: 256 threads for the column passes (tiles of 2^10 points at radix 4, 2^11 at
+// radix 8), 128 for the row passes (2^9 at radix 4, 2^10 at radix 8).
+template <int S>
+struct SCfg {
+  static constexpr bool ROW = S == 0 || S == 3 || S == 4 || S == 7;
+  static constexpr int NT = ROW ? 128 : 256;
+  // resident blocks per SM (register budget): 64 registers, except the key multiply
+  // (128) and the basis-conversion column passes (80), which spill at 64
+  static constexpr int MINB = S == 3 ? 4 : S == 2 || S == 6 ? 3 : ROW ? 8 : 4;
+};
+__host__ __device__ constexpr int srl_row(int logn) { return geo_tile_log_row(logn) - 7; }
+
+template <int LOGN, int S>
+__device__ __forceinline__ void sstage(const PJob &J, int bx, int by, unsigned char *raw,
+                                       u64 *cst) {
+  constexpr int RC = prl_col(LOGN), RR = srl_row(LOGN);
+  if constexpr (S == 0) kern::inv_row_body<LOGN, RR>(J.a, J.jp, J.wo, 0, bx, by, raw);
+  if constexpr (S == 1) kern::inv_col_body<LOGN, RC, 0>(J.a, J.jp, J.wo, 0, bx, by, raw);
+  if constexpr (S == 2)
+    kern::fwd_col_body<LOGN, RC, kern::PRO_UP, 0>(J.a, J.jp, J.wo, J.up, BUF_TMP, bx, by, raw,
+                                                  cst);
+  if constexpr (S == 3)
+    kern::keymult_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.tg, bx, by, raw, cst);
+  if constexpr (S == 4) kern::inv_row_body<LOGN, RR>(J.a, J.jp, J.wo, 1, bx, by, raw);
+  if constexpr (S == 5) kern::inv_col_body<LOGN, RC, 0>(J.a, J.jp, J.wo, 1, bx, by, raw);
+  if constexpr (S == 6)
+    kern::fwd_col_body<LOGN, RC, kern::PRO_DOWN, 0>(J.a, J.jp, J.wo, J.dn, BUF_TMP2, bx, by, raw,
+                                                    cst);
+  if constexpr (S == 7)
+    kern::moddown_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.d1, bx, by, raw, cst);
+}
+
+// Items [off, off + n) of the work list (all of stage S), claimed one at a time.
+template <int S>
+__global__ void __launch_bounds__(SCfg<S>::NT, SCfg<S>::MINB)
+    k_pstage(const PJob *__restrict__ jobs, const PWork *__restrict__ work, int off, int n,
+             PState *st) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __shared__ u64 cst[kMaxLimbs];
+  __shared__ PJob J;
+  __shared__ int item, cur_job;
+  if (threadIdx.x == 0) cur_job = -1;
+  while (true) {
+    if (threadIdx.x == 0) item = atomicAdd(&st->snext[S], 1);
+    __syncthreads();
+    const int k = item;
+    if (k >= n) break;
+    const PWork w = work[off + k];
+    if (w.job != cur_job) {
+      const int *src = reinterpret_cast<const int *>(jobs + w.job);
+      int *dst = reinterpret_cast<int *>(&J);
+      for (int q = threadIdx.x; q < (int)(sizeof(PJob) / sizeof(int)); q += SCfg<S>::NT)
+        dst[q] = src[q];
+      __syncthreads();
+      if (threadIdx.x == 0) cur_job = w.job;
+    }
+    switch (J.logn) {
+      case 13: sstage<13, S>(J, w.bx, w.by, raw, cst); break;
+      case 14: sstage<14, S>(J, w.bx, w.by, raw, cst); break;
+      case 15: sstage<15, S>(J, w.bx, w.by, raw, cst); break;
+      case 16: sstage<16, S>(J, w.bx, w.by, raw, cst); break;
+      default: sstage<17, S>(J, w.bx, w.by, raw, cst); break;
+    }
+    // this tile's generic shared-memory reads before the next tile's bulk copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+  }
+  pdl_trigger();
+}
+
+template <int S, int LOGN>
+constexpr int ssmem_one() {
+  return SCfg<S>::ROW ? GeoT<LOGN, srl_row(LOGN), 1>::SMEM_ROW
+                      : GeoT<LOGN, prl_col(LOGN), 0>::SMEM_COL;
+}
+template <int S>
+constexpr int ssmem() {
+  return cmax_(cmax_(cmax_(ssmem_one<S, 13>(), ssmem_one<S, 14>()),
+                     cmax_(ssmem_one<S, 15>(), ssmem_one<S, 16>())),
+               ssmem_one<S, 17>());
+}
+template <int LOGN>
+constexpr bool snt_ok() {
+  return GeoT<LOGN, srl_row(LOGN), 1>::NT == 128 && GeoT<LOGN, prl_col(LOGN), 0>::NT == 256;
+}
+static_assert(snt_ok<13>() && snt_ok<14>() && snt_ok<15>() && snt_ok<16>() && snt_ok<17>(),
+              "one block size per pass kind");
+
 template <int LOGN>
 constexpr int smem_of() {
   using GC = GeoT<LOGN, prl_col(LOGN), 0>;
@@ -236,7 +332,12 @@ struct PersistBatch {
   std::vector<PJob> jobs;
   std::vector<PWork> work;
   int ncnt = 0;
+  int soff[kStages + 1] = {};  // work[soff[s] .. soff[s + 1]) is stage s
 };
+
+void persist_stage_offsets(const PersistBatch &pb, int *off) {
+  for (int s = 0; s <= kStages; ++s) off[s] = pb.soff[s];
+}
 
 bool persist_supported(const ks_context *c) { return c->logn >= 13 && c->logn <= 17; }
 
@@ -342,7 +443,8 @@ void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
     w.sig = sig;
     pb.work.push_back(w);
   };
-  for (int s = 0; s < kStages; ++s)
+  for (int s = 0; s < kStages; ++s) {
+    pb.soff[s] = (int)pb.work.size();
     for (int kk = 0; kk < n; ++kk) {
       const int k = ord[kk];
       const ks_context *c = ctx[k];
@@ -402,6 +504,8 @@ void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
           break;
       }
     }
+  }
+  pb.soff[kStages] = (int)pb.work.size();
 }
 
 size_t persist_state_bytes(int ncnt) { return sizeof(PState) + sizeof(int) * (size_t)ncnt; }
@@ -456,6 +560,73 @@ int persist_launch(void *dev, int njobs, int nwork, int ncnt, size_t state_offse
   k_persist<<<grid, kPNT, kPSmem, s>>>((const PJob *)base, (const PWork *)(base + jb), nwork, st,
                                        limit_ns);
   return cudaGetLastError() == cudaSuccess ? KS_OK : KS_ECUDA;
+}
+
+namespace {
+template <int S>
+cudaError_t stage_prepare(int *blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_pstage<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ssmem<S>());
+  if (!e)
+    e = cudaFuncSetAttribute(k_pstage<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (!e)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pstage<S>, SCfg<S>::NT,
+                                                      ssmem<S>());
+  return e;
+}
+template <int S>
+cudaError_t stage_launch(const PJob *jobs, const PWork *work, const int *off, PState *st,
+                         int grid_max, cudaStream_t s) {
+  const int n = off[S + 1] - off[S];
+  if (n == 0) return cudaSuccess;
+  const int grid = std::max(1, std::min(n, grid_max));
+  if (S == 0) {  // after the state reset: an ordinary dependency
+    k_pstage<S><<<grid, SCfg<S>::NT, ssmem<S>(), s>>>(jobs, work, off[S], n, st);
+    return cudaGetLastError();
+  }
+  return launch_pdl(k_pstage<S>, dim3(grid), dim3(SCfg<S>::NT), ssmem<S>(), s, jobs, work, off[S],
+                    n, st);
+}
+}  // namespace
+
+// Reset the state and launch the stage-major kernels over an uploaded image
+// (capturable): eight launches, each stage's kernel waiting for the previous one.
+int persist_launch_staged(void *dev, int njobs, const int *off, int ncnt, size_t state_offset,
+                          cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  static int bps[kStages] = {}, sms = 0;
+  std::call_once(once, [] {
+    int d = 0;
+    attr = cudaGetDevice(&d);
+    if (!attr) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+    if (!attr) attr = stage_prepare<0>(&bps[0]);
+    if (!attr) attr = stage_prepare<1>(&bps[1]);
+    if (!attr) attr = stage_prepare<2>(&bps[2]);
+    if (!attr) attr = stage_prepare<3>(&bps[3]);
+    if (!attr) attr = stage_prepare<4>(&bps[4]);
+    if (!attr) attr = stage_prepare<5>(&bps[5]);
+    if (!attr) attr = stage_prepare<6>(&bps[6]);
+    if (!attr) attr = stage_prepare<7>(&bps[7]);
+  });
+  if (attr != cudaSuccess) return KS_ECUDA;
+  for (int k = 0; k < kStages; ++k)
+    if (bps[k] < 1) return KS_ECUDA;
+  char *base = (char *)dev;
+  const PJob *jobs = (const PJob *)base;
+  const PWork *work = (const PWork *)(base + align16((size_t)njobs * sizeof(PJob)));
+  PState *st = (PState *)(base + state_offset);
+  cudaError_t e = cudaMemsetAsync(st, 0, persist_state_bytes(ncnt), s);
+  if (!e) e = stage_launch<0>(jobs, work, off, st, bps[0] * sms, s);
+  if (!e) e = stage_launch<1>(jobs, work, off, st, bps[1] * sms, s);
+  if (!e) e = stage_launch<2>(jobs, work, off, st, bps[2] * sms, s);
+  if (!e) e = stage_launch<3>(jobs, work, off, st, bps[3] * sms, s);
+  if (!e) e = stage_launch<4>(jobs, work, off, st, bps[4] * sms, s);
+  if (!e) e = stage_launch<5>(jobs, work, off, st, bps[5] * sms, s);
+  if (!e) e = stage_launch<6>(jobs, work, off, st, bps[6] * sms, s);
+  if (!e) e = stage_launch<7>(jobs, work, off, st, bps[7] * sms, s);
+  return e == cudaSuccess ? KS_OK : KS_ECUDA;
 }
 
 // Error word of a persistent launch whose state is at dev + state_offset (synchronizes s).
