@@ -368,9 +368,10 @@ def batch_measure(args, ks, torch, dev, stream, hbm):
            "persistent": {"value": len(jobs) / (ms_p / 1e3), "ms_per_batch": ms_p,
                           "status": ks.strerror(p_status),
                           "speedup_vs_best_fixed": len(jobs) / (ms_p / 1e3) / plain[best_name],
-                          "form": "eight persistent kernels, one per stage over all 64 "
-                                  "jobs' tiles, chained by programmatic dependent launch "
-                                  "(graph replay)"}}
+                          "form": "persistent kernels, one per stage over all 64 jobs' "
+                                  "tiles (key multiply and ModDown rows in two, by row-tile "
+                                  "size), chained by programmatic dependent launch (graph "
+                                  "replay)"}}
     if sel_info and "batch_value" in sel_info:
         out["selector_speedup_vs_best_fixed"] = sel_info["batch_value"] / plain[best_name]
     for c in ctxs.values():

@@ -312,8 +312,8 @@ typedef struct {
 #define KS_BATCH_GRAPH 0x1    /* capture the batch in a CUDA graph, replay it on later
                                  calls with the same jobs (same pointers) */
 #define KS_BATCH_AUTOTUNE 0x2 /* ks_tune each context first (once per group size) */
-#define KS_BATCH_PERSISTENT 0x4 /* run the whole batch in eight persistent kernels, one
-                                   per stage over every job (every job's N in
+#define KS_BATCH_PERSISTENT 0x4 /* run the whole batch in persistent kernels, one per
+                                   stage over every job (every job's N in
                                    2^13..2^17; plans DPOB, fused) */
 #define KS_BATCH_SELECT 0x8  /* jobs naming KS_AUTO run the plan of the installed selector
                                 network (ks_select, run once per context and selector);
@@ -323,11 +323,11 @@ typedef struct {
                                      dependencies unreachable, so that the bounded wait
                                      gives up and ks_batch_status reports KS_ETIMEOUT */
 
-/* With KS_BATCH_PERSISTENT, eight kernel launches run the batch, one per stage (input
+/* With KS_BATCH_PERSISTENT, one persistent kernel per stage runs the batch (input
  * iNTT rows, columns, ModUp, key multiply, accumulator iNTT rows, columns, ModDown
- * columns, ModDown rows): each launch's CTAs claim the tiles of that stage of every
- * job, and each stage's launch waits for the previous one (programmatic dependent
- * launch). With KS_BATCH_TEST_STALL the batch runs instead as one dataflow kernel
+ * columns, ModDown rows; the key multiply and ModDown rows in two launches, N >= 2^16
+ * and N <= 2^15): each launch's CTAs claim the tiles of that stage of every job, and
+ * each launch waits for the previous one (programmatic dependent launch). With KS_BATCH_TEST_STALL the batch runs instead as one dataflow kernel
  * whose tiles wait, with a bounded wait (about 2 s of device time), for the tiles they
  * read; a wait that runs out sets a device error word and every CTA returns;
  * ks_batch_status then reports KS_ETIMEOUT. The persistent grids assume they have the

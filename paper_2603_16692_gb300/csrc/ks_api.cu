@@ -751,7 +751,7 @@ int batch_persistent(const ks_job *jobs, int njobs, int flags, cudaStream_t s) {
   const size_t bytes = persist_bytes(*pb), soff = persist_state_offset(*pb);
   int nj = 0, nw = 0, nc = 0;
   persist_counts(*pb, &nj, &nw, &nc);
-  int stage_off[kPersistStages + 1];
+  int stage_off[kPersistStages + 3];
   persist_stage_offsets(*pb, stage_off);
   int rc = KS_OK;
   void *buf = nullptr;

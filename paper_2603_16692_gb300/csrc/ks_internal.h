@@ -280,8 +280,10 @@ size_t persist_bytes(const PersistBatch &pb);
 size_t persist_state_offset(const PersistBatch &pb);
 int persist_counts(const PersistBatch &pb, int *njobs, int *nwork, int *ncnt);
 int persist_upload(const PersistBatch &pb, void *dev, cudaStream_t s);
-// Stage-major form: the work list's stage boundaries (kPersistStages + 1 offsets), and
-// the launch of one persistent kernel per stage (no waits inside a kernel).
+// Stage-major form: the work list's stage boundaries (kPersistStages + 1 offsets, then
+// the ends of the key-multiply and ModDown-row items of N >= 2^16 jobs, which come first
+// in their stages), and the launch of one persistent kernel per stage (two for those
+// stages; no waits inside a kernel).
 constexpr int kPersistStages = 8;
 void persist_stage_offsets(const PersistBatch &pb, int *off);
 int persist_launch_staged(void *dev, int njobs, const int *stage_off, int ncnt,

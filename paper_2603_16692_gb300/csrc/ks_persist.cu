@@ -79,7 +79,7 @@ struct PState {
   int abort;
   int err;
   int pad;
-  int snext[kStages];  // next item of each stage (stage-major launches)
+  int snext[kStages + 2];  // next item of each stage-major launch
   int cnt[1];          // dependency counters
 };
 
@@ -214,13 +214,19 @@ constexpr int cmax_(int a, int b) { return a > b ? a : b; }
 // stage kernel holds one stage body per N (its own register budget) and its own block
 // size: 256 threads for the column passes (tiles of 2^10 points at radix 4, 2^11 at
 // radix 8), 128 for the row passes (2^9 at radix 4, 2^10 at radix 8).
-template <int S>
+// CLS: the key multiply and the ModDown row pass (stages 3 and 7) run in two launches,
+// N <= 2^15 (CLS 1: 2^9-point row tiles, 128 threads) and N >= 2^16 (CLS 2: 2^10-point
+// row tiles, 256 threads), both with the software-pipelined radix-4 bodies; every other
+// stage is one launch (CLS 0).
+template <int S, int CLS = 0>
 struct SCfg {
   static constexpr bool ROW = S == 0 || S == 3 || S == 4 || S == 7;
-  static constexpr int NT = ROW ? 128 : 256;
-  // resident blocks per SM (register budget): 64 registers, except the key multiply
-  // (128) and the basis-conversion column passes (80), which spill at 64
-  static constexpr int MINB = S == 3 ? 4 : S == 2 || S == 6 ? 3 : ROW ? 8 : 4;
+  static constexpr bool PIPE = S == 3 || S == 7;
+  static constexpr int NT = PIPE ? (CLS == 2 ? 256 : 128) : ROW ? 128 : 256;
+  // resident blocks per SM (register budget): 64 registers, except the basis-conversion
+  // column passes (80), which spill at 64
+  static constexpr int MINB = S == 2 || S == 6 ? 3 : 1024 / NT;
+  static constexpr int LO = CLS == 2 ? 16 : 13, HI = CLS == 1 ? 15 : 17;  // log N range
 };
 __host__ __device__ constexpr int srl_row(int logn) { return geo_tile_log_row(logn) - 7; }
 
@@ -228,34 +234,35 @@ template <int LOGN, int S>
 __device__ __forceinline__ void sstage(const PJob &J, int bx, int by, unsigned char *raw,
                                        u64 *cst) {
   constexpr int RC = prl_col(LOGN), RR = srl_row(LOGN);
+  static_assert(kern::ROW_PIPE<LOGN, 2>, "pipelined row bodies at two-pass sizes");
   if constexpr (S == 0) kern::inv_row_body<LOGN, RR>(J.a, J.jp, J.wo, 0, bx, by, raw);
   if constexpr (S == 1) kern::inv_col_body<LOGN, RC, 0>(J.a, J.jp, J.wo, 0, bx, by, raw);
   if constexpr (S == 2)
     kern::fwd_col_body<LOGN, RC, kern::PRO_UP, 0>(J.a, J.jp, J.wo, J.up, BUF_TMP, bx, by, raw,
                                                   cst);
-  if constexpr (S == 3)
-    kern::keymult_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.tg, bx, by, raw, cst);
+  if constexpr (S == 3) kern::keymult_pipe_body<LOGN, 2>(J.a, J.jp, J.wo, J.tg, bx, by, raw);
   if constexpr (S == 4) kern::inv_row_body<LOGN, RR>(J.a, J.jp, J.wo, 1, bx, by, raw);
   if constexpr (S == 5) kern::inv_col_body<LOGN, RC, 0>(J.a, J.jp, J.wo, 1, bx, by, raw);
   if constexpr (S == 6)
     kern::fwd_col_body<LOGN, RC, kern::PRO_DOWN, 0>(J.a, J.jp, J.wo, J.dn, BUF_TMP2, bx, by, raw,
                                                     cst);
-  if constexpr (S == 7)
-    kern::moddown_body<LOGN, RR, kern::PRO_LOAD>(J.a, J.jp, J.wo, J.d1, bx, by, raw, cst);
+  if constexpr (S == 7) kern::moddown_pipe_body<LOGN, 2>(J.a, J.jp, J.wo, J.d1, bx, by, raw);
 }
 
-// Items [off, off + n) of the work list (all of stage S), claimed one at a time.
-template <int S>
-__global__ void __launch_bounds__(SCfg<S>::NT, SCfg<S>::MINB)
+// Items [off, off + n) of the work list (all of stage S, of class CLS), claimed one at a
+// time through counter st->snext[ctr].
+template <int S, int CLS>
+__global__ void __launch_bounds__(SCfg<S, CLS>::NT, SCfg<S, CLS>::MINB)
     k_pstage(const PJob *__restrict__ jobs, const PWork *__restrict__ work, int off, int n,
-             PState *st) {
+             PState *st, int ctr) {
+  using C = SCfg<S, CLS>;
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ u64 cst[kMaxLimbs];
   __shared__ PJob J;
   __shared__ int item, cur_job;
   if (threadIdx.x == 0) cur_job = -1;
   while (true) {
-    if (threadIdx.x == 0) item = atomicAdd(&st->snext[S], 1);
+    if (threadIdx.x == 0) item = atomicAdd(&st->snext[ctr], 1);
     __syncthreads();
     const int k = item;
     if (k >= n) break;
@@ -263,17 +270,29 @@ __global__ void __launch_bounds__(SCfg<S>::NT, SCfg<S>::MINB)
     if (w.job != cur_job) {
       const int *src = reinterpret_cast<const int *>(jobs + w.job);
       int *dst = reinterpret_cast<int *>(&J);
-      for (int q = threadIdx.x; q < (int)(sizeof(PJob) / sizeof(int)); q += SCfg<S>::NT)
-        dst[q] = src[q];
+      for (int q = threadIdx.x; q < (int)(sizeof(PJob) / sizeof(int)); q += C::NT) dst[q] = src[q];
       __syncthreads();
       if (threadIdx.x == 0) cur_job = w.job;
     }
-    switch (J.logn) {
-      case 13: sstage<13, S>(J, w.bx, w.by, raw, cst); break;
-      case 14: sstage<14, S>(J, w.bx, w.by, raw, cst); break;
-      case 15: sstage<15, S>(J, w.bx, w.by, raw, cst); break;
-      case 16: sstage<16, S>(J, w.bx, w.by, raw, cst); break;
-      default: sstage<17, S>(J, w.bx, w.by, raw, cst); break;
+    if constexpr (C::LO == 16) {
+      if (J.logn == 16)
+        sstage<16, S>(J, w.bx, w.by, raw, cst);
+      else
+        sstage<17, S>(J, w.bx, w.by, raw, cst);
+    } else if constexpr (C::HI == 15) {
+      switch (J.logn) {
+        case 13: sstage<13, S>(J, w.bx, w.by, raw, cst); break;
+        case 14: sstage<14, S>(J, w.bx, w.by, raw, cst); break;
+        default: sstage<15, S>(J, w.bx, w.by, raw, cst); break;
+      }
+    } else {
+      switch (J.logn) {
+        case 13: sstage<13, S>(J, w.bx, w.by, raw, cst); break;
+        case 14: sstage<14, S>(J, w.bx, w.by, raw, cst); break;
+        case 15: sstage<15, S>(J, w.bx, w.by, raw, cst); break;
+        case 16: sstage<16, S>(J, w.bx, w.by, raw, cst); break;
+        default: sstage<17, S>(J, w.bx, w.by, raw, cst); break;
+      }
     }
     // this tile's generic shared-memory reads before the next tile's bulk copies
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -284,18 +303,29 @@ __global__ void __launch_bounds__(SCfg<S>::NT, SCfg<S>::MINB)
 
 template <int S, int LOGN>
 constexpr int ssmem_one() {
-  return SCfg<S>::ROW ? GeoT<LOGN, srl_row(LOGN), 1>::SMEM_ROW
-                      : GeoT<LOGN, prl_col(LOGN), 0>::SMEM_COL;
+  using GR = GeoT<LOGN, 2, 1>;
+  return S == 3   ? kern::KmSmem<GR>::BYTES
+         : S == 7 ? kern::MdSmem<GR>::BYTES
+         : SCfg<S>::ROW ? GeoT<LOGN, srl_row(LOGN), 1>::SMEM_ROW
+                        : GeoT<LOGN, prl_col(LOGN), 0>::SMEM_COL;
 }
-template <int S>
+template <int S, int CLS>
 constexpr int ssmem() {
-  return cmax_(cmax_(cmax_(ssmem_one<S, 13>(), ssmem_one<S, 14>()),
-                     cmax_(ssmem_one<S, 15>(), ssmem_one<S, 16>())),
-               ssmem_one<S, 17>());
+  int m = 0;
+  for (int l = SCfg<S, CLS>::LO; l <= SCfg<S, CLS>::HI; ++l) {
+    const int v = l == 13   ? ssmem_one<S, 13>()
+                  : l == 14 ? ssmem_one<S, 14>()
+                  : l == 15 ? ssmem_one<S, 15>()
+                  : l == 16 ? ssmem_one<S, 16>()
+                            : ssmem_one<S, 17>();
+    m = cmax_(m, v);
+  }
+  return m;
 }
 template <int LOGN>
 constexpr bool snt_ok() {
-  return GeoT<LOGN, srl_row(LOGN), 1>::NT == 128 && GeoT<LOGN, prl_col(LOGN), 0>::NT == 256;
+  return GeoT<LOGN, srl_row(LOGN), 1>::NT == 128 && GeoT<LOGN, prl_col(LOGN), 0>::NT == 256 &&
+         GeoT<LOGN, 2, 1>::NT == (LOGN >= 16 ? 256 : 128);
 }
 static_assert(snt_ok<13>() && snt_ok<14>() && snt_ok<15>() && snt_ok<16>() && snt_ok<17>(),
               "one block size per pass kind");
@@ -333,10 +363,14 @@ struct PersistBatch {
   std::vector<PWork> work;
   int ncnt = 0;
   int soff[kStages + 1] = {};  // work[soff[s] .. soff[s + 1]) is stage s
+  int big_end[kStages] = {};    // stages 3 and 7: items of N >= 2^16 jobs first, up to here
 };
 
+// kStages + 1 stage boundaries, then the ends of stage 3's and stage 7's N >= 2^16 items.
 void persist_stage_offsets(const PersistBatch &pb, int *off) {
   for (int s = 0; s <= kStages; ++s) off[s] = pb.soff[s];
+  off[kStages + 1] = pb.big_end[3];
+  off[kStages + 2] = pb.big_end[7];
 }
 
 bool persist_supported(const ks_context *c) { return c->logn >= 13 && c->logn <= 17; }
@@ -506,6 +540,12 @@ void persist_build(PersistBatch &pb, const std::vector<const ks_context *> &ctx,
     }
   }
   pb.soff[kStages] = (int)pb.work.size();
+  // stages 3 and 7 run as two launches by row-tile size: N >= 2^16 items first
+  for (int st : {3, 7}) {
+    auto b = pb.work.begin() + pb.soff[st], e = pb.work.begin() + pb.soff[st + 1];
+    auto mid = std::stable_partition(b, e, [&](const PWork &w) { return pb.jobs[w.job].logn >= 16; });
+    pb.big_end[st] = (int)(mid - pb.work.begin());
+  }
 }
 
 size_t persist_state_bytes(int ncnt) { return sizeof(PState) + sizeof(int) * (size_t)ncnt; }
@@ -563,69 +603,76 @@ int persist_launch(void *dev, int njobs, int nwork, int ncnt, size_t state_offse
 }
 
 namespace {
-template <int S>
+template <int S, int CLS>
 cudaError_t stage_prepare(int *blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_pstage<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ssmem<S>());
+  cudaError_t e = cudaFuncSetAttribute(k_pstage<S, CLS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ssmem<S, CLS>());
   if (!e)
-    e = cudaFuncSetAttribute(k_pstage<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_pstage<S, CLS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (!e)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pstage<S>, SCfg<S>::NT,
-                                                      ssmem<S>());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pstage<S, CLS>,
+                                                      SCfg<S, CLS>::NT, ssmem<S, CLS>());
   return e;
 }
-template <int S>
-cudaError_t stage_launch(const PJob *jobs, const PWork *work, const int *off, PState *st,
-                         int grid_max, cudaStream_t s) {
-  const int n = off[S + 1] - off[S];
+// Items [b, e) of the work list through counter ctr.
+template <int S, int CLS>
+cudaError_t stage_launch(const PJob *jobs, const PWork *work, int b, int e, int ctr, PState *st,
+                         int grid_max, bool first, cudaStream_t s) {
+  const int n = e - b;
   if (n == 0) return cudaSuccess;
   const int grid = std::max(1, std::min(n, grid_max));
-  if (S == 0) {  // after the state reset: an ordinary dependency
-    k_pstage<S><<<grid, SCfg<S>::NT, ssmem<S>(), s>>>(jobs, work, off[S], n, st);
+  if (first) {  // after the state reset: an ordinary dependency
+    k_pstage<S, CLS><<<grid, SCfg<S, CLS>::NT, ssmem<S, CLS>(), s>>>(jobs, work, b, n, st, ctr);
     return cudaGetLastError();
   }
-  return launch_pdl(k_pstage<S>, dim3(grid), dim3(SCfg<S>::NT), ssmem<S>(), s, jobs, work, off[S],
-                    n, st);
+  return launch_pdl(k_pstage<S, CLS>, dim3(grid), dim3(SCfg<S, CLS>::NT), ssmem<S, CLS>(), s,
+                    jobs, work, b, n, st, ctr);
 }
 }  // namespace
 
 // Reset the state and launch the stage-major kernels over an uploaded image
-// (capturable): eight launches, each stage's kernel waiting for the previous one.
+// (capturable): ten launches (stages 3 and 7 in two), each waiting for the previous one.
 int persist_launch_staged(void *dev, int njobs, const int *off, int ncnt, size_t state_offset,
                           cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
-  static int bps[kStages] = {}, sms = 0;
+  static int bps[kStages + 2] = {}, sms = 0;
   std::call_once(once, [] {
     int d = 0;
     attr = cudaGetDevice(&d);
     if (!attr) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
-    if (!attr) attr = stage_prepare<0>(&bps[0]);
-    if (!attr) attr = stage_prepare<1>(&bps[1]);
-    if (!attr) attr = stage_prepare<2>(&bps[2]);
-    if (!attr) attr = stage_prepare<3>(&bps[3]);
-    if (!attr) attr = stage_prepare<4>(&bps[4]);
-    if (!attr) attr = stage_prepare<5>(&bps[5]);
-    if (!attr) attr = stage_prepare<6>(&bps[6]);
-    if (!attr) attr = stage_prepare<7>(&bps[7]);
+    if (!attr) attr = stage_prepare<0, 0>(&bps[0]);
+    if (!attr) attr = stage_prepare<1, 0>(&bps[1]);
+    if (!attr) attr = stage_prepare<2, 0>(&bps[2]);
+    if (!attr) attr = stage_prepare<3, 2>(&bps[3]);
+    if (!attr) attr = stage_prepare<3, 1>(&bps[8]);
+    if (!attr) attr = stage_prepare<4, 0>(&bps[4]);
+    if (!attr) attr = stage_prepare<5, 0>(&bps[5]);
+    if (!attr) attr = stage_prepare<6, 0>(&bps[6]);
+    if (!attr) attr = stage_prepare<7, 2>(&bps[7]);
+    if (!attr) attr = stage_prepare<7, 1>(&bps[9]);
   });
   if (attr != cudaSuccess) return KS_ECUDA;
-  for (int k = 0; k < kStages; ++k)
+  for (int k = 0; k < kStages + 2; ++k)
     if (bps[k] < 1) return KS_ECUDA;
   char *base = (char *)dev;
   const PJob *jobs = (const PJob *)base;
   const PWork *work = (const PWork *)(base + align16((size_t)njobs * sizeof(PJob)));
   PState *st = (PState *)(base + state_offset);
+  const int e3 = off[kStages + 1], e7 = off[kStages + 2];
   cudaError_t e = cudaMemsetAsync(st, 0, persist_state_bytes(ncnt), s);
-  if (!e) e = stage_launch<0>(jobs, work, off, st, bps[0] * sms, s);
-  if (!e) e = stage_launch<1>(jobs, work, off, st, bps[1] * sms, s);
-  if (!e) e = stage_launch<2>(jobs, work, off, st, bps[2] * sms, s);
-  if (!e) e = stage_launch<3>(jobs, work, off, st, bps[3] * sms, s);
-  if (!e) e = stage_launch<4>(jobs, work, off, st, bps[4] * sms, s);
-  if (!e) e = stage_launch<5>(jobs, work, off, st, bps[5] * sms, s);
-  if (!e) e = stage_launch<6>(jobs, work, off, st, bps[6] * sms, s);
-  if (!e) e = stage_launch<7>(jobs, work, off, st, bps[7] * sms, s);
+  if (!e) e = stage_launch<0, 0>(jobs, work, off[0], off[1], 0, st, bps[0] * sms, true, s);
+  if (!e) e = stage_launch<1, 0>(jobs, work, off[1], off[2], 1, st, bps[1] * sms, false, s);
+  if (!e) e = stage_launch<2, 0>(jobs, work, off[2], off[3], 2, st, bps[2] * sms, false, s);
+  if (!e) e = stage_launch<3, 2>(jobs, work, off[3], e3, 3, st, bps[3] * sms, false, s);
+  if (!e) e = stage_launch<3, 1>(jobs, work, e3, off[4], 8, st, bps[8] * sms, false, s);
+  if (!e) e = stage_launch<4, 0>(jobs, work, off[4], off[5], 4, st, bps[4] * sms, false, s);
+  if (!e) e = stage_launch<5, 0>(jobs, work, off[5], off[6], 5, st, bps[5] * sms, false, s);
+  if (!e) e = stage_launch<6, 0>(jobs, work, off[6], off[7], 6, st, bps[6] * sms, false, s);
+  if (!e) e = stage_launch<7, 2>(jobs, work, off[7], e7, 7, st, bps[7] * sms, false, s);
+  if (!e) e = stage_launch<7, 1>(jobs, work, e7, off[8], 9, st, bps[9] * sms, false, s);
   return e == cudaSuccess ? KS_OK : KS_ECUDA;
 }
 
