@@ -626,9 +626,13 @@ def main():
     wss = [torch.empty(nws, dtype=torch.uint64, device=dev) for _ in range(MAX_STREAMS)]
     ws = wss[0]
     streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(MAX_STREAMS - 1)]
-    scalls = [[ks.prepare_switch(ctx.h, d, evk, out, variant, args.chunks, wss[q], streams[q])
-               for d, evk, out in sets] for q in range(MAX_STREAMS)]
-    calls = scalls[0]
+    # plans for KeySwitches in flight: the tuned plan, and without its split ModDown (the
+    # split forks onto the context's one side stream, which streams in flight share)
+    cands = [variant] + ([variant & ~ks.KS_SPLIT_DOWN] if variant & ks.KS_SPLIT_DOWN else [])
+    scalls_by = {v: [[ks.prepare_switch(ctx.h, d, evk, out, v, args.chunks, wss[q], streams[q])
+                      for d, evk, out in sets] for q in range(MAX_STREAMS)] for v in cands}
+    scalls = scalls_by[variant]
+    calls = scalls[0]  # one stream, warm L2, host cost, profile: the tuned plan
 
     def run_streams(nstreams, n, k0=0):
         """n steps (KeySwitch k on stream k mod nstreams), fork from and join to `stream`."""
@@ -649,11 +653,24 @@ def main():
         torch.cuda.synchronize(dev)
         return n / (e0.elapsed_time(e1) / 1e3)
 
-    # streams in flight: the count with the highest rate on a short probe (ring >= count)
-    probe = {q: rate(q, max(30, 10 * q)) for q in range(1, min(MAX_STREAMS, ring) + 1)}
-    nstreams = max(probe, key=probe.get)
-    plan_info = {"variant": ks.variant_name(variant, args.chunks), "chunks": args.chunks,
-                 "chosen_by": "ks_tune (timed over dataflows x radices)"
+    # streams in flight and their plan: the pair with the highest rate on a short probe
+    # (ring >= count)
+    probe_by_plan = {}
+    for v in cands:
+        scalls = scalls_by[v]
+        probe_by_plan[v] = {q: rate(q, max(30, 10 * q))
+                            for q in range(1, min(MAX_STREAMS, ring) + 1)}
+    run_variant, nstreams = max(((v, q) for v in cands for q in probe_by_plan[v]),
+                                key=lambda vq: probe_by_plan[vq[0]][vq[1]])
+    scalls = scalls_by[run_variant]
+    probe = probe_by_plan[run_variant]
+    plan_info = {"variant": ks.variant_name(run_variant, args.chunks), "chunks": args.chunks,
+                 "tuned_variant": ks.variant_name(variant, args.chunks),
+                 "probe_ks_per_s_by_plan": {ks.variant_name(v, args.chunks): p_
+                                            for v, p_ in probe_by_plan.items()},
+                 "chosen_by": "ks_tune (timed over dataflows x radices; with streams in "
+                               "flight, the tuned plan or the same without its split ModDown, "
+                               "the faster on the probe)"
                  if args.variant.lower() == "tuned" else "--variant",
                  "l2": f"ring of {ring} distinct (d, evk, out) sets, {ring * set_bytes / 1e6:.0f}"
                        f" MB > 2 x L2 ({l2 / 1e6:.0f} MB): every step reads HBM"}
@@ -739,7 +756,10 @@ def main():
     for k in range(kprof):
         pcalls[k % ring]()
     stats = ks.ks_profile_end()
-    launches_per_step = sum(s["launches"] for s in stats) / kprof + (pvar != variant)
+    # the timed plan's launches: the profiled (unsplit) plan's, plus the split key
+    # multiply's second launch when the timed plan splits
+    launches_per_step = sum(s["launches"] for s in stats) / kprof + \
+        (1 if run_variant & ks.KS_SPLIT_DOWN else 0)
 
     # end to end through the host-buffer entry points: a ring of pinned host inputs and
     # outputs; every step's input is read from and its result written to host memory
@@ -785,7 +805,7 @@ def main():
     hstreams = streams + [torch.cuda.Stream(device=dev) for _ in range(e2e_max - MAX_STREAMS)]
     hscr = [torch.empty(hws, dtype=torch.uint64, device=dev) for _ in range(e2e_max)]
     hscalls = [[ks.prepare_switch_host_async_ws(ctx.h, d_hs[k % hring], sets[k % ring][1],
-                                                 out_hs[k % hring], hscr[q], variant,
+                                                 out_hs[k % hring], hscr[q], run_variant,
                                                  args.chunks, hstreams[q])
                 for k in range(period)] for q in range(e2e_max)]
 
