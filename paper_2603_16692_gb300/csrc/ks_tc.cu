@@ -157,7 +157,7 @@ struct TcGeo {
   static constexpr int TILE_W = N1 * PC;  // words of one target's NTT tile
   static constexpr int APMAX = 10;        // K slots (alpha <= 9)
   __host__ __device__ static constexpr int smem(int ap) {
-    return ap * TP * 16 + GRP * 512 * ap + GRP * 2 * TILE_W * 8;
+    return ap * TP * 16 + GRP * 1024 * ap + GRP * 2 * TILE_W * 8;
   }
   static_assert(LOGGC >= 1 && MB % 4 == 0 && (HT / 32) % 4 == 0 && GRP * DCOLS <= 512 &&
                     smem(APMAX) <= 227 * 1024 - 256 && NT + 32 <= 1024,
@@ -185,23 +185,25 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
     k_bconv_tc(KArgs a, JobSet js, WsOff wo, Tasks tk, TcItems ti) {
   using G = TcGeo<LOGN, GRP>;
   extern __shared__ __align__(16) unsigned char raw[];
-  // Per group g: bar_b[g] (the pair's constants landed; releases the pair's info),
-  // bar_m[g] (the MMAs into the group's accumulator completed), bar_tm[g] (every warp
-  // of the group has read the accumulator and the info: both, and the constant buffer,
-  // may be refilled). bar_a: a tile's source bytes landed.
-  __shared__ u64 bar_a, bar_b[GRP], bar_m[GRP], bar_tm[GRP];
+  // Per group g, whose k-th item uses constant buffer and info slot b = k mod 2:
+  // bar_b[g][b] (the pair's constants landed; releases the pair's info), bar_m[g] (the
+  // MMAs into the group's accumulator completed), bar_tm[g] (every warp of the group has
+  // read the accumulator and the info of its item). bar_a: a tile's source bytes landed.
+  // The producer fetches a group's next constants as soon as the group has read its
+  // current sums, so the copy lands while the group finishes its item.
+  __shared__ u64 bar_a, bar_b[GRP][2], bar_m[GRP], bar_tm[GRP];
   __shared__ uint32_t tm_slot;
-  // per group, written by the producer before it arms bar_b: the pair's decoded work
-  // items, how many are real, the tile, and whether both moduli take the fast
+  // per group and slot, written by the producer before it arms bar_b: the pair's decoded
+  // work items, how many are real, the tile, and whether both moduli take the fast
   // butterflies
-  __shared__ uint32_t info_w[GRP][2];
-  __shared__ int info_cnt[GRP], info_tile[GRP], info_fast[GRP];
+  __shared__ uint32_t info_w[GRP][2][2];
+  __shared__ int info_cnt[GRP][2], info_tile[GRP][2], info_fast[GRP][2];
   const JobPtr &jp = js.j[blockIdx.z];
   const int AP = a.tc_ap;
   const int it0 = blockIdx.x * ti.per_cta, it1 = min(ti.items, it0 + ti.per_cta);
   unsigned char *sA = raw;
-  unsigned char *sB = raw + (size_t)AP * G::TP * 16;       // [GRP][2][256 ap]
-  u64 *sT = reinterpret_cast<u64 *>(sB + (size_t)GRP * 512 * AP);  // [GRP][2][TILE_W]
+  unsigned char *sB = raw + (size_t)AP * G::TP * 16;  // [GRP][buffer 2][target 2][256 ap]
+  u64 *sT = reinterpret_cast<u64 *>(sB + (size_t)GRP * 1024 * AP);  // [GRP][2][TILE_W]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int CW = G::NT / 32;  // consumer warps; warp CW is the producer
 
@@ -209,7 +211,8 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
   if (threadIdx.x == 0) {
     mbar_init(&bar_a, 1);
     for (int g = 0; g < GRP; ++g) {
-      mbar_init(&bar_b[g], 1);
+      mbar_init(&bar_b[g][0], 1);
+      mbar_init(&bar_b[g][1], 1);
       mbar_init(&bar_m[g], 1);
       mbar_init(&bar_tm[g], G::GT / 32);
     }
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
   // zero), with bf16 1.0 in the first K element of slot alpha (the 2^23 row); B: zero.
   for (int k = threadIdx.x; k < AP * G::TP; k += blockDim.x)
     reinterpret_cast<uint4 *>(sA)[k] = make_uint4(k / G::TP == a.alpha ? 0x3F80u : 0u, 0, 0, 0);
-  for (int k = threadIdx.x; k < GRP * 32 * AP; k += blockDim.x)
+  for (int k = threadIdx.x; k < GRP * 64 * AP; k += blockDim.x)
     reinterpret_cast<uint4 *>(sB)[k] = make_uint4(0, 0, 0, 0);
   proxy_fence();
   tc_fence_before();
@@ -229,33 +232,44 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
 
   auto target = [&](const TcItem &x, int u) { return decode(a, tk, x.y0 + min(u, x.cnt - 1)); };
   if (warp == CW) {
-    // Producer (one thread): constants, source bytes and MMAs, each group's next item as
-    // soon as the group has read its previous one.
+    // Producer (one thread): constants, source bytes and MMAs.
     if (lane == 0) {
       const u64 *pbase = jp.ws + (PRO == PRO_UP ? wo.pv : wo.ppv);
       const u64 ad0 = smem_desc(smem_u32(sA), G::TP * 16, 128);
+      // item it's constants into its group's buffer (its index in the group mod 2), and
+      // its info into the same slot
+      auto load_b = [&](int it) {
+        const int g = (it - it0) % GRP, b = ((it - it0) / GRP) & 1;
+        const TcItem x = tc_item(ti, it);
+        const uint32_t wp[2] = {target(x, 0), target(x, 1)};
+        info_w[g][b][0] = wp[0];
+        info_w[g][b][1] = wp[1];
+        info_cnt[g][b] = x.cnt;
+        info_tile[g][b] = x.tile;
+        info_fast[g][b] = a.tab.mod[task_limb(wp[0])].m < kFastModulus &&
+                          a.tab.mod[task_limb(wp[1])].m < kFastModulus;
+        mbar_expect_tx(&bar_b[g][b], 2u * 256 * AP);  // releases the info
+        for (int v = 0; v < 2; ++v) {
+          const int t = task_limb(wp[v]);
+          const u64 *src = PRO == PRO_UP
+                               ? a.tab.bup + ((size_t)task_dig(wp[v]) * a.qp + t) * 32 * AP
+                               : a.tab.bdown + (size_t)t * 32 * AP;
+          bulk_g2s(sB + (size_t)((g * 2 + b) * 2 + v) * 256 * AP, src, 256 * AP, &bar_b[g][b]);
+        }
+      };
+      for (int it = it0; it < it1 && it < it0 + GRP; ++it) load_b(it);
       unsigned pha = 0;
       int cur_tile = -1, cur_set = -1;
       for (int it = it0; it < it1; ++it) {
         const int g = (it - it0) % GRP;
         const unsigned k = (unsigned)(it - it0) / GRP;  // the group's k-th item
+        const int b = k & 1;
         const TcItem x = tc_item(ti, it);
+        // the group has read the sums and the info of its previous item (so its MMAs,
+        // the last readers of the other constant buffer, are done): fetch the group's
+        // next constants into that buffer while this item runs
         if (k > 0 && !mbar_wait(&bar_tm[g], (k - 1) & 1)) atomicExch(a.tab.err, 1);
-        const uint32_t wp[2] = {target(x, 0), target(x, 1)};
-        info_w[g][0] = wp[0];
-        info_w[g][1] = wp[1];
-        info_cnt[g] = x.cnt;
-        info_tile[g] = x.tile;
-        info_fast[g] = a.tab.mod[task_limb(wp[0])].m < kFastModulus &&
-                       a.tab.mod[task_limb(wp[1])].m < kFastModulus;
-        mbar_expect_tx(&bar_b[g], 2u * 256 * AP);  // releases the info
-        for (int v = 0; v < 2; ++v) {
-          const int t = task_limb(wp[v]);
-          const u64 *b = PRO == PRO_UP
-                             ? a.tab.bup + ((size_t)task_dig(wp[v]) * a.qp + t) * 32 * AP
-                             : a.tab.bdown + (size_t)t * 32 * AP;
-          bulk_g2s(sB + (size_t)(g * 2 + v) * 256 * AP, b, 256 * AP, &bar_b[g]);
-        }
+        if (it + GRP < it1) load_b(it + GRP);
         if (x.tile != cur_tile || x.set != cur_set) {
           // a new tile's source bytes, once the MMAs of the previous item no longer read A
           if (it > it0) {
@@ -276,15 +290,16 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
           cur_tile = x.tile;
           cur_set = x.set;
         }
-        if (!mbar_wait(&bar_b[g], k & 1)) atomicExch(a.tab.err, 1);
+        if (!mbar_wait(&bar_b[g][b], (k >> 1) & 1)) atomicExch(a.tab.err, 1);
         tc_fence_after();
-        const u64 bd0 = smem_desc(smem_u32(sB + (size_t)g * 512 * AP), 128, AP * 128);
+        const u64 bd0 = smem_desc(smem_u32(sB + (size_t)(g * 2 + b) * 512 * AP), 128, AP * 128);
         const uint32_t d0 = tmem + g * G::DCOLS;
-        // descriptors advance by (byte offset >> 4) in their start-address field
+        // descriptors advance by (byte offset >> 4) in their start-address field; the
+        // K steps outside, so consecutive MMAs accumulate into different M blocks
+        for (int s = 0; s < AP / 2; ++s)
 #pragma unroll
-        for (int b = 0; b < G::MB; ++b)
-          for (int s = 0; s < AP / 2; ++s)
-            tc_mma(d0 + b * 32, ad0 + (u64)(2 * s * G::TP + b * 128), bd0 + (u64)(16 * s),
+          for (int mb = 0; mb < G::MB; ++mb)
+            tc_mma(d0 + mb * 32, ad0 + (u64)(2 * s * G::TP + mb * 128), bd0 + (u64)(16 * s),
                    tc_idesc(32), s > 0);
         tc_commit(&bar_m[g]);
       }
@@ -298,10 +313,11 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
     u64 *tile = sT + (group * 2 + half) * G::TILE_W;
     for (int it = it0 + group, k = 0; it < it1; it += GRP, ++k) {
       // the pair's decoded items (the producer's info, released with its constants)
-      if (!mbar_wait(&bar_b[group], k & 1)) atomicExch(a.tab.err, 1);
-      const uint32_t w = info_w[group][half];
-      const int cnt = info_cnt[group], xtile = info_tile[group];
-      const bool fast = info_fast[group] != 0;
+      const int b = k & 1;
+      if (!mbar_wait(&bar_b[group][b], (k >> 1) & 1)) atomicExch(a.tab.err, 1);
+      const uint32_t w = info_w[group][b][half];
+      const int cnt = info_cnt[group][b], xtile = info_tile[group][b];
+      const bool fast = info_fast[group][b] != 0;
       const ModInfo mi = a.tab.mod[task_limb(w)];
       if (!mbar_wait(&bar_m[group], k & 1)) atomicExch(a.tab.err, 1);
       tc_fence_after();
