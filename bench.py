@@ -47,7 +47,7 @@ WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 # keyed by (workload, kernel name of the library's profiler), so a change of the
 # dominant kernel still finds its row. The split key multiply's two launches (P-limb
 # and Q-limb targets) are averaged, as the profiler averages them. Plans with the
-# tensor-core basis conversions (KS_BCONV_TC) run other column kernels: NCU_TC holds
+# tensor-core basis conversions (KS_BCONV_TC, KS_BCONV_TC_DOWN) run other column kernels:
 # their rows (profiles/bconv_tc_4_2e16_35_ncu.md); the inverse column passes that write
 # the source bytes for them were not captured (None).
 NCU = {("c3", k): {"traffic": t, "plan": "DPOB[km4,dnr4]-split", **pipes} for k, t, pipes in (
@@ -66,10 +66,19 @@ NCU_TC = {("c3", "modup_col"): {"traffic": 111940000, "plan": "DPOB[km4,dnr4]-tc
           ("c3", "intt_col(d)"): None, ("c3", "intt_col(accP)"): None}
 
 
-def ncu_row(workload, name, tc):
+def ncu_row(workload, name, tc_up, tc_down):
+    """The ncu row of a kernel of the plan; tc_up / tc_down: the plan's ModUp / ModDown
+    conversions run on the tensor cores."""
+    tc = tc_up if name in ("intt_col(d)", "modup_col") else tc_down
     if tc and (workload, name) in NCU_TC:
         return NCU_TC[(workload, name)]
     return NCU.get((workload, name))
+
+
+def tc_sides(ks, variant):
+    """(ModUp, ModDown) conversions of a plan on the tensor cores."""
+    return (bool(variant & ks.KS_BCONV_TC),
+            bool(variant & (ks.KS_BCONV_TC | ks.KS_BCONV_TC_DOWN)))
 
 
 def measured_alu(ks, stream):
@@ -78,6 +87,21 @@ def measured_alu(ks, stream):
     bf = max(ks.ks_calibrate(ks.KS_CAL_BUTTERFLY, 16384, stream) for _ in range(3))
     mac = max(ks.ks_calibrate(ks.KS_CAL_MAC, 4096, stream) for _ in range(3))
     return bf, mac
+
+
+def tensor_roofline(dom, per_launch_ms, peaks):
+    """The tensor-core part of a kernel (the basis conversions of KS_BCONV_TC plans), or
+    None: its bf16 FLOPs against the measured sustained cuBLAS bf16 rate (the kernel runs
+    inside a long step)."""
+    if not dom.get("tensor_flops"):
+        return None
+    fl = dom["tensor_flops"] / dom["launches"]
+    pk = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
+    return {"flops_per_launch": fl, "achieved": fl / (per_launch_ms / 1e3) / 1e12,
+            "peak": pk / 1e12, "unit": "TFLOP/s", "frac": fl / pk * 1e3 / per_launch_ms,
+            "t_ceil_ms": fl / pk * 1e3,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if
+            "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained"}
 
 
 def alu_roofline(dom, per_launch_ms, bf, mac):
@@ -858,7 +882,8 @@ def main():
     # the recipe's unit counts for context: SMs x 64 IMAD lanes x max clock / 10 IMAD per
     # 64-bit Shoup product
     derived = sms * 64 * sm_mhz * 1e6 / 10 / 1e9
-    ncu = ncu_row(args.workload, dom["name"], bool(pvar & ks.KS_BCONV_TC))
+    tens = tensor_roofline(dom, per_launch_ms, peaks)
+    ncu = ncu_row(args.workload, dom["name"], *tc_sides(ks, pvar))
     roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu["achieved"],
                 "peak": alu["peak"], "unit": "Gop/s (butterfly-equivalent)",
                 "frac": alu["frac"], "traffic": ncu["traffic"] if ncu else None,
@@ -881,6 +906,17 @@ def main():
                                  "source": f"{sms} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz / 10 IMAD"
                                            " per modop"},
                 "ncu": ncu}
+    if tens:
+        # a tensor-core conversion: its products on the tensor pipe, its REDCs and NTT on
+        # the integer pipes; the bound is the larger of the two ceilings
+        roofline["tensor"] = tens
+        roofline["what"] = ("tensor-core basis conversion fused with the column NTT: ALU "
+                            "part = one REDC per output + the NTT's Shoup products; tensor "
+                            "part = the byte-split bf16 products")
+        if tens["t_ceil_ms"] > alu["t_ceil_ms"]:
+            roofline.update({"bound": "tensor", "achieved": tens["achieved"] * 1e3,
+                             "peak": tens["peak"] * 1e3, "unit": "GFLOP/s (bf16)",
+                             "frac": tens["frac"]})
     # the whole KeySwitch at the measured ceiling: every kernel's arithmetic
     t_ceil_step = sum((s["macs"] / mac + (s["ops"] - s["macs"]) / bf) for s in stats) / kprof * 1e3
     algo = prm.algo_bytes()
@@ -893,7 +929,7 @@ def main():
         k = {"name": s_["name"], "launches_per_step": n / kprof, "ms_per_launch": round(t, 5),
              "event_ms_per_launch": round(s_["ms"] / n, 5), "alu_frac": round(tc / t, 4),
              "share": round(s_["ms"] / sum(x["ms"] for x in stats), 4)}
-        nc = ncu_row(args.workload, s_["name"], bool(pvar & ks.KS_BCONV_TC))
+        nc = ncu_row(args.workload, s_["name"], *tc_sides(ks, pvar))
         if nc:
             k["dram_bytes"] = nc["traffic"]
             k["algo_bytes"] = s_["bytes"] / n
@@ -909,7 +945,11 @@ def main():
         "ks_alu_roofline": {"bound": "alu", "t_ceil_ms": t_ceil_step, "ms_per_step": step_ms,
                             "frac": t_ceil_step / step_ms,
                             "one_stream_frac": t_ceil_step / one_stream_ms,
-                            "what": "the whole KeySwitch's arithmetic at the measured ceiling"},
+                            "tensor_t_ceil_ms": sum(x.get("tensor_flops", 0) for x in stats)
+                            / kprof / (float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e9),
+                            "what": "the whole KeySwitch's integer arithmetic at the measured "
+                                    "ceiling (the products of tensor-core conversions apart: "
+                                    "tensor_t_ceil_ms at the sustained bf16 rate)"},
         "streams": {"in_flight": nstreams, "probe_ks_per_s": probe,
                     "one_stream_value": job_rate(world, 1, one_stream_ms),
                     "one_stream_ms_per_step": one_stream_ms,

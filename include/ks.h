@@ -98,9 +98,13 @@ extern "C" {
  * products summed below 2^23, recombined into the exact 128-bit sum and reduced once,
  * fused with the first forward NTT pass (the inverse column passes write the bytes of
  * their output instead of the output). Same result bits as the integer path. Effective
- * on contexts with ks_info.tc = 1 (2^13 <= N <= 2^17, 2 <= alpha <= 15); ignored
+ * on contexts with ks_info.tc = 1 (2^13 <= N <= 2^17, 2 <= alpha <= 9, dnum <= 64); ignored
  * otherwise and by unfused plans. */
 #define KS_BCONV_TC 0x800
+/* OR-ed into a fused variant: the ModDown basis conversion alone runs on the tensor cores
+ * as KS_BCONV_TC describes; the ModUp conversion stays on the integer path. Same
+ * conditions as KS_BCONV_TC, which includes it. */
+#define KS_BCONV_TC_DOWN 0x1000
 
 typedef struct {
   uint32_t dnum;     /* decomposition number (>= 1) */
@@ -432,7 +436,10 @@ typedef struct {
   double bytes;  /* summed algorithmic bytes */
   double ops;    /* summed modular operations */
   double macs;   /* of which exact 128-bit multiply-accumulate terms (basis conversion,
-                    key multiply); the rest are Shoup products (butterflies, scalings) */
+                    key multiply) and Montgomery reductions; the rest are Shoup products
+                    (butterflies, scalings) */
+  double tensor_flops; /* summed tensor-core FLOPs (2 per bf16 multiply-add), counted
+                          apart from ops: the basis conversions of KS_BCONV_TC plans */
 } ks_kernel_stat;
 
 int ks_profile_begin(void);

@@ -36,7 +36,8 @@ struct Plan {
   int ca[ST_COUNT];   // per stage: 1 = alternative column tile (stages with column passes)
   int code;      // every variant bit that changes the launches (graph-cache key)
   bool split;    // KS_SPLIT_DOWN in effect (fused DPOB, two-pass N)
-  bool tc;       // KS_BCONV_TC in effect (fused, context with a tensor-core path)
+  bool tc_up;    // KS_BCONV_TC in effect (fused, context with a tensor-core path)
+  bool tc_down;  // KS_BCONV_TC or KS_BCONV_TC_DOWN in effect
   int chunks;    // phase-1 and phase-2 group counts (1 for OB)
   int clen;      // max QP-limbs per phase-1 group
   int clq;       // max Q-limbs per phase-2 group
@@ -50,7 +51,7 @@ constexpr int kSchedMask = 0x3ff << KS_STAGE_SHIFT;
 
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT |
-                  KS_SPLIT_DOWN | KS_BCONV_TC))
+                  KS_SPLIT_DOWN | KS_BCONV_TC | KS_BCONV_TC_DOWN))
     return KS_EINVAL;
   if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
@@ -87,7 +88,8 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   pl->ca[ST_DNC] = (variant & KS_COLALT_DNC) ? 1 : 0;
   pl->code = variant & ~0xff;
   pl->split = (variant & KS_SPLIT_DOWN) && base == KS_DPOB && !pl->unfused && c->loga > 0;
-  pl->tc = (variant & KS_BCONV_TC) && !pl->unfused && c->tc_ap > 0;
+  pl->tc_up = (variant & KS_BCONV_TC) && !pl->unfused && c->tc_ap > 0;
+  pl->tc_down = (variant & (KS_BCONV_TC | KS_BCONV_TC_DOWN)) && !pl->unfused && c->tc_ap > 0;
   pl->chunks = chunks;
   pl->clen = (c->qp + chunks - 1) / chunks;
   pl->clq = (c->nq + chunks - 1) / chunks;
@@ -114,8 +116,8 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   pl->off_vp = take((size_t)2 * c->np * N);
   pl->off_tmp2 = take(pl->tmp2_slots * N);
   // the bf16 bytes of v and vp (16 bytes per residue) for the tensor-core conversions
-  pl->off_pv = pl->tc ? take((size_t)2 * c->nq * N) : 0;
-  pl->off_ppv = pl->tc ? take((size_t)4 * c->np * N) : 0;
+  pl->off_pv = pl->tc_up ? take((size_t)2 * c->nq * N) : 0;
+  pl->off_ppv = pl->tc_down ? take((size_t)4 * c->np * N) : 0;
   pl->total = off;
   return KS_OK;
 }
@@ -141,7 +143,7 @@ int cuda_rc(cudaError_t e) {
 struct ProfRec {
   const char *name;
   cudaEvent_t a, b;
-  double bytes, ops, macs;
+  double bytes, ops, macs, tflops;
 };
 
 struct Profiler {
@@ -162,16 +164,17 @@ struct Profiler {
 
 thread_local Profiler g_prof;
 
-// Run one launcher; when profiling, bracket it with events on its stream.
+// Run one launcher; when profiling, bracket it with events on its stream. tflops: the
+// launch's tensor-core FLOPs (2 per bf16 multiply-add).
 template <class F>
 cudaError_t timed(const char *name, double bytes, double ops, double macs, cudaStream_t s,
-                  F f) {
+                  F f, double tflops = 0) {
   if (!g_prof.on) return f();
   cudaEvent_t a = g_prof.get(), b = g_prof.get();
   cudaEventRecord(a, s);
   cudaError_t e = f();
   cudaEventRecord(b, s);
-  g_prof.recs.push_back({name, a, b, bytes, ops, macs});
+  g_prof.recs.push_back({name, a, b, bytes, ops, macs, tflops});
   return e;
 }
 
@@ -212,8 +215,8 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
     KS_TRY(timed("intt_row(d)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), 0, s,
                  [&] { return L.intt_row(c, js, wo, 0, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(d)", (pl.tc ? 3 : 2) * nl * W, nl * (BF_A + NJ), 0, s, [&] {
-        return pl.tc ? L.intt_col_tc(c, js, wo, 0, s) : L.intt_col(c, js, wo, 0, s);
+      KS_TRY(timed("intt_col(d)", (pl.tc_up ? 3 : 2) * nl * W, nl * (BF_A + NJ), 0, s, [&] {
+        return pl.tc_up ? L.intt_col_tc(c, js, wo, 0, s) : L.intt_col(c, js, wo, 0, s);
       }));
   }
 
@@ -236,25 +239,33 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
       Tasks tg = up;
       tg.mode = TASK_TARGET;
       const int nconv = L.count(c, up);
-      double src_b = 0, conv_ops = 0;
+      // tc_tg: the targets the tensor-core form converts (each digit's in pairs)
+      double src_b = 0, conv_ops = 0, tc_tg = 0;
       for (int j = up.j0; j < up.j1; ++j) src_b += dsize(j) * W;
       {
         for (int j = up.j0; j < up.j1; ++j) {
           Tasks one = up;
           one.j0 = j;
           one.j1 = j + 1;
-          conv_ops += (double)L.count(c, one) * NJ * (dsize(j) + 1);
+          const int cnt = L.count(c, one);
+          conv_ops += (double)cnt * NJ * (dsize(j) + 1);
+          tc_tg += (cnt + 1) / 2 * 2;
         }
       }
       const double nt = t1 - t0, nd = up.j1 - up.j0;
       const double own = nd * nt - nconv;
       if (!pl.unfused) {
-        if (!single)
+        // the tensor-core form reads the sources as bytes (16 per residue), runs the
+        // products on the tensor cores (tc_ap * 256 FLOPs per target point) and one REDC
+        // per output on the integer pipes
+        if (!single && pl.tc_up)
+          KS_TRY(timed(
+              "modup_col", nconv * W + 2 * src_b, nconv * (NJ + BF_A), nconv * NJ, s,
+              [&] { return launch_bconv_tc(c, js, wo, up, true, s); },
+              tc_tg * NJ * c->tc_ap * 256));
+        else if (!single)
           KS_TRY(timed("modup_col", nconv * W + src_b, conv_ops + nconv * BF_A, conv_ops, s,
-                       [&] {
-                         return pl.tc ? launch_bconv_tc(c, js, wo, up, true, s)
-                                      : LU.modup_col(c, js, wo, up, s);
-                       }));
+                       [&] { return LU.modup_col(c, js, wo, up, s); }));
       } else {
         KS_TRY(timed("bconv_up", nconv * W + src_b, conv_ops, conv_ops, s,
                      [&] { return launch_bconv_up(c, js, wo, up, nconv, s); }));
@@ -302,9 +313,11 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
     KS_TRY(timed("intt_row(accP)", 2 * nl * W, nl * (BF_B + (single ? NJ : 0)), 0, s,
                  [&] { return L.intt_row(c, js, wo, 1, s); }));
     if (!single)
-      KS_TRY(timed("intt_col(accP)", (pl.tc ? 3 : 2) * nl * W, nl * (BF_A + NJ), 0, s, [&] {
-        return pl.tc ? L.intt_col_tc(c, js, wo, 1, s) : L.intt_col(c, js, wo, 1, s);
-      }));
+      KS_TRY(timed("intt_col(accP)", (pl.tc_down ? 3 : 2) * nl * W, nl * (BF_A + NJ), 0, s,
+                   [&] {
+                     return pl.tc_down ? L.intt_col_tc(c, js, wo, 1, s)
+                                       : L.intt_col(c, js, wo, 1, s);
+                   }));
   }
 
   // Phase 2: ModDown (BConv P->Q + NTT) and (acc - .) * P^-1, per output group.
@@ -321,11 +334,14 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
     d1.mode = TASK_DOWN1;
     const double n = 2.0 * (i1 - i0), vp_b = 2.0 * c->np * W, conv = n * NJ * (c->np + 1.0);
     if (!pl.unfused) {
-      if (!single)
-        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s, [&] {
-          return pl.tc ? launch_bconv_tc(c, js, wo, dn, false, s)
-                       : LDC.moddown_col(c, js, wo, dn, s);
-        }));
+      if (!single && pl.tc_down)  // counted as for modup_col
+        KS_TRY(timed(
+            "moddown_col", n * W + 2 * vp_b, n * (NJ + BF_A), n * NJ, s,
+            [&] { return launch_bconv_tc(c, js, wo, dn, false, s); },
+            2.0 * ((i1 - i0 + 1) / 2 * 2) * NJ * c->tc_ap * 256));
+      else if (!single)
+        KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s,
+                     [&] { return LDC.moddown_col(c, js, wo, dn, s); }));
       const double b = 3 * n * W + (single ? vp_b - n * W : 0);
       const double o = n * (BF_B + NJ) + (single ? conv : 0);
       if (split) KS_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -1440,26 +1456,16 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
         best_c = b[1];
       }
     }
-  // 2) the schedule of the winner, one coordinate at a time: the tensor-core basis
-  // conversions, each stage's radix, then each column pass's tile, then the split
-  // ModDown; the winner is re-timed with the same number of repetitions, and a change is
+  // 2) the schedule of the winner, one coordinate at a time: each stage's radix, then the
+  // tensor-core basis conversions (both, else the ModDown one alone; a column pass they
+  // replace drops its radix), then each remaining column pass's tile, then the split
+  // ModDown. The winner is re-timed with the same number of repetitions, and a change is
   // kept only if the whole KeySwitch gets faster by more than the timing noise (1.5%).
-  // With the tensor-core conversions the ModUp / ModDown column passes have no radix or
-  // tile of their own to tune.
   if (rc == KS_OK && c->loga > 0) {
     best = time_plan(best_v, best_c, 6);
-    if (c->tc_ap > 0 && !(best_v & KS_UNFUSED)) {
-      const float ms = time_plan(best_v | KS_BCONV_TC, best_c, 6);
-      if (ms < 0.985f * best) {
-        best = ms;
-        best_v |= KS_BCONV_TC;
-      }
-    }
-    const bool tc = (best_v & KS_BCONV_TC) != 0;
     const int plan_code3 = (best_v & KS_RADIX4) ? KS_R4 : (best_v & KS_RADIX16) ? KS_R16 : KS_R8;
     for (int st = 0; st < ST_COUNT && rc == KS_OK; ++st)
       for (int code = KS_R4; code <= KS_R16 && rc == KS_OK; ++code) {
-        if (tc && (st == ST_UPC || st == ST_DNC)) continue;
         if (code == plan_code3) continue;
         const int cur = (best_v >> (KS_STAGE_SHIFT + 2 * st)) & 3;
         if (cur == code) continue;
@@ -1470,9 +1476,25 @@ int ks_tune(ks_context *c, const uint64_t *d, const uint64_t *evk, uint64_t *out
           best_v = v;
         }
       }
+    if (rc == KS_OK && c->tc_ap > 0 && !(best_v & KS_UNFUSED)) {
+      const int up_dn = KS_STAGE_RADIX(ST_UPC, 3) | KS_STAGE_RADIX(ST_DNC, 3);
+      const int cand[2] = {(best_v & ~up_dn) | KS_BCONV_TC,
+                           (best_v & ~KS_STAGE_RADIX(ST_DNC, 3)) | KS_BCONV_TC_DOWN};
+      for (int v : cand) {
+        if (rc != KS_OK) break;
+        const float ms = time_plan(v, best_c, 6);
+        if (ms < 0.985f * best) {
+          best = ms;
+          best_v = v;
+          break;
+        }
+      }
+    }
+    const bool tc_up = (best_v & KS_BCONV_TC) != 0;
+    const bool tc_down = (best_v & (KS_BCONV_TC | KS_BCONV_TC_DOWN)) != 0;
     for (int bit : {KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC, KS_SPLIT_DOWN}) {
       if (rc != KS_OK) break;
-      if (tc && (bit == KS_COLALT_UPC || bit == KS_COLALT_DNC)) continue;
+      if ((tc_up && bit == KS_COLALT_UPC) || (tc_down && bit == KS_COLALT_DNC)) continue;
       if (bit == KS_SPLIT_DOWN && ((best_v & 0xff) != KS_DPOB || (best_v & KS_UNFUSED))) continue;
       const float ms = time_plan(best_v ^ bit, best_c, 6);
       if (ms < 0.985f * best) {
@@ -1535,6 +1557,7 @@ int ks_profile_end(ks_kernel_stat *stats, int max_stats, int *count) {
     hit->bytes += r.bytes;
     hit->ops += r.ops;
     hit->macs += r.macs;
+    hit->tensor_flops += r.tflops;
     g_prof.pool.push_back(r.a);
     g_prof.pool.push_back(r.b);
   }

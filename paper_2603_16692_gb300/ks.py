@@ -25,6 +25,7 @@ KS_COLALT_INV, KS_COLALT_UPC, KS_COLALT_DNC = 0x4000000, 0x8000000, 0x10000000
 KS_COLTILE_ALT = KS_COLALT_INV | KS_COLALT_UPC | KS_COLALT_DNC
 KS_SPLIT_DOWN = 0x20000000
 KS_BCONV_TC = 0x800
+KS_BCONV_TC_DOWN = 0x1000
 STAGE_NAMES = ("inv", "upc", "km", "dnc", "dnr")
 
 
@@ -64,7 +65,8 @@ class ks_info(ctypes.Structure):
 
 class ks_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("ops", ctypes.c_double), ("macs", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("ops", ctypes.c_double), ("macs", ctypes.c_double),
+                ("tensor_flops", ctypes.c_double)]
 
 
 KS_MLP_PARAMS, KS_MLP_MAX_BATCH = 4868, 4096
@@ -397,12 +399,14 @@ def ks_profile_begin():
 
 
 def ks_profile_end() -> list:
-    """[{name, launches, ms, bytes, ops, macs}] aggregated over the profiled launches."""
+    """[{name, launches, ms, bytes, ops, macs, tensor_flops}] aggregated over the profiled
+    launches."""
     arr = (ks_kernel_stat * 64)()
     n = ctypes.c_int()
     _check(load().ks_profile_end(arr, 64, ctypes.byref(n)), "ks_profile_end")
     return [{"name": arr[k].name.decode(), "launches": arr[k].launches, "ms": arr[k].ms,
-             "bytes": arr[k].bytes, "ops": arr[k].ops, "macs": arr[k].macs}
+             "bytes": arr[k].bytes, "ops": arr[k].ops, "macs": arr[k].macs,
+             "tensor_flops": arr[k].tensor_flops}
             for k in range(min(n.value, 64))]
 
 
@@ -476,6 +480,8 @@ def variant_name(v: int, chunks: int = 0) -> str:
         s += "-split"
     if v & KS_BCONV_TC:
         s += "-tc"
+    elif v & KS_BCONV_TC_DOWN:
+        s += "-tcdown"
     return s
 
 

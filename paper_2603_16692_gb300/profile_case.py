@@ -84,6 +84,8 @@ def parse_sched(text: str) -> int:
             v |= ks.KS_SPLIT_DOWN
         elif item == "tc":
             v |= ks.KS_BCONV_TC
+        elif item == "tcdown":
+            v |= ks.KS_BCONV_TC_DOWN
         elif item == "colalt":
             v |= ks.KS_COLTILE_ALT
         elif item.startswith("colalt-"):
@@ -121,9 +123,12 @@ def stats(run, reps):
         ceil = (r["macs"] / mac + (r["ops"] - r["macs"]) / bf) * 1e6 / r["launches"]
         us = r["ms"] * 1e3 / r["launches"]
         ceil_op += ceil * r["launches"] / reps
-        print(f"{r['name']:22s} {us:10.2f} {ceil:8.2f} {ceil / us:6.1%} {r['ms'] / total:6.1%}")
-    print(f"operation: {op_ms * 1e3:.1f} us, arithmetic at the measured ceiling {ceil_op:.1f} us"
-          f" ({ceil_op / (op_ms * 1e3):.1%})")
+        tc = r.get("tensor_flops", 0) / r["launches"]
+        extra = f"  tensor {tc / (us * 1e-6) / 1e12:.0f} TFLOP/s" if tc else ""
+        print(f"{r['name']:22s} {us:10.2f} {ceil:8.2f} {ceil / us:6.1%} {r['ms'] / total:6.1%}"
+              + extra)
+    print(f"operation: {op_ms * 1e3:.1f} us, integer arithmetic at the measured ceiling "
+          f"{ceil_op:.1f} us ({ceil_op / (op_ms * 1e3):.1%})")
 
 
 if __name__ == "__main__":

@@ -99,3 +99,15 @@ def test_new_entry_points_reject_bad_arguments_on_host():
     sel.x_std[2] = 1.0
     sel.variant[1] = 7  # not a dataflow
     assert lib.ks_selector_load(ctypes.byref(sel)) == ks.KS_EINVAL
+
+
+def test_plan_flags_match_the_header():
+    """Every plan flag of the binding has the value include/ks.h gives it, and the plan
+    names spell the tensor-core flags."""
+    text = open(os.path.join(ROOT, "include", "ks.h")).read()
+    defs = dict(re.findall(r"#define (KS_\w+) (0x[0-9a-fA-F]+|\d+)\b", text))
+    for name in ("KS_UNFUSED", "KS_RADIX4", "KS_RADIX16", "KS_BCONV_TC", "KS_BCONV_TC_DOWN",
+                 "KS_SPLIT_DOWN", "KS_COLALT_INV", "KS_COLALT_UPC", "KS_COLALT_DNC"):
+        assert getattr(ks, name) == int(defs[name], 0), name
+    assert ks.variant_name(ks.KS_DPOB | ks.KS_BCONV_TC_DOWN) == "DPOB-tcdown"
+    assert ks.variant_name(ks.KS_DPOB | ks.KS_BCONV_TC_DOWN | ks.KS_BCONV_TC) == "DPOB-tc"

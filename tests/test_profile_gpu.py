@@ -62,3 +62,41 @@ def test_profile_counts_key_multiply_terms():
     mac = ks.ks_calibrate(ks.KS_CAL_MAC, 2048)
     t_ceil = km["macs"] / mac + (km["ops"] - km["macs"]) / bf
     assert t_ceil / (km["ms"] / 1e3) <= 1.5, (t_ceil, km["ms"])
+
+
+def test_profile_counts_tensor_core_conversions():
+    """With KS_BCONV_TC at (4, 2^16, 35) the two column conversions count their products
+    as tensor-core FLOPs (tc_ap * 256 per target point, alpha = 9 -> tc_ap = 10, each
+    digit's targets in pairs) and only one REDC per output as a MAC term; the integer
+    plan's launches count no tensor FLOPs."""
+    import torch
+    prm = W.make_params(*W.C3)
+    ctx = ks.Context(prm)
+    try:
+        s_from, s_to, a, e = (dev(x) for x in W.gen_keys(prm, 0))
+        evk = ctx.keygen(s_from, s_to, a, e)
+        d = dev(W.gen_input(prm, 0))
+        out = torch.empty((2, prm.L + 1, prm.N), dtype=torch.uint64, device="cuda")
+        got = {}
+        for v in (ks.KS_DPOB | ks.KS_BCONV_TC, ks.KS_DPOB):
+            ctx.switch(d, evk, out, variant=v)
+            torch.cuda.synchronize()
+            ks.ks_profile_begin()
+            ctx.switch(d, evk, out, variant=v)
+            got[v] = {s["name"]: s for s in ks.ks_profile_end()}
+    finally:
+        ctx.close()
+    nq, qp, N = prm.L + 1, prm.L + 1 + prm.alpha, prm.N
+    assert prm.alpha == 9
+    tc = got[ks.KS_DPOB | ks.KS_BCONV_TC]
+    up_targets = prm.beta * qp - nq  # every digit converts onto the limbs it lacks
+    up_padded = sum((qp - min(nq, (j + 1) * prm.alpha) + j * prm.alpha + 1) // 2 * 2
+                    for j in range(prm.beta))
+    assert tc["modup_col"]["macs"] == up_targets * N
+    assert tc["modup_col"]["tensor_flops"] == up_padded * N * 10 * 256
+    assert tc["moddown_col"]["macs"] == 2 * nq * N
+    assert tc["moddown_col"]["tensor_flops"] == 2 * ((nq + 1) // 2 * 2) * N * 10 * 256
+    for s in got[ks.KS_DPOB].values():
+        assert s["tensor_flops"] == 0
+    for name in ("modup_row_keymult", "moddown_row"):
+        assert tc[name]["tensor_flops"] == 0

@@ -106,3 +106,22 @@ def test_tc_batch_and_entry_points():
         assert np.array_equal(host(got), cases[2][7]), "noalloc entry point"
     finally:
         ctx.close()
+
+
+TCD = ks.KS_BCONV_TC_DOWN
+TCD_PLANS = [
+    ks.KS_DPOB | TCD,
+    ks.KS_DSOB | TCD,
+    ks.KS_DPOC | TCD,
+    ks.KS_DPOB | TCD | ks.KS_SPLIT_DOWN | ks.KS_STAGE_RADIX(ks.KS_ST_UPC, ks.KS_R16)
+    | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4) | ks.KS_COLALT_UPC,
+    ks.KS_DPOB | TCD | TC | ks.KS_RADIX4,  # both flags: both conversions
+    ks.KS_DPOB | TCD | ks.KS_UNFUSED,  # unfused plans ignore the flag
+]
+
+
+@pytest.mark.parametrize("cfg", [W.C2, W.C3, (10, 17, 60), (2, 14, 17)])
+def test_tc_down_only(cfg):
+    """KS_BCONV_TC_DOWN: the ModDown conversion on the tensor cores, the ModUp one on the
+    integer path (its own radix and column tile), every dataflow."""
+    check(cfg, 2, TCD_PLANS, chunk_list=(3,))
