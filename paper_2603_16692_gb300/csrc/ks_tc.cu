@@ -29,12 +29,14 @@
 //
 // One CTA per SM walks a contiguous range of (column tile, target pair) items; the
 // bytes of a tile's sources stay in shared memory while the CTA converts them onto
-// successive pairs of targets. Roles: one producer thread (its own warp) issues the
-// bulk copies and the MMAs (completion on mbarriers through tcgen05.commit); two
-// consumer groups take the items in turn: each reads its lanes' 16 sums per target from
-// TMEM, recombines them into the exact 128-bit S, applies REDC and writes the tiles,
-// then its two halves run the column NTT of the pair's two targets side by side and
-// store them. Full / empty mbarriers hand the buffers over between the roles.
+// successive pairs of targets. Roles: one issuer thread (its own warp) copies the
+// tile's source bytes and issues the MMAs (completion on mbarriers through
+// tcgen05.commit); one loader thread (another warp) decodes each item's targets and
+// copies their constants an item ahead, off the issuer's path; two consumer groups
+// take the items in turn: each reads its lanes' 16 sums per target from TMEM,
+// recombines them into the exact 128-bit S, applies REDC and writes the tiles, then its
+// two halves run the column NTT of the pair's two targets side by side and store them.
+// Full / empty mbarriers and a read counter hand the buffers over between the roles.
 #include <algorithm>
 
 #include "ks_internal.h"
@@ -129,6 +131,28 @@ __device__ __forceinline__ U128 tc_sum(const uint32_t (&r)[16]) {
   return s;
 }
 
+// A progress counter in shared memory, written by one thread and polled by another:
+// rd_set publishes v after the writer's earlier shared-memory accesses; rd_wait polls
+// until the counter reaches want (at most ~1 s of %globaltimer and 2^24 polls; false if
+// it gave up) and orders the caller's later accesses after it.
+__device__ __forceinline__ void rd_set(volatile int *c, int v) {
+  __threadfence_block();
+  *c = v;
+}
+__device__ __forceinline__ bool rd_wait(volatile int *c, int want) {
+  bool ok = *c >= want;
+  if (!ok) {
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < (1 << 24) && !ok; ++it) {
+      __nanosleep(32);
+      ok = *c >= want;
+      if (global_ns() - t0 > 1000000000ull) break;
+    }
+  }
+  __threadfence_block();
+  return ok;
+}
+
 // Column tiles of TP = 2^10 points (N1 rows x GC columns); the inverse column passes
 // write the source bytes in blocks of this size (tc_tplog).
 constexpr int kTcTpLog = 10;
@@ -150,7 +174,7 @@ struct TcGeo {
   static constexpr int PTS = 8, RM = 3;  // points per consumer thread, NTT stages per round
   static constexpr int HT = TP / PTS;    // consumer threads per target
   static constexpr int GT = 2 * HT;      // threads per group
-  static constexpr int NT = GRP * GT;    // consumer threads
+  static constexpr int NT = GRP * GT;    // consumer threads (+ issuer and loader warps)
   static constexpr int TILES = (1 << LOGN) / TP;
   static constexpr int DCOLS = MB * 32;  // TMEM columns per group
   static constexpr int COLS = GRP * DCOLS <= 256 ? 256 : 512;
@@ -160,7 +184,7 @@ struct TcGeo {
     return ap * TP * 16 + GRP * 1024 * ap + GRP * 2 * TILE_W * 8;
   }
   static_assert(LOGGC >= 1 && MB % 4 == 0 && (HT / 32) % 4 == 0 && GRP * DCOLS <= 512 &&
-                    smem(APMAX) <= 227 * 1024 - 256 && NT + 32 <= 1024,
+                    smem(APMAX) <= 227 * 1024 - 256 && NT + 64 <= 1024,
                 "tile shape");
 };
 
@@ -181,7 +205,7 @@ __device__ __forceinline__ TcItem tc_item(const TcItems &ti, int it) {
 }
 
 template <int LOGN, int PRO, int GRP>
-__global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
+__global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 64, 1)
     k_bconv_tc(KArgs a, JobSet js, WsOff wo, Tasks tk, TcItems ti) {
   using G = TcGeo<LOGN, GRP>;
   extern __shared__ __align__(16) unsigned char raw[];
@@ -189,10 +213,14 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
   // bar_b[g][b] (the pair's constants landed; releases the pair's info), bar_m[g] (the
   // MMAs into the group's accumulator completed), bar_tm[g] (every warp of the group has
   // read the accumulator and the info of its item). bar_a: a tile's source bytes landed.
-  // The producer fetches a group's next constants as soon as the group has read its
-  // current sums, so the copy lands while the group finishes its item.
+  // rd[g]: items of group g whose sums the issuer has seen read (written by the issuer
+  // after its bar_tm wait). The loader fetches a group's next constants into the buffer
+  // of its item before last once rd shows that item read, so the copy lands while the
+  // group finishes its current item. (A counter, not a second wait on bar_tm: the loader
+  // may lag the consumers by more than one phase.)
   __shared__ u64 bar_a, bar_b[GRP][2], bar_m[GRP], bar_tm[GRP];
   __shared__ uint32_t tm_slot;
+  __shared__ volatile int rd[GRP];
   // per group and slot, written by the producer before it arms bar_b: the pair's decoded
   // work items, how many are real, the tile, and whether both moduli take the fast
   // butterflies
@@ -205,10 +233,11 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
   unsigned char *sB = raw + (size_t)AP * G::TP * 16;  // [GRP][buffer 2][target 2][256 ap]
   u64 *sT = reinterpret_cast<u64 *>(sB + (size_t)GRP * 1024 * AP);  // [GRP][2][TILE_W]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int CW = G::NT / 32;  // consumer warps; warp CW is the producer
+  constexpr int CW = G::NT / 32;  // consumer warps; warp CW issues, warp CW + 1 loads
 
   if (warp == 0) tmem_alloc(&tm_slot, G::COLS);
   if (threadIdx.x == 0) {
+    for (int g = 0; g < GRP; ++g) rd[g] = 0;
     mbar_init(&bar_a, 1);
     for (int g = 0; g < GRP; ++g) {
       mbar_init(&bar_b[g][0], 1);
@@ -231,15 +260,15 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
   pdl_wait();
 
   auto target = [&](const TcItem &x, int u) { return decode(a, tk, x.y0 + min(u, x.cnt - 1)); };
-  if (warp == CW) {
-    // Producer (one thread): constants, source bytes and MMAs.
+  if (warp == CW + 1) {
+    // Loader (one thread): each item's decoded targets (the info its group reads) and
+    // the pair's constants, into the group's buffer of the item's index mod 2.
     if (lane == 0) {
-      const u64 *pbase = jp.ws + (PRO == PRO_UP ? wo.pv : wo.ppv);
-      const u64 ad0 = smem_desc(smem_u32(sA), G::TP * 16, 128);
-      // item it's constants into its group's buffer (its index in the group mod 2), and
-      // its info into the same slot
-      auto load_b = [&](int it) {
-        const int g = (it - it0) % GRP, b = ((it - it0) / GRP) & 1;
+      for (int it = it0; it < it1; ++it) {
+        const int g = (it - it0) % GRP, k = (it - it0) / GRP, b = k & 1;
+        // buffer b and info slot b were last used by the group's item k - 2: wait until
+        // the issuer has seen its sums read (its MMAs, the buffer's readers, are done)
+        if (k >= 2 && !rd_wait(&rd[g], k - 1)) atomicExch(a.tab.err, 1);
         const TcItem x = tc_item(ti, it);
         const uint32_t wp[2] = {target(x, 0), target(x, 1)};
         info_w[g][b][0] = wp[0];
@@ -256,8 +285,13 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
                                : a.tab.bdown + (size_t)t * 32 * AP;
           bulk_g2s(sB + (size_t)((g * 2 + b) * 2 + v) * 256 * AP, src, 256 * AP, &bar_b[g][b]);
         }
-      };
-      for (int it = it0; it < it1 && it < it0 + GRP; ++it) load_b(it);
+      }
+    }
+  } else if (warp == CW) {
+    // Issuer (one thread): source bytes and MMAs.
+    if (lane == 0) {
+      const u64 *pbase = jp.ws + (PRO == PRO_UP ? wo.pv : wo.ppv);
+      const u64 ad0 = smem_desc(smem_u32(sA), G::TP * 16, 128);
       unsigned pha = 0;
       int cur_tile = -1, cur_set = -1;
       for (int it = it0; it < it1; ++it) {
@@ -265,11 +299,12 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 32, 1)
         const unsigned k = (unsigned)(it - it0) / GRP;  // the group's k-th item
         const int b = k & 1;
         const TcItem x = tc_item(ti, it);
-        // the group has read the sums and the info of its previous item (so its MMAs,
-        // the last readers of the other constant buffer, are done): fetch the group's
-        // next constants into that buffer while this item runs
-        if (k > 0 && !mbar_wait(&bar_tm[g], (k - 1) & 1)) atomicExch(a.tab.err, 1);
-        if (it + GRP < it1) load_b(it + GRP);
+        // the group has read the sums and the info of its previous item: its accumulator
+        // is free, and the loader may refill that item's constant buffer and info slot
+        if (k > 0) {
+          if (!mbar_wait(&bar_tm[g], (k - 1) & 1)) atomicExch(a.tab.err, 1);
+          rd_set(&rd[g], (int)k);
+        }
         if (x.tile != cur_tile || x.set != cur_set) {
           // a new tile's source bytes, once the MMAs of the previous item no longer read A
           if (it > it0) {
@@ -389,9 +424,9 @@ cudaError_t launch_one(const ks_context *c, const JobSet &js, const WsOff &wo, c
   using G = TcGeo<LOGN, GRP>;
   const int smem = G::smem(c->tc_ap);
   if (up)
-    return launch_pdl(k_bconv_tc<LOGN, PRO_UP, GRP>, dim3(grid, 1, js.n), dim3(G::NT + 32), smem,
+    return launch_pdl(k_bconv_tc<LOGN, PRO_UP, GRP>, dim3(grid, 1, js.n), dim3(G::NT + 64), smem,
                       s, args_of(c), js, wo, tk, ti);
-  return launch_pdl(k_bconv_tc<LOGN, PRO_DOWN, GRP>, dim3(grid, 1, js.n), dim3(G::NT + 32), smem,
+  return launch_pdl(k_bconv_tc<LOGN, PRO_DOWN, GRP>, dim3(grid, 1, js.n), dim3(G::NT + 64), smem,
                     s, args_of(c), js, wo, tk, ti);
 }
 
