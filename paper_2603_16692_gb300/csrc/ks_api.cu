@@ -239,7 +239,8 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
       Tasks tg = up;
       tg.mode = TASK_TARGET;
       const int nconv = L.count(c, up);
-      // tc_tg: the targets the tensor-core form converts (each digit's in pairs)
+      // tc_tg: the targets the tensor-core form converts (each digit's in groups of
+      // kTcTargets)
       double src_b = 0, conv_ops = 0, tc_tg = 0;
       for (int j = up.j0; j < up.j1; ++j) src_b += dsize(j) * W;
       {
@@ -249,7 +250,7 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
           one.j1 = j + 1;
           const int cnt = L.count(c, one);
           conv_ops += (double)cnt * NJ * (dsize(j) + 1);
-          tc_tg += (cnt + 1) / 2 * 2;
+          tc_tg += (cnt + kTcTargets - 1) / kTcTargets * kTcTargets;
         }
       }
       const double nt = t1 - t0, nd = up.j1 - up.j0;
@@ -338,7 +339,8 @@ int run_plan(ks_context *c, const Plan &pl, const JobSet &js, cudaStream_t s,
         KS_TRY(timed(
             "moddown_col", n * W + 2 * vp_b, n * (NJ + BF_A), n * NJ, s,
             [&] { return launch_bconv_tc(c, js, wo, dn, false, s); },
-            2.0 * ((i1 - i0 + 1) / 2 * 2) * NJ * c->tc_ap * 256));
+            2.0 * ((i1 - i0 + kTcTargets - 1) / kTcTargets * kTcTargets) * NJ * c->tc_ap *
+                256));
       else if (!single)
         KS_TRY(timed("moddown_col", n * W + vp_b, conv + n * BF_A, conv, s,
                      [&] { return LDC.moddown_col(c, js, wo, dn, s); }));
@@ -523,7 +525,7 @@ int create_context(int dnum, int logn, int L, const u64 *q, const u64 *p, int al
   if (c->loga > 0 && logn <= 17 && alpha >= 2 && alpha <= 9 && beta <= ks::kTcMaxSets &&
       c->run_up >= alpha && c->run_down >= alpha) {
     c->tc_ap = (alpha + 2) & ~1;  // alpha + 1 slots (the last adds 2^23), rounded to even
-    c->tc_tplog = 10;             // 1024-point column tiles
+    c->tc_tplog = ks::kTcTpLog;   // column tiles of the tensor-core items
     if (ks::tc_prepare(logn) != cudaSuccess) {
       cudaGetLastError();
       c->tc_ap = c->tc_tplog = 0;

@@ -105,14 +105,18 @@ struct Tables {
 
 // Tensor-core basis conversion: at most this many source sets (digits) per context.
 constexpr int kTcMaxSets = 64;
-// Work of one tensor-core BConv launch: the target pairs of every source set, over all
-// column tiles; item = (tile, pair), tile-major (see ks_tc.cu).
+// Tensor-core BConv work items: column tiles of 2^kTcTpLog points, kTcTargets targets
+// (of one source set) per item.
+constexpr int kTcTpLog = 10;
+constexpr int kTcTargets = 2;
+// Work of one tensor-core BConv launch: the target groups of every source set, over all
+// column tiles; item = (tile, target group), tile-major (see ks_tc.cu).
 struct TcItems {
-  int nsets, pairs, tiles, items, per_cta;
+  int nsets, pairs, tiles, items, per_cta;  // pairs: target groups per tile
   int set_id[kTcMaxSets];       // digit j (ModUp) or polynomial c (ModDown)
   int set_y0[kTcMaxSets];       // first work item (Tasks index) of the set
   int set_cnt[kTcMaxSets];      // work items of the set
-  int set_p0[kTcMaxSets + 1];   // pairs before the set
+  int set_p0[kTcMaxSets + 1];   // target groups before the set
 };
 
 struct LaunchTable;

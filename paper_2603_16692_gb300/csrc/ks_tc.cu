@@ -31,7 +31,7 @@
 // bytes of a tile's sources stay in shared memory while the CTA converts them onto
 // successive pairs of targets. Roles: one issuer thread (its own warp) copies the
 // tile's source bytes and issues the MMAs (completion on mbarriers through
-// tcgen05.commit); one loader thread (another warp) decodes each item's targets and
+// tcgen05.commit); a loader warp decodes each item's targets (a lane per target) and
 // copies their constants an item ahead, off the issuer's path; two consumer groups
 // take the items in turn: each reads its lanes' 16 sums per target from TMEM,
 // recombines them into the exact 128-bit S, applies REDC and writes the tiles, then its
@@ -153,9 +153,9 @@ __device__ __forceinline__ bool rd_wait(volatile int *c, int want) {
   return ok;
 }
 
-// Column tiles of TP = 2^10 points (N1 rows x GC columns); the inverse column passes
-// write the source bytes in blocks of this size (tc_tplog).
-constexpr int kTcTpLog = 10;
+// Column tiles of TP = 2^kTcTpLog points (N1 rows x GC columns; the inverse column
+// passes write the source bytes in blocks of this size), kTcTargets = 2 targets per
+// work item (ks_internal.h).
 // Consumer groups per CTA.
 constexpr int kTcGroups = 2;
 
@@ -183,8 +183,8 @@ struct TcGeo {
   __host__ __device__ static constexpr int smem(int ap) {
     return ap * TP * 16 + GRP * 1024 * ap + GRP * 2 * TILE_W * 8;
   }
-  static_assert(LOGGC >= 1 && MB % 4 == 0 && (HT / 32) % 4 == 0 && GRP * DCOLS <= 512 &&
-                    smem(APMAX) <= 227 * 1024 - 256 && NT + 64 <= 1024,
+  static_assert(kTcTargets == 2 && LOGGC >= 1 && MB % 4 == 0 && (HT / 32) % 4 == 0 &&
+                    GRP * DCOLS <= 512 && smem(APMAX) <= 227 * 1024 - 256 && NT + 64 <= 1024,
                 "tile shape");
 };
 
@@ -199,8 +199,8 @@ __device__ __forceinline__ TcItem tc_item(const TcItems &ti, int it) {
   while (s + 1 < ti.nsets && ti.set_p0[s + 1] <= q) ++s;
   r.set = s;
   const int k = q - ti.set_p0[s];
-  r.y0 = ti.set_y0[s] + 2 * k;
-  r.cnt = min(2, ti.set_cnt[s] - 2 * k);
+  r.y0 = ti.set_y0[s] + kTcTargets * k;
+  r.cnt = min(kTcTargets, ti.set_cnt[s] - kTcTargets * k);
   return r;
 }
 
@@ -221,11 +221,11 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 64, 1)
   __shared__ u64 bar_a, bar_b[GRP][2], bar_m[GRP], bar_tm[GRP];
   __shared__ uint32_t tm_slot;
   __shared__ volatile int rd[GRP];
-  // per group and slot, written by the producer before it arms bar_b: the pair's decoded
-  // work items, how many are real, the tile, and whether both moduli take the fast
-  // butterflies
+  // per group and slot, written by the loader before it arms bar_b: the pair's decoded
+  // work items, how many are real, the tile, whether both moduli take the fast
+  // butterflies, and the source set
   __shared__ uint32_t info_w[GRP][2][2];
-  __shared__ int info_cnt[GRP][2], info_tile[GRP][2], info_fast[GRP][2];
+  __shared__ int info_cnt[GRP][2], info_tile[GRP][2], info_fast[GRP][2], info_set[GRP][2];
   const JobPtr &jp = js.j[blockIdx.z];
   const int AP = a.tc_ap;
   const int it0 = blockIdx.x * ti.per_cta, it1 = min(ti.items, it0 + ti.per_cta);
@@ -261,30 +261,44 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 64, 1)
 
   auto target = [&](const TcItem &x, int u) { return decode(a, tk, x.y0 + min(u, x.cnt - 1)); };
   if (warp == CW + 1) {
-    // Loader (one thread): each item's decoded targets (the info its group reads) and
-    // the pair's constants, into the group's buffer of the item's index mod 2.
-    if (lane == 0) {
-      for (int it = it0; it < it1; ++it) {
-        const int g = (it - it0) % GRP, k = (it - it0) / GRP, b = k & 1;
-        // buffer b and info slot b were last used by the group's item k - 2: wait until
-        // the issuer has seen its sums read (its MMAs, the buffer's readers, are done)
-        if (k >= 2 && !rd_wait(&rd[g], k - 1)) atomicExch(a.tab.err, 1);
-        const TcItem x = tc_item(ti, it);
-        const uint32_t wp[2] = {target(x, 0), target(x, 1)};
-        info_w[g][b][0] = wp[0];
-        info_w[g][b][1] = wp[1];
+    // Loader warp: each item's decoded targets (the info its group and the issuer read)
+    // and the pair's constants, into the group's buffer of the item's index mod 2; lane
+    // u < 2 decodes and copies target u.
+    for (int it = it0; it < it1; ++it) {
+      const int g = (it - it0) % GRP, k = (it - it0) / GRP, b = k & 1;
+      // buffer b and info slot b were last used by the group's item k - 2: wait until
+      // the issuer has seen its sums read (its MMAs, the buffer's readers, are done)
+      if (k >= 2) {
+        int ok = 1;
+        if (lane == 0) ok = rd_wait(&rd[g], k - 1);
+        if (!__shfl_sync(0xffffffffu, ok, 0) && lane == 0) atomicExch(a.tab.err, 1);
+        __threadfence_block();
+      }
+      const TcItem x = tc_item(ti, it);
+      uint32_t w = 0;
+      int f = 1;
+      if (lane < 2) {
+        w = target(x, lane);
+        info_w[g][b][lane] = w;
+        f = a.tab.mod[task_limb(w)].m < kFastModulus;
+      }
+      f = __all_sync(0xffffffffu, f);
+      if (lane == 0) {
         info_cnt[g][b] = x.cnt;
         info_tile[g][b] = x.tile;
-        info_fast[g][b] = a.tab.mod[task_limb(wp[0])].m < kFastModulus &&
-                          a.tab.mod[task_limb(wp[1])].m < kFastModulus;
-        mbar_expect_tx(&bar_b[g][b], 2u * 256 * AP);  // releases the info
-        for (int v = 0; v < 2; ++v) {
-          const int t = task_limb(wp[v]);
-          const u64 *src = PRO == PRO_UP
-                               ? a.tab.bup + ((size_t)task_dig(wp[v]) * a.qp + t) * 32 * AP
-                               : a.tab.bdown + (size_t)t * 32 * AP;
-          bulk_g2s(sB + (size_t)((g * 2 + b) * 2 + v) * 256 * AP, src, 256 * AP, &bar_b[g][b]);
-        }
+        info_set[g][b] = x.set;
+        info_fast[g][b] = f;
+      }
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_expect_tx(&bar_b[g][b], 2u * 256 * AP);  // releases the info
+      __syncwarp();
+      if (lane < 2) {
+        const int t = task_limb(w);
+        const u64 *src = PRO == PRO_UP
+                             ? a.tab.bup + ((size_t)task_dig(w) * a.qp + t) * 32 * AP
+                             : a.tab.bdown + (size_t)t * 32 * AP;
+        bulk_g2s(sB + (size_t)((g * 2 + b) * 2 + lane) * 256 * AP, src, 256 * AP, &bar_b[g][b]);
       }
     }
   } else if (warp == CW) {
@@ -298,34 +312,35 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 64, 1)
         const int g = (it - it0) % GRP;
         const unsigned k = (unsigned)(it - it0) / GRP;  // the group's k-th item
         const int b = k & 1;
-        const TcItem x = tc_item(ti, it);
         // the group has read the sums and the info of its previous item: its accumulator
         // is free, and the loader may refill that item's constant buffer and info slot
         if (k > 0) {
           if (!mbar_wait(&bar_tm[g], (k - 1) & 1)) atomicExch(a.tab.err, 1);
           rd_set(&rd[g], (int)k);
         }
-        if (x.tile != cur_tile || x.set != cur_set) {
+        // the item's constants and info (its tile and source set)
+        if (!mbar_wait(&bar_b[g][b], (k >> 1) & 1)) atomicExch(a.tab.err, 1);
+        const int xtile = info_tile[g][b], xset = info_set[g][b];
+        if (xtile != cur_tile || xset != cur_set) {
           // a new tile's source bytes, once the MMAs of the previous item no longer read A
           if (it > it0) {
             const int gp = (it - 1 - it0) % GRP;
             if (!mbar_wait(&bar_m[gp], ((unsigned)(it - 1 - it0) / GRP) & 1))
               atomicExch(a.tab.err, 1);
           }
-          const int j = ti.set_id[x.set];
+          const int j = ti.set_id[xset];
           const int ns = PRO == PRO_UP ? min(a.nq, (j + 1) * a.alpha) - j * a.alpha : a.np;
           const size_t l0 = (size_t)j * (PRO == PRO_UP ? a.alpha : a.np);
           mbar_expect_tx(&bar_a, (unsigned)ns * G::TP * 16);
           for (int s = 0; s < ns; ++s)
             bulk_g2s(sA + (size_t)s * G::TP * 16,
-                     pbase + (((l0 + s) * G::TILES + x.tile) << G::TPLOG) * 2, G::TP * 16,
+                     pbase + (((l0 + s) * G::TILES + xtile) << G::TPLOG) * 2, G::TP * 16,
                      &bar_a);
           if (!mbar_wait(&bar_a, pha)) atomicExch(a.tab.err, 1);
           pha ^= 1;
-          cur_tile = x.tile;
-          cur_set = x.set;
+          cur_tile = xtile;
+          cur_set = xset;
         }
-        if (!mbar_wait(&bar_b[g][b], (k >> 1) & 1)) atomicExch(a.tab.err, 1);
         tc_fence_after();
         const u64 bd0 = smem_desc(smem_u32(sB + (size_t)(g * 2 + b) * 512 * AP), 128, AP * 128);
         const uint32_t d0 = tmem + g * G::DCOLS;
@@ -459,7 +474,8 @@ bool build_items(const ks_context *c, const Tasks &tk, bool up, TcItems &ti) {
     ti.nsets = 2;
   }
   ti.set_p0[0] = 0;
-  for (int k = 0; k < ti.nsets; ++k) ti.set_p0[k + 1] = ti.set_p0[k] + (ti.set_cnt[k] + 1) / 2;
+  for (int k = 0; k < ti.nsets; ++k)
+    ti.set_p0[k + 1] = ti.set_p0[k] + (ti.set_cnt[k] + kTcTargets - 1) / kTcTargets;
   ti.pairs = ti.set_p0[ti.nsets];
   ti.tiles = c->N >> c->tc_tplog;
   ti.items = ti.tiles * ti.pairs;
