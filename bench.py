@@ -42,37 +42,59 @@ WORKLOADS = {"c1": W.C1, "c2": W.C2, "c3": W.C3}
 
 # Per-kernel DRAM bytes (read + write) per launch and pipe use, from the cold-cache ncu
 # launch list and the per-kernel --set full captures of one KeySwitch of the workload
-# (profile_case with the plan DPOB[km4,dnr4]-split; summaries and commands in
-# profiles/keyswitch_4_2e16_35_launches.md and keyswitch_4_2e16_35_kernels_ncu.md);
-# keyed by (workload, kernel name of the library's profiler), so a change of the
-# dominant kernel still finds its row. The split key multiply's two launches (P-limb
-# and Q-limb targets) are averaged, as the profiler averages them. Plans with the
-# tensor-core basis conversions (KS_BCONV_TC, KS_BCONV_TC_DOWN) run other column kernels:
-# their rows (profiles/bconv_tc_4_2e16_35_ncu.md); the inverse column passes that write
-# the source bytes for them were not captured (None).
-NCU = {("c3", k): {"traffic": t, "plan": "DPOB[km4,dnr4]-split", **pipes} for k, t, pipes in (
-    ("intt_row(d)", 57100000, {"issue_pct": 47.3, "fmaheavy_pct": 45.0, "alu_pct": 37.3}),
-    ("intt_col(d)", 19100000, {"issue_pct": 45.8, "fmaheavy_pct": 47.0, "alu_pct": 35.0}),
-    ("modup_col", 38400000, {"issue_pct": 59.8, "fmaheavy_pct": 69.0, "alu_pct": 48.3}),
-    ("modup_row_keymult", 176050000, {"issue_pct": 54.1, "fmaheavy_pct": 55.0, "alu_pct": 37.2}),
-    ("intt_row(accP)", 18900000, {"issue_pct": 45.2, "fmaheavy_pct": 38.0, "alu_pct": 38.6}),
-    ("intt_col(accP)", 9500000, {"issue_pct": 45.0, "fmaheavy_pct": 41.0, "alu_pct": 37.1}),
-    ("moddown_col", 9600000, {"issue_pct": 58.2, "fmaheavy_pct": 66.0, "alu_pct": 46.0}),
-    ("moddown_row", 123700000, {"issue_pct": 51.7, "fmaheavy_pct": 52.0, "alu_pct": 44.7}))}
-NCU_TC = {("c3", "modup_col"): {"traffic": 111940000, "plan": "DPOB[km4,dnr4]-tc",
-                                "issue_pct": 29.9, "tensor_pct": 6.4, "alu_pct": 21.7},
-          ("c3", "moddown_col"): {"traffic": 19640000, "plan": "DPOB[km4,dnr4]-tc",
-                                  "issue_pct": 31.0, "tensor_pct": 6.9, "alu_pct": 22.4},
-          ("c3", "intt_col(d)"): None, ("c3", "intt_col(accP)"): None}
+# (profile_case; summaries and commands in profiles/keyswitch_4_2e16_35_launches.md,
+# keyswitch_4_2e16_35_kernels_ncu.md and bconv_tc_4_2e16_35_ncu.md), one table per
+# captured plan, keyed by the kernel names of the library's profiler, so a change of the
+# dominant kernel still finds its row. In the split plan the key multiply's two launches
+# (P-limb and Q-limb targets) are averaged, as the profiler averages them. The integer
+# plan DPOB[km4,dnr4]-split and the tensor-core plan DPOB[km4]-tc (KS_BCONV_TC); pipe
+# use where a --set full capture exists.
+NCU_PLANS = {
+    ("c3", "DPOB[km4,dnr4]-split"): {k: {"traffic": t, **pipes} for k, t, pipes in (
+        ("intt_row(d)", 57100000, {"issue_pct": 47.3, "fmaheavy_pct": 45.0, "alu_pct": 37.3}),
+        ("intt_col(d)", 19100000, {"issue_pct": 45.8, "fmaheavy_pct": 47.0, "alu_pct": 35.0}),
+        ("modup_col", 38400000, {"issue_pct": 59.8, "fmaheavy_pct": 69.0, "alu_pct": 48.3}),
+        ("modup_row_keymult", 176050000,
+         {"issue_pct": 54.1, "fmaheavy_pct": 55.0, "alu_pct": 37.2}),
+        ("intt_row(accP)", 18900000, {"issue_pct": 45.2, "fmaheavy_pct": 38.0, "alu_pct": 38.6}),
+        ("intt_col(accP)", 9500000, {"issue_pct": 45.0, "fmaheavy_pct": 41.0, "alu_pct": 37.1}),
+        ("moddown_col", 9600000, {"issue_pct": 58.2, "fmaheavy_pct": 66.0, "alu_pct": 46.0}),
+        ("moddown_row", 123700000, {"issue_pct": 51.7, "fmaheavy_pct": 52.0, "alu_pct": 44.7}))},
+    ("c3", "DPOB[km4]-tc"): {k: {"traffic": t, **pipes} for k, t, pipes in (
+        ("intt_row(d)", 57050000, {}),
+        ("intt_col(d)", 19080000, {}),
+        ("modup_col", 108350000,
+         {"issue_pct": 41.3, "tensor_pct": 8.9, "alu_pct": 29.1, "fma_pct": 27.9}),
+        ("modup_row_keymult", 361500000, {}),
+        ("intt_row(accP)", 18880000, {}),
+        ("intt_col(accP)", 9520000, {}),
+        ("moddown_col", 19190000,
+         {"issue_pct": 41.1, "tensor_pct": 9.1, "alu_pct": 28.5, "fma_pct": 27.5}),
+        ("moddown_row", 126320000, {}))},
+}
+# the column-pass kernels whose code depends on the tensor-core flags: a row for another
+# plan with the same flags stands for them (the other kernels' traffic depends on the
+# plan's split and schedule)
+TC_KERNELS = {"intt_col(d)": "up", "modup_col": "up", "intt_col(accP)": "down",
+              "moddown_col": "down"}
 
 
-def ncu_row(workload, name, tc_up, tc_down):
-    """The ncu row of a kernel of the plan; tc_up / tc_down: the plan's ModUp / ModDown
-    conversions run on the tensor cores."""
-    tc = tc_up if name in ("intt_col(d)", "modup_col") else tc_down
-    if tc and (workload, name) in NCU_TC:
-        return NCU_TC[(workload, name)]
-    return NCU.get((workload, name))
+def ncu_row(workload, plan, name, tc_up, tc_down):
+    """The ncu row of kernel `name` of plan `plan` (its variant name): the captured plan
+    itself, else, for the tensor-core-dependent column kernels, the captured plan with
+    the same conversion on the same kind of pipe; None when there is no such capture.
+    tc_up / tc_down: the plan's ModUp / ModDown conversions run on the tensor cores."""
+    rows = NCU_PLANS.get((workload, plan))
+    if rows and name in rows:
+        return {"plan": plan, **rows[name]}
+    side = TC_KERNELS.get(name)
+    if side:
+        tc = tc_up if side == "up" else tc_down
+        ref = "DPOB[km4]-tc" if tc else "DPOB[km4,dnr4]-split"
+        row = NCU_PLANS.get((workload, ref), {}).get(name)
+        if row:
+            return {"plan": ref, **row}
+    return None
 
 
 def tc_sides(ks, variant):
@@ -883,7 +905,8 @@ def main():
     # 64-bit Shoup product
     derived = sms * 64 * sm_mhz * 1e6 / 10 / 1e9
     tens = tensor_roofline(dom, per_launch_ms, peaks)
-    ncu = ncu_row(args.workload, dom["name"], *tc_sides(ks, pvar))
+    ncu = ncu_row(args.workload, ks.variant_name(pvar, args.chunks), dom["name"],
+                  *tc_sides(ks, pvar))
     roofline = {"bound": "alu", "kernel": dom["name"], "achieved": alu["achieved"],
                 "peak": alu["peak"], "unit": "Gop/s (butterfly-equivalent)",
                 "frac": alu["frac"], "traffic": ncu["traffic"] if ncu else None,
@@ -929,7 +952,8 @@ def main():
         k = {"name": s_["name"], "launches_per_step": n / kprof, "ms_per_launch": round(t, 5),
              "event_ms_per_launch": round(s_["ms"] / n, 5), "alu_frac": round(tc / t, 4),
              "share": round(s_["ms"] / sum(x["ms"] for x in stats), 4)}
-        nc = ncu_row(args.workload, s_["name"], *tc_sides(ks, pvar))
+        nc = ncu_row(args.workload, ks.variant_name(pvar, args.chunks), s_["name"],
+                     *tc_sides(ks, pvar))
         if nc:
             k["dram_bytes"] = nc["traffic"]
             k["algo_bytes"] = s_["bytes"] / n

@@ -89,3 +89,20 @@ def test_reference_arm_prints_the_contract_line(capsys):
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_bench_ncu_rows_follow_the_profiled_plan():
+    """The roofline's ncu traffic row: the profiled plan's own capture when there is
+    one; for the tensor-core-dependent column kernels, the capture with the same kind of
+    conversion; nothing for a kernel of an uncaptured plan otherwise."""
+    import bench
+    r = bench.ncu_row("c3", "DPOB[km4]-tc", "modup_col", True, True)
+    assert r["plan"] == "DPOB[km4]-tc" and r["tensor_pct"] > 0
+    r = bench.ncu_row("c3", "DPOB[km4]-split-tc", "modup_col", True, True)
+    assert r["plan"] == "DPOB[km4]-tc"
+    r = bench.ncu_row("c3", "DPOB[km4]-split-tc", "moddown_col", False, False)
+    assert r["plan"] == "DPOB[km4,dnr4]-split" and "tensor_pct" not in r
+    assert bench.ncu_row("c3", "DPOB[km4]-split-tc", "modup_row_keymult", True, True) is None
+    r = bench.ncu_row("c3", "DPOB[km4,dnr4]-split", "modup_row_keymult", False, False)
+    assert r["traffic"] > 0
+    assert bench.ncu_row("c2", "DPOB-r4", "modup_col", False, False) is None
