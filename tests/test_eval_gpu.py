@@ -14,7 +14,10 @@ pytestmark = pytest.mark.gpu
 
 PLANS = [(ks.KS_DSOB, 0), (ks.KS_DPOB, 0), (ks.KS_DSOC, 3), (ks.KS_DPOC, 2),
          (ks.KS_DPOB | ks.KS_RADIX4, 0), (ks.KS_DPOB | ks.KS_UNFUSED, 0),
-         (ks.KS_DSOC | ks.KS_RADIX16, 2), (ks.KS_DPOC | ks.KS_UNFUSED | ks.KS_RADIX4, 2)]
+         (ks.KS_DSOC | ks.KS_RADIX16, 2), (ks.KS_DPOC | ks.KS_UNFUSED | ks.KS_RADIX4, 2),
+         # the tensor-core conversions (ignored where a context has no tensor-core path)
+         (ks.KS_DPOB | ks.KS_BCONV_TC | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4), 0),
+         (ks.KS_DSOC | ks.KS_BCONV_TC_DOWN, 2)]
 
 
 def rand_ct(prm, level, seed):

@@ -116,12 +116,18 @@ def test_plain_workloads_radix_schedules(cfg):
     check(cfg, 0, SCHEDULES, chunk_list=(3,))
 
 
-@pytest.mark.parametrize("radix", [0, ks.KS_RADIX4, ks.KS_RADIX16])
+# the tensor-core plan the benchmark times at (4, 2^16, 35), with and without its split
+KM4_TC = ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4) | ks.KS_BCONV_TC
+
+
+@pytest.mark.parametrize("radix", [0, ks.KS_RADIX4, ks.KS_RADIX16, KM4_TC,
+                                   KM4_TC | ks.KS_SPLIT_DOWN])
 @pytest.mark.parametrize("cfg", [W.C2, W.C3])
 def test_host_entry_points_with_each_radix(cfg, radix):
     """ks_switch_host and ks_switch_host_async (pinned buffers: the input iNTT reads the
     host input over the CPU-GPU link, the last kernel writes the host output) with the
-    DPOB plan of each radix, over a ring of three host buffers and three calls each."""
+    DPOB plan of each radix and the tensor-core plans, over a ring of three host buffers
+    and three calls each."""
     import torch
     prm = W.make_params(*cfg)
     cases = [oracle_case(cfg, seed) for seed in (0, 1, 2)]
@@ -153,7 +159,8 @@ def test_host_entry_points_with_each_radix(cfg, radix):
 
 @pytest.mark.parametrize("plan", [ks.KS_DPOB | ks.KS_RADIX4,
                                   ks.KS_DPOB | ks.KS_STAGE_RADIX(ks.KS_ST_KM, ks.KS_R4)
-                                  | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R4) | ks.KS_SPLIT_DOWN])
+                                  | ks.KS_STAGE_RADIX(ks.KS_ST_DNR, ks.KS_R4) | ks.KS_SPLIT_DOWN,
+                                  ks.KS_DPOB | KM4_TC, ks.KS_DPOB | KM4_TC | ks.KS_SPLIT_DOWN])
 @pytest.mark.parametrize("cfg", [W.C2, W.C3, (2, 12, 5)])
 def test_host_async_with_caller_scratch_on_three_streams(cfg, plan):
     """ks_switch_host_async_ws: host-buffer KeySwitches in flight on three streams, each
