@@ -291,8 +291,8 @@ int ks_switch_host_async_ws(ks_context *ctx, const uint64_t *d_host, const uint6
  *   chunks >= 4, not with KS_DPOB).
  *   Device: the current device must be the context's (else KS_EINVAL).
  *   Set-up: the first call on a device looks up the array's device address (with
- *   that device current) and keeps it for the life of the process; make that first
- *   call before any stream capture. A device reset (cudaDeviceReset) is not supported.
+ *   that device current) and keeps it for the life of the process. A device reset
+ *   (cudaDeviceReset) is not supported.
  *   Sharing: every call uses the same array and leaves its contents behind; no part
  *   of it needs to start at zero. Calls that overlap on the GPU (other streams,
  *   other threads) race on it: order them, e.g. on one stream.
