@@ -210,3 +210,58 @@ def test_random_batches(k):
     finally:
         for c in ctxs.values():
             c.close()
+
+
+def draw_tc(k: int):
+    """Case k of the tensor-core sweep: a two-pass workload (N = 2^13..2^17) whose digit
+    size alpha is 2..9 (the tensor-core path's range; last digits ragged at random), a
+    level (the top, or a view below it), and a plan with KS_BCONV_TC or
+    KS_BCONV_TC_DOWN over a random dataflow, chunk count, schedule and split."""
+    g = W.rng(13000 + k, 21)
+    logn = int(g.integers(13, 18))
+    cap = {13: 40, 14: 32, 15: 24, 16: 20, 17: 10}[logn]  # L+1 bound: oracle time
+    alpha = int(g.integers(2, 10))
+    dnum = int(g.integers(1, max(1, cap // alpha) + 1))
+    L = max(alpha, dnum * alpha - int(g.integers(0, alpha))) - 1  # L+1 in (.., dnum*alpha]
+    dnum = -(-(L + 1) // alpha)
+    level = L if g.random() < 0.7 or L < 1 else int(g.integers(0, L + 1))
+    base = int(BASES[g.integers(0, 4)])
+    v = base | (ks.KS_BCONV_TC if g.random() < 0.7 else ks.KS_BCONV_TC_DOWN)
+    v |= int(RADIX[g.integers(0, 3)])
+    for st in range(5):
+        if g.random() < 0.5:
+            v |= ks.KS_STAGE_RADIX(st, int(g.integers(1, 4)))
+    if g.random() < 0.4:
+        v |= ks.KS_SPLIT_DOWN
+    if g.random() < 0.3:
+        v |= ks.KS_COLALT_INV
+    chunks = int(g.integers(1, 8)) if base in (ks.KS_DSOC, ks.KS_DPOC) else 0
+    return (dnum, logn, L), level, v, chunks
+
+
+@pytest.mark.parametrize("k", range(24))
+def test_random_tensor_core_plans(k):
+    """The tensor-core basis conversions under random workloads, levels and plans, bit
+    for bit against the oracle."""
+    import torch
+    cfg, level, v, chunks = draw_tc(k)
+    prm = W.make_params(*cfg)
+    assert 2 <= prm.alpha <= 9, cfg
+    g = W.rng(14000 + k, 22)
+    key = W.uniform_limbs(g, prm.mods * (2 * prm.beta), prm.N).reshape(prm.beta, 2, prm.QP,
+                                                                       prm.N)
+    x = W.uniform_limbs(g, prm.q[:level + 1], prm.N)
+    want = O.keyswitch_level(prm, level, x, key)
+    top = ks.Context(prm)
+    view = top.at_level(level) if level < prm.L else top
+    try:
+        out = view.switch(dev(x), dev(key), variant=v, chunks=chunks)
+        torch.cuda.synchronize()
+        got = host(out)
+    finally:
+        if view is not top:
+            view.close()
+        top.close()
+    name = ks.variant_name(v, chunks)
+    assert np.array_equal(got, want), f"{prm.name()} level {level} {name}: " + \
+        first_mismatch(got, want)
