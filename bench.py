@@ -189,11 +189,14 @@ def job_rate(world: int, units_per_rank: int, ms: float) -> float:
 
 
 def workload_config(prm):
-    """The workload, identical on both arms (the plan and the L2 protocol are reported
-    beside it, under "plan")."""
+    """The workload, identical on both arms (the plan and the ring's sizes are reported
+    beside it, under "plan"); `l2` states how the GPU arm keeps L2 from serving repeated
+    inputs."""
     return {"workload": f"plain KeySwitch (dnum,N,L)={prm.name()}", "dnum": prm.dnum,
             "N": prm.N, "L": prm.L, "alpha": prm.alpha, "beta": prm.beta, "QP": prm.QP,
-            "qbits": 50, "pbits": 60}
+            "qbits": 50, "pbits": 60,
+            "l2": "inputs larger than L2: each GPU step switches the next (d, evk, out) set "
+                  "of a ring of distinct sets over 2 x L2"}
 
 
 # ---------------------------------------------------------------------------
