@@ -590,6 +590,12 @@ def eval_measure(args, ks, torch, dev, stream, l2):
                        "ms_fixed": round(tf, 5), "ms_tuned": round(td, 5)}
                 if sel is not None:
                     _, vm, cm = S.CANDS[sel.choose([S.level_shape(prm, level)])[0]]
+                    # the plan the library runs for a selected context (ks_select's rule:
+                    # the tensor-core conversions where the context has them, N >= 2^16
+                    # and more than one digit)
+                    if (ks.ks_context_info(view.h)["tc"] and prm.N >= 1 << 16
+                            and level + 1 > prm.alpha):
+                        vm |= ks.KS_BCONV_TC
                     if (vm, cm) == (fixed, 0):
                         tm = tf
                     elif (vm, cm) == (v, c):

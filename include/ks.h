@@ -420,7 +420,10 @@ int ks_selector_load(const ks_selector *sel);
  * it then synchronizes) and records the pick as the context's selected plan: KS_AUTO
  * uses it when ks_tune has not chosen one, and ks_switch_batch with KS_BATCH_SELECT
  * uses it for jobs naming KS_AUTO. Writes the plan to *variant / *chunks when not
- * null. KS_EINVAL when no selector is installed on the current device. */
+ * null (ks_info.selected_variant reports the same pick). The selected plan runs with
+ * KS_BCONV_TC added where the context has the tensor-core path (ks_info.tc), N >= 2^16
+ * and the input spans more than one digit (L+1 > alpha). KS_EINVAL when no selector is
+ * installed on the current device. */
 int ks_select(ks_context *ctx, int *variant, int *chunks, void *stream);
 
 /* Per-kernel timing with CUDA events, for measurement. Between ks_profile_begin and

@@ -49,6 +49,17 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 constexpr int kSchedMask = 0x3ff << KS_STAGE_SHIFT;
 
+// The plan a selected context runs: the network's pick (a dataflow and radix among
+// integer plans), with the tensor-core basis conversions added where they measured
+// faster: contexts that have them, N >= 2^16 and an input of more than one digit (at
+// (4, 2^16, 35) the tuned per-level plans use them at every level with two or more
+// digits and at none with one).
+int selected_plan(const ks_context *c) {
+  int v = c->sel_variant;
+  if (c->tc_ap > 0 && c->logn >= 16 && c->nq > c->alpha) v |= KS_BCONV_TC;
+  return v;
+}
+
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT |
                   KS_SPLIT_DOWN | KS_BCONV_TC | KS_BCONV_TC_DOWN))
@@ -60,7 +71,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
       variant = c->tuned_variant | (variant & ~0xff);
       if (chunks == 0) chunks = c->tuned_chunks;
     } else if (c->sel_variant > 0) {
-      variant = c->sel_variant | (variant & ~0xff);
+      variant = selected_plan(c) | (variant & ~0xff);
       if (chunks == 0) chunks = c->sel_chunks;
     } else {
       variant = KS_DPOB | (variant & ~0xff);
@@ -1254,7 +1265,7 @@ int ks_switch_batch(const ks_job *jobs, int njobs, int flags, void *stream) {
         int rc = ks_select(c, nullptr, nullptr, stream);
         if (rc) return rc;
       }
-      gplan[g] = {c->sel_variant | (gplan[g].first & ~0xff),
+      gplan[g] = {selected_plan(c) | (gplan[g].first & ~0xff),
                   gplan[g].second ? gplan[g].second : c->sel_chunks};
     }
   }

@@ -150,8 +150,9 @@ def test_library_selector_matches_python_and_plans_a_batch():
                 view.close()
         finally:
             ctx.close()
-    # a batch of small jobs naming KS_AUTO, planned by the installed network
-    cfgs = [(2, 13, 7), (3, 14, 11), (2, 13, 7), (5, 12, 9)]
+    # a batch of jobs naming KS_AUTO, planned by the installed network; (3, 2^16, 11)
+    # runs its pick with the tensor-core conversions added (N >= 2^16, three digits)
+    cfgs = [(2, 13, 7), (3, 14, 11), (2, 13, 7), (5, 12, 9), (3, 16, 11)]
     ctxs, arg, want = {}, [], []
     try:
         for k, cfg in enumerate(cfgs):
@@ -173,8 +174,15 @@ def test_library_selector_matches_python_and_plans_a_batch():
             for k, (_, _, _, out) in enumerate(arg):
                 assert np.array_equal(out.cpu().numpy(), want[k]), (flags, cfgs[k])
         for cfg, c in ctxs.items():
-            v = ks.ks_context_info(c.h)["selected_variant"]
-            assert v == S.CANDS[sel.choose([W.make_params(*cfg)])[0]][1]
+            prm = W.make_params(*cfg)
+            info = ks.ks_context_info(c.h)
+            v, ch = info["selected_variant"], info["selected_chunks"]
+            assert v == S.CANDS[sel.choose([prm])[0]][1]
+            # the plan KS_AUTO runs: the pick, plus KS_BCONV_TC where the rule adds it
+            tc = info["tc"] and prm.N >= 1 << 16 and prm.L + 1 > prm.alpha
+            assert tc == (cfg == (3, 16, 11))
+            runs = v | (ks.KS_BCONV_TC if tc else 0)
+            assert ks.ks_workspace_size(c.h, ks.KS_AUTO, 0) == ks.ks_workspace_size(c.h, runs, ch)
         with pytest.raises(ks.KSError):
             ks.ks_switch_batch(arg, ks.KS_BATCH_SELECT | ks.KS_BATCH_AUTOTUNE)
     finally:
