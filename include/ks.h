@@ -193,8 +193,8 @@ int ks_workspace_size(const ks_context *ctx, int variant, int chunks, size_t *by
  *   variant KS_DSOB..KS_DPOC (| KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | a radix schedule
  *           KS_STAGE_RADIX(..) | KS_COLALT_* | KS_SPLIT_DOWN | KS_BCONV_TC |
  *           KS_BCONV_TC_DOWN), or KS_AUTO (the plan ks_tune chose for this context,
- *           else the one ks_select chose, with its tensor-core rule, else DPOB fused
- *           radix 8)
+ *           else the one ks_select chose, else DPOB fused radix 8; the last two with
+ *           KS_BCONV_TC added where ks_info.tc = 1, N >= 2^16 and L+1 > alpha)
  *   chunks  1..64 output groups for the OC variants (0 = 2; the paper searches 2..10);
  *           ignored for OB
  *   workspace_dev / workspace_bytes: caller scratch of at least

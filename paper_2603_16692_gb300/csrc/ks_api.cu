@@ -49,16 +49,16 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 constexpr int kSchedMask = 0x3ff << KS_STAGE_SHIFT;
 
-// The plan a selected context runs: the network's pick (a dataflow and radix among
-// integer plans), with the tensor-core basis conversions added where they measured
-// faster: contexts that have them, N >= 2^16 and an input of more than one digit (at
+// The tensor-core basis conversions where they measured faster than the integer ones:
+// contexts that have them, N >= 2^16 and an input of more than one digit (at
 // (4, 2^16, 35) the tuned per-level plans use them at every level with two or more
-// digits and at none with one).
-int selected_plan(const ks_context *c) {
-  int v = c->sel_variant;
-  if (c->tc_ap > 0 && c->logn >= 16 && c->nq > c->alpha) v |= KS_BCONV_TC;
-  return v;
+// digits and at none with one). Added to the plans KS_AUTO takes without a tuned one.
+int tc_rule(const ks_context *c) {
+  return c->tc_ap > 0 && c->logn >= 16 && c->nq > c->alpha ? KS_BCONV_TC : 0;
 }
+// The plan a selected context runs: the network's pick (a dataflow and radix among
+// integer plans) with the tensor-core rule.
+int selected_plan(const ks_context *c) { return c->sel_variant | tc_rule(c); }
 
 int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   if (variant & ~(0xff | KS_UNFUSED | KS_RADIX4 | KS_RADIX16 | kSchedMask | KS_COLTILE_ALT |
@@ -67,6 +67,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
   if ((variant & KS_RADIX4) && (variant & KS_RADIX16)) return KS_EINVAL;
   if ((variant & 0xff) == KS_AUTO) {
     // the tuned choice for single KeySwitches, else the selector's, else DPOB radix 8
+    // (the last two with the tensor-core rule)
     if (c->tuned_variant > 0) {
       variant = c->tuned_variant | (variant & ~0xff);
       if (chunks == 0) chunks = c->tuned_chunks;
@@ -74,7 +75,7 @@ int make_plan(const ks_context *c, int variant, int chunks, Plan *pl) {
       variant = selected_plan(c) | (variant & ~0xff);
       if (chunks == 0) chunks = c->sel_chunks;
     } else {
-      variant = KS_DPOB | (variant & ~0xff);
+      variant = KS_DPOB | tc_rule(c) | (variant & ~0xff);
     }
   }
   const int base = variant & 0xff;
