@@ -162,8 +162,8 @@ constexpr int kTcGroups = 2;
 // Geometry. Consumers: GRP groups of 256 threads taking items round-robin (so that one
 // group's waits and barriers overlap the other's arithmetic); a group is two halves of
 // 128 threads, one per target of the pair, 8 points per thread (radix-8 NTT rounds).
-// Per group: a TMEM accumulator (8 M blocks x 32 columns), a constant buffer and two
-// NTT tiles. The column twiddles are read from the table (L1).
+// Per group: a TMEM accumulator (8 M blocks x 32 columns), a double constant buffer and
+// two NTT tiles. The column twiddles are read from the table (L1).
 template <int LOGN, int GRP>
 struct TcGeo {
   static constexpr int LOGA = geo_loga(LOGN), LOGB = LOGN - LOGA;
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(TcGeo<LOGN, GRP>::NT + 64, 1)
     u64 *dst = jp.ws + (PRO == PRO_UP ? wo.tmp : wo.tmp2);
     u64 *tile = sT + (group * 2 + half) * G::TILE_W;
     for (int it = it0 + group, k = 0; it < it1; it += GRP, ++k) {
-      // the pair's decoded items (the producer's info, released with its constants)
+      // the pair's decoded items (the loader's info, released with its constants)
       const int b = k & 1;
       if (!mbar_wait(&bar_b[group][b], (k >> 1) & 1)) atomicExch(a.tab.err, 1);
       const uint32_t w = info_w[group][b][half];
